@@ -1,0 +1,411 @@
+"""FP64 CPU oracle of the Galerkin Helmholtz single-layer operator (test infrastructure).
+
+This package is test infrastructure: only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import it.  It shares no code with
+the CUDA path in ``paper_1804_00995_gb300``; the only common inputs come from
+``synth`` (meshes, directions), which holds none of the operator's arithmetic.
+
+It follows the paper's formulation step by step:
+
+* Sec. 3, Eqs. (approxA), (WB), (A=BWB): quadrature points ``x_k``, weights
+  ``w_k``, the sparse basis matrix ``Phi_kj = phi_j(x_k)`` and ``A = Phi^T W Phi``.
+* Sec. 5, Eq. (BEM): ``V ~ (1/4pi) Phi^T W_x G W_y Phi`` with
+  ``G_kl = exp(ik|x_k - y_l|)/|x_k - y_l|`` evaluated on point clouds.
+* Sec. 5.2 (regularize ... '[1/r]'): a sparse correction on pairs of triangles
+  sharing a vertex, analytic integral in y minus the Gauss sum, outer Gauss in x.
+* Sec. 6.4, Eqs. (Singlelayer), (Singlelayerwf): right-hand side
+  ``F_i = int phi_i exp(ik d.x)`` and the solve ``V lambda = F``.
+
+Readings where the paper is silent (all listed with the design notes): the
+3-point rule is the interior (2/3, 1/6, 1/6) rule; "close enough" means sharing
+at least one vertex; a quadrature point paired with itself gets the kernel's
+smooth limit ``i k`` and is left out of the correction's Gauss sum; the outer
+rule of the correction is the domain's own rule.
+
+Parity unpinned: the absolute accuracy of the paper's regularisation itself
+(the paper prints no values); it is bounded only by the sphere convergence
+checks in the tests.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+import scipy.sparse as sp
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gyps_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C part with gcc (FP64, OpenMP, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            lib.or_quad_rule.argtypes = [ctypes.c_int, dp, dp]
+            lib.or_kernel_matvec.argtypes = [ctypes.c_int64, dp, i64p, ctypes.c_int64, dp,
+                                             ctypes.c_double, ctypes.c_int64, dp, dp]
+            lib.or_kernel_matrix.argtypes = [ctypes.c_int64, dp, i64p, ctypes.c_int64, dp,
+                                             ctypes.c_double, dp]
+            lib.or_p1_inv_r.argtypes = [dp, dp, dp, dp, dp]
+            lib.or_p1_inv_r.restype = None
+            lib.or_near_blocks.argtypes = [dp, i32p, ctypes.c_int, ctypes.c_int64, i64p, i64p, dp]
+            lib.or_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _i32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+# --------------------------------------------------------------------------
+# Sec. 3 / Sec. 4.2: quadrature and the P1 basis matrix
+# --------------------------------------------------------------------------
+
+def quad_rule(q: int):
+    """Reference rule: barycentric points (q, 3) and weights (q,) summing to 1."""
+    bary = np.zeros((q, 3))
+    w = np.zeros(q)
+    if _load().or_quad_rule(q, _dp(bary), _dp(w)) != 0:
+        raise ValueError(f"no {q}-point rule (1, 3 or 7)")
+    return bary, w
+
+
+def triangle_areas(vtx, tri):
+    a, b, c = vtx[tri[:, 0]], vtx[tri[:, 1]], vtx[tri[:, 2]]
+    return 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)
+
+
+def quad_points(vtx, tri, q):
+    """Quadrature points x_k (Nq, 3) and weights w_k (Nq,), k = t*q + j (Eq. approxA)."""
+    bary, w = quad_rule(q)
+    a, b, c = vtx[tri[:, 0]], vtx[tri[:, 1]], vtx[tri[:, 2]]
+    x = (bary[None, :, 0:1] * a[:, None, :] + bary[None, :, 1:2] * b[:, None, :]
+         + bary[None, :, 2:3] * c[:, None, :])
+    wk = triangle_areas(vtx, tri)[:, None] * w[None, :]
+    return x.reshape(-1, 3), wk.reshape(-1)
+
+
+def basis_matrix(tri, nv, q):
+    """Phi (Nq, Nv) with Phi_kj = phi_j(x_k): 3 nonzeros per row (Eq. WB)."""
+    bary, _ = quad_rule(q)
+    nt = tri.shape[0]
+    rows = np.repeat(np.arange(nt * q), 3)
+    cols = np.repeat(tri.astype(np.int64), q, axis=0).reshape(-1)
+    vals = np.tile(bary.reshape(-1), nt)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(nt * q, nv))
+
+
+def mass_matrix(vtx, tri, q):
+    """A = Phi^T W Phi (Eq. A=BWB)."""
+    x, w = quad_points(vtx, tri, q)
+    phi = basis_matrix(tri, vtx.shape[0], q)
+    return (phi.T @ sp.diags(w) @ phi).tocsr()
+
+
+# --------------------------------------------------------------------------
+# Sec. 5: the dense kernel between point clouds
+# --------------------------------------------------------------------------
+
+def kernel_matvec(xt, tid, ys, u, k):
+    """v = G u with G_tl = exp(ik r)/r, G = ik where tid[t] == l (u: (Ns, nrhs) complex)."""
+    lib = _load()
+    xt = np.ascontiguousarray(xt, dtype=np.float64)
+    ys = np.ascontiguousarray(ys, dtype=np.float64)
+    u = np.asarray(u, dtype=np.complex128)
+    if u.ndim == 1:
+        u = u[:, None]
+    nt, ns, nrhs = xt.shape[0], ys.shape[0], u.shape[1]
+    uflat = np.ascontiguousarray(u.ravel(order="F"))     # column-major, interleaved re/im
+    vflat = np.zeros(nt * nrhs, dtype=np.complex128)
+    tidp = None
+    if tid is not None:
+        tid = np.ascontiguousarray(tid, dtype=np.int64)
+        tidp = _i64p(tid)
+    lib.or_kernel_matvec(nt, _dp(xt), tidp, ns, _dp(ys), float(k), nrhs,
+                         _dp(uflat.view(np.float64)), _dp(vflat.view(np.float64)))
+    return vflat.reshape((nt, nrhs), order="F")
+
+
+def kernel_matrix(xt, tid, ys, k):
+    """Dense G (Nt, Ns) complex."""
+    lib = _load()
+    xt = np.ascontiguousarray(xt, dtype=np.float64)
+    ys = np.ascontiguousarray(ys, dtype=np.float64)
+    g = np.zeros((xt.shape[0], ys.shape[0]), dtype=np.complex128)
+    tidp = None
+    if tid is not None:
+        tid = np.ascontiguousarray(tid, dtype=np.int64)
+        tidp = _i64p(tid)
+    lib.or_kernel_matrix(xt.shape[0], _dp(xt), tidp, ys.shape[0], _dp(ys), float(k), _dp(g.view(np.float64)))
+    return g
+
+
+# --------------------------------------------------------------------------
+# Sec. 5.2: singular correction
+# --------------------------------------------------------------------------
+
+def p1_inv_r(x, p0, p1, p2):
+    """int_T lambda_j(y)/|x-y| dy for j = 0, 1, 2 over T = (p0, p1, p2) (closed form)."""
+    lib = _load()
+    out = np.zeros(3)
+    args = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, p0, p1, p2)]
+    lib.or_p1_inv_r(*[_dp(a) for a in args], _dp(out))
+    return out
+
+
+def near_pairs(tri, nv):
+    """Ordered pairs (a, b) of triangles sharing at least one vertex, a == b included.
+
+    Sorted by a, then b.
+    """
+    nt = tri.shape[0]
+    inc = sp.csr_matrix((np.ones(3 * nt), (np.repeat(np.arange(nt), 3), tri.reshape(-1).astype(np.int64))),
+                        shape=(nt, nv))
+    adj = (inc @ inc.T).tocoo()
+    order = np.lexsort((adj.col, adj.row))
+    return adj.row[order].astype(np.int64), adj.col[order].astype(np.int64)
+
+
+def near_blocks(vtx, tri, q, pa, pb):
+    """3x3 correction block for each near pair (rows: test vertices of a, cols: trial of b)."""
+    lib = _load()
+    vtx = np.ascontiguousarray(vtx, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    pa = np.ascontiguousarray(pa, dtype=np.int64)
+    pb = np.ascontiguousarray(pb, dtype=np.int64)
+    out = np.zeros((pa.shape[0], 3, 3))
+    if lib.or_near_blocks(_dp(vtx), _i32p(tri), int(q), pa.shape[0], _i64p(pa), _i64p(pb), _dp(out)) != 0:
+        raise ValueError("bad quadrature order")
+    return out
+
+
+def near_matrix(vtx, tri, q):
+    """Sparse real correction C (Nv, Nv): sum of the blocks placed at their vertex indices."""
+    nv = vtx.shape[0]
+    pa, pb = near_pairs(tri, nv)
+    blk = near_blocks(vtx, tri, q, pa, pb)
+    ti = tri[pa].astype(np.int64)  # (np, 3)
+    tj = tri[pb].astype(np.int64)
+    rows = np.repeat(ti, 3, axis=1).reshape(-1)
+    cols = np.tile(tj, (1, 3)).reshape(-1)
+    c = sp.coo_matrix((blk.reshape(-1), (rows, cols)), shape=(nv, nv)).tocsr()
+    c.sum_duplicates()
+    return c
+
+
+# --------------------------------------------------------------------------
+# The operator on a mesh
+# --------------------------------------------------------------------------
+
+class Mesh:
+    """Mesh + quadrature ``dom(mesh, q)`` and the P1 space on it (Sec. 4.1-4.3)."""
+
+    def __init__(self, vtx, tri, q):
+        self.vtx = np.ascontiguousarray(vtx, dtype=np.float64)
+        self.tri = np.ascontiguousarray(tri, dtype=np.int32)
+        self.q = int(q)
+        self.nv = self.vtx.shape[0]
+        self.nt = self.tri.shape[0]
+        self.x, self.w = quad_points(self.vtx, self.tri, self.q)
+        self.nq = self.x.shape[0]
+        self.phi = basis_matrix(self.tri, self.nv, self.q)
+        self._c = None
+
+    @property
+    def near(self):
+        if self._c is None:
+            self._c = near_matrix(self.vtx, self.tri, self.q)
+        return self._c
+
+    def mass(self):
+        return (self.phi.T @ sp.diags(self.w) @ self.phi).tocsr()
+
+    def quad_ids_of_vertices(self, rows):
+        """Quadrature points in the support of phi_i for each i in rows (sorted unique)."""
+        sub = self.phi[:, np.asarray(rows)].tocsc()
+        return np.unique(sub.indices)
+
+    def far_apply(self, k, x, rows=None):
+        """(1/4pi) Phi^T W_x G W_y Phi x, Eq. (BEM); rows: only these output rows (others 0)."""
+        x = np.asarray(x, dtype=np.complex128)
+        one = x.ndim == 1
+        if one:
+            x = x[:, None]
+        u = self.w[:, None] * (self.phi @ x)                 # W_y Psi x
+        if rows is None:
+            tids = np.arange(self.nq)
+        else:
+            tids = self.quad_ids_of_vertices(rows)
+        v = kernel_matvec(self.x[tids], tids, self.x, u, k)  # G (W_y Psi x), target rows tids
+        vfull = np.zeros((self.nq, x.shape[1]), dtype=np.complex128)
+        vfull[tids] = v
+        y = (self.phi.T @ (self.w[:, None] * vfull)) / (4.0 * np.pi)  # Phi^T W_x (...)
+        if rows is not None:
+            mask = np.zeros(self.nv, dtype=bool)
+            mask[np.asarray(rows)] = True
+            y[~mask] = 0.0
+        return y[:, 0] if one else y
+
+    def apply(self, k, x, rows=None):
+        """V x = far part + C x (Sec. 5.2, listing of Sec. 6.4: LHS = integral + regularize)."""
+        y = self.far_apply(k, x, rows)
+        cx = self.near @ np.asarray(x, dtype=np.complex128)
+        if rows is not None:
+            mask = np.zeros(self.nv, dtype=bool)
+            mask[np.asarray(rows)] = True
+            cx[~mask] = 0.0
+        return y + cx
+
+    def assemble_far(self, k):
+        g = kernel_matrix(self.x, np.arange(self.nq), self.x, k)
+        pw = (sp.diags(self.w) @ self.phi).tocsr()           # W Phi
+        return np.asarray((pw.T @ (pw.T @ g.T).T)) / (4.0 * np.pi)
+
+    def assemble(self, k):
+        """Dense V = (1/4pi) Phi^T W G W Phi + C (Nv, Nv) complex."""
+        return self.assemble_far(k) + self.near.toarray()
+
+    def rhs_planewave(self, k, dirs):
+        """F_i = int phi_i exp(ik d.x) by the domain's rule, one column per direction (Sec. 6.4)."""
+        dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+        p = np.exp(1j * k * (self.x @ dirs.T))               # (Nq, nd)
+        return np.asarray(self.phi.T @ (self.w[:, None] * p))
+
+
+# --------------------------------------------------------------------------
+# Solvers
+# --------------------------------------------------------------------------
+
+def solve_lu(a, f):
+    """Direct solve (the paper's LHS \\ RHS, Sec. 6.4)."""
+    return np.linalg.solve(a, f)
+
+
+def gmres(matvec, f, tol=1e-6, restart=200, maxit=2000, x0=None):
+    """Restarted GMRES for one right-hand side: Arnoldi with classical Gram-Schmidt
+    applied twice, Givens rotations, stop when ||f - A x|| <= tol ||f||.
+
+    Returns (x, iterations, true relative residual).
+    """
+    f = np.asarray(f, dtype=np.complex128)
+    n = f.shape[0]
+    x = np.zeros(n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
+    fn = np.linalg.norm(f)
+    if fn == 0.0:
+        return x, 0, 0.0
+    it = 0
+    while it < maxit:
+        r = f - matvec(x)
+        beta = np.linalg.norm(r)
+        if beta <= tol * fn:
+            break
+        m = min(restart, maxit - it)
+        Q = np.zeros((n, m + 1), dtype=np.complex128)
+        H = np.zeros((m + 1, m), dtype=np.complex128)
+        cs = np.zeros(m, dtype=np.complex128)
+        sn = np.zeros(m, dtype=np.complex128)
+        g = np.zeros(m + 1, dtype=np.complex128)
+        g[0] = beta
+        Q[:, 0] = r / beta
+        j_end = 0
+        for j in range(m):
+            w = matvec(Q[:, j])
+            h = Q[:, : j + 1].conj().T @ w
+            w = w - Q[:, : j + 1] @ h
+            h2 = Q[:, : j + 1].conj().T @ w
+            w = w - Q[:, : j + 1] @ h2
+            h = h + h2
+            hn = np.linalg.norm(w)
+            H[: j + 1, j] = h
+            H[j + 1, j] = hn
+            if hn > 0:
+                Q[:, j + 1] = w / hn
+            # unitary rotations [[conj(c), conj(s)], [-s, c]] with c = a/den, s = b/den
+            for i in range(j):
+                t = np.conj(cs[i]) * H[i, j] + np.conj(sn[i]) * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            a, b = H[j, j], H[j + 1, j]
+            den = np.sqrt(abs(a) ** 2 + abs(b) ** 2)
+            if den == 0:
+                cs[j], sn[j] = 1.0, 0.0
+            else:
+                cs[j] = a / den
+                sn[j] = b / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = np.conj(cs[j]) * g[j]
+            it += 1
+            j_end = j + 1
+            if abs(g[j + 1]) <= tol * fn or hn == 0:
+                break
+        y = np.linalg.solve(np.triu(H[:j_end, :j_end]), g[:j_end])
+        x = x + Q[:, :j_end] @ y
+    res = np.linalg.norm(f - matvec(x)) / fn
+    return x, it, res
+
+
+# --------------------------------------------------------------------------
+# Closed forms on the unit sphere
+# --------------------------------------------------------------------------
+
+def sphere_eigenvalue(n: int, k: float) -> complex:
+    """Single-layer eigenvalue on the unit sphere for degree-n harmonics:
+    1/(2n+1) at k = 0, else i k j_n(k) h_n^(1)(k)."""
+    from scipy.special import spherical_jn, spherical_yn
+    if k == 0.0:
+        return 1.0 / (2 * n + 1)
+    j = spherical_jn(n, k)
+    return 1j * k * j * (j + 1j * spherical_yn(n, k))
+
+
+def mie_density(k: float, d, pts):
+    """Density lambda of V lambda = F on the unit sphere for p_inc = exp(ik d.x):
+    lambda(x) = sum_n (2n+1) i^n P_n(d.x) / (i k h_n^(1)(k))."""
+    from scipy.special import eval_legendre, spherical_jn, spherical_yn
+    d = np.asarray(d, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    pts = np.asarray(pts, dtype=np.float64)
+    c = (pts / np.linalg.norm(pts, axis=1, keepdims=True)) @ d
+    nmax = int(np.ceil(k + 4.0 * k ** (1.0 / 3.0) + 10))
+    lam = np.zeros(pts.shape[0], dtype=np.complex128)
+    for n in range(nmax + 1):
+        h = spherical_jn(n, k) + 1j * spherical_yn(n, k)
+        lam += (2 * n + 1) * (1j ** n) * eval_legendre(n, c) / (1j * k * h)
+    return lam

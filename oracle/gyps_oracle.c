@@ -1,0 +1,293 @@
+/*
+ * Oracle (test infrastructure only): plain FP64 CPU evaluation of the pieces of
+ * the Galerkin single-layer operator that are O(N^2) or need closed-form
+ * integrals.  The sparse factors Phi, W of Eq. (BEM) and the solves live in
+ * oracle/__init__.py.  Only tests, the smoke check and the benchmark's CPU
+ * baseline may load this library; the product path never does.
+ *
+ * Every loop follows the paper's statement directly: no blocking, no fusion.
+ * OpenMP only splits independent target rows across threads.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Quadrature on the reference triangle, Sec. 4.2 (dom(mesh, q)) and Eq.     */
+/* (approxA): points in barycentric coordinates, weights summing to one,     */
+/* scaled by the triangle area by the caller.                                */
+/*   q = 1: centroid.                                                        */
+/*   q = 3: interior points (2/3, 1/6, 1/6) and permutations, weight 1/3.    */
+/*   q = 7: Radon's degree-5 rule (centroid, and two orbits a = (6 -+ s)/21, */
+/*          s = sqrt(15), weights (155 -+ s)/1200).                          */
+/* ------------------------------------------------------------------------ */
+int or_quad_rule(int q, double *bary, double *w)
+{
+    if (q == 1) {
+        bary[0] = bary[1] = bary[2] = 1.0 / 3.0;
+        w[0] = 1.0;
+        return 0;
+    }
+    if (q == 3) {
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) bary[3 * i + j] = (i == j) ? 2.0 / 3.0 : 1.0 / 6.0;
+            w[i] = 1.0 / 3.0;
+        }
+        return 0;
+    }
+    if (q == 7) {
+        double s = sqrt(15.0);
+        double a1 = (6.0 - s) / 21.0, a2 = (6.0 + s) / 21.0;
+        double w1 = (155.0 - s) / 1200.0, w2 = (155.0 + s) / 1200.0;
+        bary[0] = bary[1] = bary[2] = 1.0 / 3.0;
+        w[0] = 9.0 / 40.0;
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) {
+                bary[3 * (1 + i) + j] = (i == j) ? 1.0 - 2.0 * a1 : a1;
+                bary[3 * (4 + i) + j] = (i == j) ? 1.0 - 2.0 * a2 : a2;
+            }
+            w[1 + i] = w1;
+            w[4 + i] = w2;
+        }
+        return 0;
+    }
+    return -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Helmholtz kernel between point clouds, Eq. (BEM) and Eq. (Helmholtz)      */
+/* without the 1/(4 pi) factor (the paper applies it after the integral):    */
+/*   G(x, y) = exp(i k |x - y|) / |x - y|.                                   */
+/* Where target and source are the same quadrature point (tid == sid) the    */
+/* kernel takes its smooth-part limit G := i k, i.e. the limit of            */
+/* (exp(ikr) - 1)/r; the 1/r part of that pair is handled by the singular    */
+/* correction of Sec. 5.2, which leaves that pair out of its Gauss sum.      */
+/* ------------------------------------------------------------------------ */
+static inline void helmholtz_g(const double *x, const double *y, double k, double *gr, double *gi)
+{
+    double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    *gr = cos(k * r) / r;
+    *gi = sin(k * r) / r;
+}
+
+/*
+ * v[t, j] = sum_l G(x_t, y_l) u[l, j]   (the dense product G (W_y Psi x)).
+ *   xt  : nt x 3 target points, tid[t] their point ids (or NULL: none equal)
+ *   ys  : ns x 3 source points, sources have ids 0..ns-1
+ *   u   : complex (interleaved re, im) ns x nrhs, column-major (ld = ns)
+ *   v   : complex nt x nrhs, column-major (ld = nt), overwritten
+ */
+int or_kernel_matvec(int64_t nt, const double *xt, const int64_t *tid,
+                     int64_t ns, const double *ys, double k, int64_t nrhs,
+                     const double *u, double *v)
+{
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; ++t) {
+        for (int64_t j = 0; j < nrhs; ++j) {
+            double ar = 0.0, ai = 0.0;
+            for (int64_t l = 0; l < ns; ++l) {
+                double gr, gi;
+                if (tid != NULL && tid[t] == l) {
+                    gr = 0.0;
+                    gi = k;
+                } else {
+                    helmholtz_g(xt + 3 * t, ys + 3 * l, k, &gr, &gi);
+                }
+                double ur = u[2 * (j * ns + l)], ui = u[2 * (j * ns + l) + 1];
+                ar += gr * ur - gi * ui;
+                ai += gr * ui + gi * ur;
+            }
+            v[2 * (j * nt + t)] = ar;
+            v[2 * (j * nt + t) + 1] = ai;
+        }
+    }
+    return 0;
+}
+
+/* G as a dense complex nt x ns matrix, row-major, interleaved (re, im). */
+int or_kernel_matrix(int64_t nt, const double *xt, const int64_t *tid,
+                     int64_t ns, const double *ys, double k, double *g)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < nt; ++t) {
+        for (int64_t l = 0; l < ns; ++l) {
+            double gr, gi;
+            if (tid != NULL && tid[t] == l) {
+                gr = 0.0;
+                gi = k;
+            } else {
+                helmholtz_g(xt + 3 * t, ys + 3 * l, k, &gr, &gi);
+            }
+            g[2 * (t * ns + l)] = gr;
+            g[2 * (t * ns + l) + 1] = gi;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Closed-form integral of the P1 basis functions times 1/|x - y| over a     */
+/* flat triangle T = (P0, P1, P2), for one observation point x (Sec. 5.2:    */
+/* "the integral in y is computed analytically").                            */
+/*                                                                           */
+/* With n the unit normal, d = (x - P0).n, rho0 = x - d n and R = |x - y|:   */
+/*   lambda_j(y) = lambda_j(rho0) + grad(lambda_j).(y - rho0)   on T,        */
+/* so  I_j = lambda_j(rho0) * S + grad(lambda_j) . Vv  with                  */
+/*   S  = int_T 1/R,   Vv = int_T (y - rho0)/R.                              */
+/* Both come from the edge formulas of Wilton et al. (1984) and Graglia      */
+/* (1993): for edge i with unit tangent t_i, in-plane outward normal         */
+/* m_i = t_i x n, signed distance p_i = (P - rho0).m_i, end abscissae        */
+/* l^-, l^+, end distances R^-, R^+, R0^2 = p_i^2 + d^2 and                  */
+/* f_i = ln((R^+ + l^+)/(R^- + l^-)):                                        */
+/*   S  = sum_i p_i f_i - |d| sum_i [atan(p_i l^+/(R0^2 + |d| R^+))          */
+/*                                  - atan(p_i l^-/(R0^2 + |d| R^-))]        */
+/*   Vv = 1/2 sum_i m_i [R0^2 f_i + l^+ R^+ - l^- R^-]   (Vv = int grad_y R).*/
+/* R + l is evaluated as R0^2/(R - l) when l < 0 to avoid cancellation; the  */
+/* log terms are dropped where R0^2 vanishes (x on an edge line), where      */
+/* their prefactors p_i and R0^2 are zero.                                   */
+/* ------------------------------------------------------------------------ */
+static inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static inline void cross3(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double r_plus_l(double R, double l, double R02)
+{
+    return (l >= 0.0) ? R + l : R02 / (R - l);
+}
+
+void or_p1_inv_r(const double *x, const double *P0, const double *P1, const double *P2, double *out)
+{
+    const double *P[3] = {P0, P1, P2};
+    double e1[3], e2[3], nn[3];
+    for (int c = 0; c < 3; ++c) {
+        e1[c] = P1[c] - P0[c];
+        e2[c] = P2[c] - P0[c];
+    }
+    cross3(e1, e2, nn);
+    double twoA = sqrt(dot3(nn, nn));
+    double n[3] = {nn[0] / twoA, nn[1] / twoA, nn[2] / twoA};
+    double xp0[3] = {x[0] - P0[0], x[1] - P0[1], x[2] - P0[2]};
+    double d = dot3(xp0, n);
+    double ad = fabs(d);
+    double rho0[3] = {x[0] - d * n[0], x[1] - d * n[1], x[2] - d * n[2]};
+    double scale2 = twoA; /* squared length scale of the triangle */
+
+    double S = 0.0, Vv[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < 3; ++i) {
+        const double *Pm = P[i], *Pp = P[(i + 1) % 3];
+        double t[3] = {Pp[0] - Pm[0], Pp[1] - Pm[1], Pp[2] - Pm[2]};
+        double len = sqrt(dot3(t, t));
+        t[0] /= len; t[1] /= len; t[2] /= len;
+        double m[3];
+        cross3(t, n, m);
+        double am[3] = {Pm[0] - rho0[0], Pm[1] - rho0[1], Pm[2] - rho0[2]};
+        double ap[3] = {Pp[0] - rho0[0], Pp[1] - rho0[1], Pp[2] - rho0[2]};
+        double lm = dot3(am, t), lp = dot3(ap, t);
+        double p = dot3(am, m);
+        double R02 = p * p + d * d;
+        double xm[3] = {x[0] - Pm[0], x[1] - Pm[1], x[2] - Pm[2]};
+        double xpp[3] = {x[0] - Pp[0], x[1] - Pp[1], x[2] - Pp[2]};
+        double Rm = sqrt(dot3(xm, xm)), Rp = sqrt(dot3(xpp, xpp));
+        double f = 0.0;
+        if (R02 > 1e-30 * scale2) f = log(r_plus_l(Rp, lp, R02) / r_plus_l(Rm, lm, R02));
+        S += p * f;
+        if (ad > 0.0)
+            S -= ad * (atan(p * lp / (R02 + ad * Rp)) - atan(p * lm / (R02 + ad * Rm)));
+        double vc = 0.5 * (R02 * f + lp * Rp - lm * Rm);
+        Vv[0] += m[0] * vc;
+        Vv[1] += m[1] * vc;
+        Vv[2] += m[2] * vc;
+    }
+    for (int j = 0; j < 3; ++j) {
+        const double *A = P[(j + 1) % 3], *B = P[(j + 2) % 3];
+        double ab[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+        double g[3];
+        cross3(n, ab, g); /* grad lambda_j = n x (P_{j+2} - P_{j+1}) / (2 area) */
+        g[0] /= twoA; g[1] /= twoA; g[2] /= twoA;
+        double rj[3] = {rho0[0] - P[j][0], rho0[1] - P[j][1], rho0[2] - P[j][2]};
+        double lam0 = 1.0 + dot3(g, rj);
+        out[j] = lam0 * S + dot3(g, Vv);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Singular correction of Sec. 5.2 (regularize(S, S, Vh, '[1/r]', Vh)),      */
+/* scaled by 1/(4 pi) as in the paper's listing of Sec. 6.4.  For each       */
+/* ordered pair (a, b) of triangles that share at least one vertex, each     */
+/* quadrature point x_k of a and each local vertex j of b:                   */
+/*   exact_j = int_b lambda_j(y)/|x_k - y| dy          (closed form above)   */
+/*   gauss_j = sum_{l in b, l != k} eta_l lambda_j(y_l)/|x_k - y_l|          */
+/*   block[i][j] += w_k lambda_i(x_k) (exact_j - gauss_j) / (4 pi)           */
+/* The l == k point exists only when a == b; it is the self pair whose      */
+/* kernel value is i k in the dense part.                                    */
+/*   vtx: nv x 3, tri: nt x 3 (int32), pa/pb: npairs ordered pairs           */
+/*   blocks: npairs x 3 x 3 (row i: test vertex of a, column j: trial of b)  */
+/* ------------------------------------------------------------------------ */
+int or_near_blocks(const double *vtx, const int32_t *tri, int q,
+                   int64_t npairs, const int64_t *pa, const int64_t *pb, double *blocks)
+{
+    double bary[21], wr[7];
+    if (or_quad_rule(q, bary, wr) != 0) return -1;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < npairs; ++p) {
+        int64_t a = pa[p], b = pb[p];
+        const double *A[3], *B[3];
+        for (int m = 0; m < 3; ++m) {
+            A[m] = vtx + 3 * (int64_t)tri[3 * a + m];
+            B[m] = vtx + 3 * (int64_t)tri[3 * b + m];
+        }
+        double ea[3], fa[3], na[3], eb[3], fb[3], nb[3];
+        for (int c = 0; c < 3; ++c) {
+            ea[c] = A[1][c] - A[0][c]; fa[c] = A[2][c] - A[0][c];
+            eb[c] = B[1][c] - B[0][c]; fb[c] = B[2][c] - B[0][c];
+        }
+        cross3(ea, fa, na);
+        cross3(eb, fb, nb);
+        double area_a = 0.5 * sqrt(dot3(na, na)), area_b = 0.5 * sqrt(dot3(nb, nb));
+        double blk[9] = {0};
+        for (int kq = 0; kq < q; ++kq) {
+            double xk[3];
+            for (int c = 0; c < 3; ++c)
+                xk[c] = bary[3 * kq] * A[0][c] + bary[3 * kq + 1] * A[1][c] + bary[3 * kq + 2] * A[2][c];
+            double wk = wr[kq] * area_a;
+            double ex[3];
+            or_p1_inv_r(xk, B[0], B[1], B[2], ex);
+            double gs[3] = {0.0, 0.0, 0.0};
+            for (int lq = 0; lq < q; ++lq) {
+                if (a == b && lq == kq) continue;
+                double yl[3];
+                for (int c = 0; c < 3; ++c)
+                    yl[c] = bary[3 * lq] * B[0][c] + bary[3 * lq + 1] * B[1][c] + bary[3 * lq + 2] * B[2][c];
+                double dd[3] = {xk[0] - yl[0], xk[1] - yl[1], xk[2] - yl[2]};
+                double r = sqrt(dot3(dd, dd));
+                double eta = wr[lq] * area_b;
+                for (int j = 0; j < 3; ++j) gs[j] += eta * bary[3 * lq + j] / r;
+            }
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    blk[3 * i + j] += wk * bary[3 * kq + i] * (ex[j] - gs[j]) / (4.0 * M_PI);
+        }
+        for (int e = 0; e < 9; ++e) blocks[9 * p + e] = blk[e];
+    }
+    return 0;
+}
+
+/* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
