@@ -1,0 +1,212 @@
+/*
+ * gyps.h - C ABI of the GB300 Galerkin single-layer library (libgyps.so).
+ *
+ * The operator is the Helmholtz single layer on P1 triangle meshes,
+ *     V_ij = int int phi_i(x) exp(ik|x-y|) / (4 pi |x-y|) phi_j(y) dx dy,
+ * discretised as in Sec. 5, Eq. (BEM) of the paper:
+ *     V ~ (1/4pi) Phi^T W_x G W_y Phi  +  C,
+ * with Gauss points on each triangle, the dense kernel G_kl = exp(ik r_kl)/r_kl
+ * between point clouds, the sparse P1 matrix Phi and the sparse singular
+ * correction C of Sec. 5.2 (analytic y-integral of 1/r minus its Gauss sum, for
+ * triangles sharing a vertex).  The sound-soft sphere example of Sec. 6.4 is the
+ * intended use: V lambda = F with F_i = int phi_i exp(ik d.x).
+ *
+ * Conventions for every call:
+ *  - Return value: GYPS_OK (0) or an error code; gyps_last_error() gives the
+ *    message of the calling thread's last failing call.  No call aborts, traps
+ *    or exits the process; invalid arguments return GYPS_ERR_INVALID.
+ *  - Complex vectors and matrices are interleaved (re, im) pairs of the stated
+ *    type (double2 = two doubles), column-major with a leading dimension counted
+ *    in complex elements (ld >= number of rows).  Column j of an Nv x nrhs
+ *    block X starts at X + j*ldx.
+ *  - The caller owns every array it passes.  Unless a pointer is documented as
+ *    a host pointer, it may be device memory (then the call is asynchronous on
+ *    `stream`) or host memory (then the call copies through library-owned
+ *    device staging and returns after `stream` has finished).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  The library owns mesh handles and the device memory inside them.
+ *  - The wavenumber k must be finite and >= 0 (k = 0 is the Laplace kernel).
+ */
+#ifndef GYPS_H
+#define GYPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GYPS_OK = 0,
+    GYPS_ERR_INVALID = 1,       /* bad argument (sizes, indices, k, degenerate triangle) */
+    GYPS_ERR_CUDA = 2,          /* a CUDA runtime call failed; message names it */
+    GYPS_ERR_OOM = 3,           /* device allocation failed */
+    GYPS_ERR_NOT_CONVERGED = 4, /* GMRES hit maxit; X holds the last iterate */
+    GYPS_ERR_NAN = 5,           /* a non-finite value appeared in the solve */
+    GYPS_ERR_TIMEOUT = 6,       /* a device wait exceeded its iteration limit */
+    GYPS_ERR_UNSUPPORTED = 7    /* option not available on this device/build */
+} gyps_status;
+
+/* Arithmetic of the dense kernel product G u (Sec. 5, Eq. BEM). The sparse
+ * factors, the correction C and the output are FP64 in every mode. */
+typedef enum {
+    GYPS_PREC_FP64 = 0,         /* G and G u in FP64 (the plain reference form) */
+    GYPS_PREC_FP32 = 1,         /* G in FP32 on the CUDA cores, compensated FP32 sums */
+    GYPS_PREC_TC_BF16X3 = 2,    /* G tile x RHS panel on tensor cores, bf16 hi+lo split */
+    GYPS_PREC_AUTO = 4          /* FP32 below 16 right-hand sides, tensor cores above */
+} gyps_prec;
+
+/* gyps_sl_apply flags */
+#define GYPS_APPLY_NO_NEAR 0x1u /* far part (1/4pi) Phi^T W G W Phi only, no correction C */
+
+typedef struct gyps_mesh_s *gyps_mesh_t;
+
+typedef struct {
+    int64_t nv;          /* vertices = P1 degrees of freedom */
+    int64_t nt;          /* triangles */
+    int64_t nq;          /* quadrature points = q * nt */
+    int32_t q;           /* points per triangle (1, 3 or 7) */
+    int32_t device;      /* CUDA device the mesh lives on */
+    int64_t near_pairs;  /* ordered triangle pairs sharing a vertex (a == b included) */
+    int64_t near_nnz;    /* nonzeros of the correction matrix C */
+    int64_t device_bytes;/* device memory held by the handle */
+} gyps_mesh_info_t;
+
+/* Library version string (static storage). */
+const char *gyps_version(void);
+
+/* Copies the calling thread's last error message into buf (NUL-terminated,
+ * truncated to n bytes) and returns the last error code. */
+gyps_status gyps_last_error(char *buf, size_t n);
+
+/*
+ * Mesh + quadrature domain + P1 space: msh, dom(mesh, q) and fem(mesh, 'P1')
+ * of Sec. 4.1-4.3.
+ *   vtx  HOST, nv x 3 doubles, row-major (x, y, z per vertex).
+ *   tri  HOST, nt x 3 int32, row-major, 0-based vertex indices; the orientation
+ *        does not matter to the single layer.
+ *   quad_points  1 (centroid), 3 (interior points (2/3,1/6,1/6)) or 7 (Radon,
+ *        degree 5): the Gauss rule of Sec. 4.2 used on both x and y.
+ *   flags  0.
+ * Builds on the device, on `stream`: the quadrature points and weights (Eq.
+ * approxA), the vertex-to-quadrature-point incidence (Eq. WB), the list of
+ * triangle pairs sharing a vertex and the correction C of Sec. 5.2 in CSR form
+ * (real, independent of k).  Returns after the build finished.
+ * Errors: INVALID for nv < 3, nt < 1, an index outside [0, nv), repeated
+ * vertices in a triangle, a zero-area triangle, non-finite coordinates or an
+ * unsupported quad_points; OOM; CUDA.
+ */
+gyps_status gyps_mesh_create(const double *vtx, int64_t nv, const int32_t *tri, int64_t nt,
+                             int quad_points, uint32_t flags, void *stream, gyps_mesh_t *out);
+
+/* Releases the handle and its device memory (synchronises its device first).
+ * NULL is accepted. */
+gyps_status gyps_mesh_destroy(gyps_mesh_t mesh);
+
+/* Sizes of a mesh. info: HOST. */
+gyps_status gyps_mesh_info(gyps_mesh_t mesh, gyps_mesh_info_t *info);
+
+/*
+ * Quadrature points and weights (x_k, w_k) of Eq. (approxA), k = t*q + j,
+ * written as nq x 4 doubles (x, y, z, w) into xw (device or host).
+ */
+gyps_status gyps_quad_points(gyps_mesh_t mesh, double *xw, void *stream);
+
+/*
+ * The correction matrix C of Sec. 5.2 (already multiplied by 1/(4 pi), as the
+ * listing of Sec. 6.4 adds it), CSR with sorted columns.  All HOST buffers:
+ * rowptr nv+1, col near_nnz, val near_nnz.  Synchronous.
+ */
+gyps_status gyps_near_export(gyps_mesh_t mesh, int64_t *rowptr, int32_t *col, double *val);
+
+/*
+ * Matrix-free single layer (Sec. 5, Eq. BEM, plus the Sec. 5.2 correction):
+ *     Y = (1/4pi) Phi^T W_x G W_y Phi X + C X       (Y is overwritten)
+ * with G_kl = exp(ik r_kl)/r_kl, and G_kk = i k for a point paired with itself
+ * (the limit of the kernel minus its 1/r part, which C carries).
+ *   X  nv x nrhs complex double2, leading dimension ldx >= nv.
+ *   Y  nv x nrhs complex double2, leading dimension ldy >= nv (not aliasing X).
+ *   nrhs  1 .. 4096.
+ *   prec  gyps_prec: arithmetic of the G u product (see above).
+ *   flags  GYPS_APPLY_NO_NEAR leaves C out.
+ *   tri_begin, tri_end  restrict the TEST side to triangles [tri_begin,
+ *        tri_end) (both -1: all).  The far part then sums only over target
+ *        points of those triangles and C only over those test triangles, so
+ *        applies over a partition of the triangles add up to the full apply.
+ * Errors: INVALID (nrhs, ld, k, range), UNSUPPORTED (tensor-core precision
+ * with fewer than 16 right-hand sides), OOM, CUDA, TIMEOUT.
+ */
+gyps_status gyps_sl_apply(gyps_mesh_t mesh, double k, int nrhs, const void *X, int64_t ldx,
+                          void *Y, int64_t ldy, int prec, uint32_t flags,
+                          int64_t tri_begin, int64_t tri_end, void *stream);
+
+/*
+ * Y += C X with the correction C of Sec. 5.2 (regularize(S, S, Vh, '[1/r]', Vh)
+ * times 1/(4 pi)).  X, Y: nv x nrhs complex double2 (device or host).
+ */
+gyps_status gyps_near_correct(gyps_mesh_t mesh, int nrhs, const void *X, int64_t ldx,
+                              void *Y, int64_t ldy, void *stream);
+
+/*
+ * Dense assembly of the whole operator (the listing of Sec. 6.4:
+ * LHS = integral(...)/(4 pi) + regularize(...)/(4 pi)):
+ *     V = (1/4pi) Phi^T W G W Phi + C,   nv x nv complex double2,
+ * column-major with ldv >= nv; V_ij pairs test function i with trial
+ * function j.  prec: GYPS_PREC_FP64 or GYPS_PREC_FP32 (kernel values in FP32,
+ * sums in FP64).  Errors: INVALID, UNSUPPORTED, CUDA.
+ */
+gyps_status gyps_sl_assemble(gyps_mesh_t mesh, double k, int prec, void *V, int64_t ldv, void *stream);
+
+/*
+ * Right-hand sides of the sound-soft example (Sec. 6.4, RHS = integral(S2, Vh,
+ * PW)): F_ij = sum_k w_k phi_i(x_k) exp(i k d_j . x_k) by the mesh's rule.
+ *   dirs  HOST, nrhs x 3 doubles (propagation directions d_j, used as given).
+ *   F     nv x nrhs complex double2, leading dimension ldf.
+ */
+gyps_status gyps_rhs_planewave(gyps_mesh_t mesh, double k, int nrhs, const double *dirs,
+                               void *F, int64_t ldf, void *stream);
+
+/* GMRES options (gyps_gmres_solve). */
+typedef struct {
+    double tol;          /* relative residual ||F - V X|| / ||F|| per column (e.g. 1e-6) */
+    int32_t restart;     /* Krylov dimension m before a restart (>= 1) */
+    int32_t maxit;       /* total inner iterations per call (>= 1) */
+    int32_t prec;        /* gyps_prec of the operator inside the Krylov loop */
+    int32_t check_prec;  /* gyps_prec of the true-residual check (GYPS_PREC_FP64 normally) */
+    int32_t use_x0;      /* 1: X holds the initial guess on entry; 0: start from zero */
+    int32_t max_refine;  /* refinement sweeps when the check exceeds tol (0 = none) */
+} gyps_gmres_opts;
+
+/* GMRES report, HOST.  Arrays are caller-owned, length nrhs, may be NULL. */
+typedef struct {
+    int32_t iterations;      /* inner iterations done (all columns advance together) */
+    int32_t applies;         /* operator applies in the working precision */
+    int32_t check_applies;   /* applies in check_prec */
+    int32_t refinements;     /* refinement sweeps done */
+    double *est_residual;    /* last Arnoldi residual estimate per column (relative) */
+    double *true_residual;   /* ||F - V X||/||F|| with check_prec, per column */
+    int32_t *converged;      /* 1 where true_residual <= tol */
+} gyps_gmres_report;
+
+/*
+ * Solves V X = F (Sec. 6.4, Eq. Singlelayerwf) for nrhs columns by restarted
+ * GMRES: Arnoldi with classical Gram-Schmidt applied twice, in FP64 on the
+ * device, Givens rotations on the host, one Krylov space per column, the
+ * operator applied to all columns at once with `opts->prec`.  After the
+ * Krylov loop the residual is recomputed with `opts->check_prec`; while it is
+ * above tol and refinements remain, GMRES is run on the residual equation
+ * and the correction added (mixed-precision iterative refinement).
+ *   F, X  nv x nrhs complex double2 (device or host).  report: HOST or NULL.
+ * Returns NOT_CONVERGED (X = last iterate) when a column misses tol, NAN
+ * when a non-finite value appears.
+ */
+gyps_status gyps_gmres_solve(gyps_mesh_t mesh, double k, int nrhs, const void *F, int64_t ldf,
+                             void *X, int64_t ldx, const gyps_gmres_opts *opts,
+                             gyps_gmres_report *report, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GYPS_H */

@@ -1,0 +1,304 @@
+"""Python binding of libgyps (GB300 Galerkin Helmholtz single layer on P1 meshes).
+
+Argument marshalling only: every step of the operator runs in the CUDA kernels
+of ``libgyps.so``, behind the C ABI declared in ``include/gyps.h``.  Torch is
+used for device memory and streams.  Importing works without the library; the
+first call that needs it raises ``RuntimeError`` when it has not been built
+(``python -m paper_1804_00995_gb300.build``).
+
+Complex blocks are torch ``complex128`` tensors of shape (nv,) or (nv, nrhs);
+they are passed column-major (stride (1, ld)), copied to that layout when
+needed.  CPU tensors are accepted too: the library then stages them through
+device memory and the call returns when the result is back on the host.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "PREC", "GypsError", "Mesh", "load", "sl_apply", "near_correct", "sl_assemble", "rhs_planewave",
+    "gmres_solve", "version",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgyps.so")
+
+PREC = {"fp64": 0, "fp32": 1, "tc_bf16x3": 2, "auto": 4}
+NO_NEAR = 0x1
+
+_STATUS = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "NAN", 6: "TIMEOUT", 7: "UNSUPPORTED"}
+
+
+class GypsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gyps {_STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.status = _STATUS.get(code, str(code))
+
+
+class _MeshInfo(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int64), ("nt", ctypes.c_int64), ("nq", ctypes.c_int64), ("q", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("near_pairs", ctypes.c_int64), ("near_nnz", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class _GmresOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("check_prec", ctypes.c_int32), ("use_x0", ctypes.c_int32),
+                ("max_refine", ctypes.c_int32)]
+
+
+class _GmresReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("applies", ctypes.c_int32), ("check_applies", ctypes.c_int32),
+                ("refinements", ctypes.c_int32), ("est_residual", ctypes.POINTER(ctypes.c_double)),
+                ("true_residual", ctypes.POINTER(ctypes.c_double)), ("converged", ctypes.POINTER(ctypes.c_int32))]
+
+
+_lib = None
+
+# every symbol the header declares, with its ctypes signature
+_SIGS = {
+    "gyps_version": ([], ctypes.c_char_p),
+    "gyps_last_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+    "gyps_mesh_create": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                          ctypes.c_uint32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "gyps_mesh_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "gyps_mesh_info": ([ctypes.c_void_p, ctypes.POINTER(_MeshInfo)], ctypes.c_int),
+    "gyps_quad_points": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "gyps_near_export": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "gyps_sl_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32, ctypes.c_int64,
+                       ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
+    "gyps_near_correct": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                           ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
+    "gyps_sl_assemble": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                          ctypes.c_void_p], ctypes.c_int),
+    "gyps_rhs_planewave": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
+    "gyps_gmres_solve": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                          ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(_GmresOpts),
+                          ctypes.POINTER(_GmresReport), ctypes.c_void_p], ctypes.c_int),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Loads libgyps.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgyps.so not built at {path}: run python -m paper_1804_00995_gb300.build")
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def version() -> str:
+    return load().gyps_version().decode()
+
+
+def _check(code):
+    if code != 0:
+        buf = ctypes.create_string_buffer(512)
+        load().gyps_last_error(buf, 512)
+        raise GypsError(code, buf.value.decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _colmajor(x, nv, name):
+    """Returns (tensor, nrhs, ld) with x viewed column-major complex128."""
+    torch = _torch()
+    if not isinstance(x, torch.Tensor):
+        x = torch.as_tensor(np.asarray(x))
+    if x.dtype != torch.complex128:
+        x = x.to(torch.complex128)
+    if x.dim() == 1:
+        x = x.reshape(-1, 1)
+    if x.dim() != 2 or x.shape[0] != nv:
+        raise ValueError(f"{name} must have shape (nv,) or (nv, nrhs) with nv={nv}")
+    if x.stride(0) != 1 or x.stride(1) < nv:
+        x = x.t().contiguous().t()
+    return x, x.shape[1], max(x.stride(1), nv) if x.shape[1] > 1 else nv
+
+
+def _empty_colmajor(nv, nrhs, device):
+    torch = _torch()
+    return torch.empty((nrhs, nv), dtype=torch.complex128, device=device).t()
+
+
+@dataclass
+class MeshInfo:
+    nv: int
+    nt: int
+    nq: int
+    q: int
+    device: int
+    near_pairs: int
+    near_nnz: int
+    device_bytes: int
+
+
+class Mesh:
+    """gyps_mesh_create: mesh, Gauss rule dom(mesh, q), P1 space and the correction C."""
+
+    def __init__(self, vtx, tri, q: int = 3, stream=None):
+        lib = load()
+        vtx = np.ascontiguousarray(np.asarray(vtx, dtype=np.float64))
+        tri = np.ascontiguousarray(np.asarray(tri, dtype=np.int32))
+        if vtx.ndim != 2 or vtx.shape[1] != 3 or tri.ndim != 2 or tri.shape[1] != 3:
+            raise ValueError("vtx must be (nv, 3) and tri (nt, 3)")
+        h = ctypes.c_void_p()
+        _check(lib.gyps_mesh_create(vtx.ctypes.data, vtx.shape[0], tri.ctypes.data, tri.shape[0], int(q), 0,
+                                    _stream(stream), ctypes.byref(h)))
+        self._h = h
+        info = _MeshInfo()
+        _check(lib.gyps_mesh_info(self._h, ctypes.byref(info)))
+        self.info = MeshInfo(info.nv, info.nt, info.nq, info.q, info.device, info.near_pairs, info.near_nnz,
+                             info.device_bytes)
+        self.nv, self.nt, self.nq, self.q = info.nv, info.nt, info.nq, info.q
+        self.device = f"cuda:{info.device}"
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("mesh was closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.gyps_mesh_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def quad_points(self, stream=None):
+        """(nq, 4) float64 tensor (x, y, z, w) on the mesh's device."""
+        torch = _torch()
+        out = torch.empty((self.nq, 4), dtype=torch.float64, device=self.device)
+        _check(load().gyps_quad_points(self.handle, out.data_ptr(), _stream(stream)))
+        return out
+
+    def near_csr(self):
+        """Correction matrix C (CSR: rowptr int64, col int32, val float64), host numpy."""
+        rowptr = np.zeros(self.nv + 1, dtype=np.int64)
+        col = np.zeros(self.info.near_nnz, dtype=np.int32)
+        val = np.zeros(self.info.near_nnz, dtype=np.float64)
+        _check(load().gyps_near_export(self.handle, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data))
+        return rowptr, col, val
+
+
+def sl_apply(mesh: Mesh, k: float, X, prec: str = "fp32", near: bool = True, tri_range=None, out=None, stream=None):
+    """Y = (1/4pi) Phi^T W G W Phi X + C X (gyps_sl_apply).  Returns Y shaped like X."""
+    torch = _torch()
+    one = (hasattr(X, "dim") and X.dim() == 1) or (not hasattr(X, "dim") and np.asarray(X).ndim == 1)
+    x, nrhs, ldx = _colmajor(X, mesh.nv, "X")
+    y = out if out is not None else _empty_colmajor(mesh.nv, nrhs, x.device)
+    if y.stride(0) != 1:
+        raise ValueError("out must be column-major")
+    tb, te = (-1, -1) if tri_range is None else (int(tri_range[0]), int(tri_range[1]))
+    _check(load().gyps_sl_apply(mesh.handle, float(k), nrhs, x.data_ptr(), ldx, y.data_ptr(),
+                                max(y.stride(1), mesh.nv) if nrhs > 1 else mesh.nv, PREC[prec],
+                                0 if near else NO_NEAR, tb, te, _stream(stream)))
+    return y[:, 0] if one else y
+
+
+def near_correct(mesh: Mesh, X, Y, stream=None):
+    """Y += C X in place (gyps_near_correct); Y column-major complex128."""
+    x, nrhs, ldx = _colmajor(X, mesh.nv, "X")
+    y = Y.reshape(-1, 1) if Y.dim() == 1 else Y
+    if y.stride(0) != 1 or y.dtype != _torch().complex128:
+        raise ValueError("Y must be column-major complex128")
+    _check(load().gyps_near_correct(mesh.handle, nrhs, x.data_ptr(), ldx, y.data_ptr(),
+                                    max(y.stride(1), mesh.nv) if nrhs > 1 else mesh.nv, _stream(stream)))
+    return Y
+
+
+def sl_assemble(mesh: Mesh, k: float, prec: str = "fp64", device=None, stream=None):
+    """Dense V (nv, nv) complex128, column-major, V[i, j] = test i, trial j (gyps_sl_assemble)."""
+    dev = mesh.device if device is None else device
+    v = _empty_colmajor(mesh.nv, mesh.nv, dev)
+    _check(load().gyps_sl_assemble(mesh.handle, float(k), PREC[prec], v.data_ptr(), mesh.nv, _stream(stream)))
+    return v
+
+
+def rhs_planewave(mesh: Mesh, k: float, dirs, device=None, stream=None):
+    """F (nv, nrhs): F_ij = int phi_i exp(i k d_j . x) (gyps_rhs_planewave)."""
+    dirs = np.ascontiguousarray(np.atleast_2d(np.asarray(dirs, dtype=np.float64)))
+    dev = mesh.device if device is None else device
+    f = _empty_colmajor(mesh.nv, dirs.shape[0], dev)
+    _check(load().gyps_rhs_planewave(mesh.handle, float(k), dirs.shape[0], dirs.ctypes.data, f.data_ptr(), mesh.nv,
+                                     _stream(stream)))
+    return f
+
+
+@dataclass
+class GmresReport:
+    iterations: int
+    applies: int
+    check_applies: int
+    refinements: int
+    est_residual: np.ndarray
+    true_residual: np.ndarray
+    converged: np.ndarray
+    status: str
+
+
+def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, maxit: int = 1000,
+                prec: str = "fp32", check_prec: str = "fp64", x0=None, max_refine: int = 3, raise_on_fail=False,
+                stream=None):
+    """Solves V X = F (gyps_gmres_solve).  Returns (X, GmresReport)."""
+    f, nrhs, ldf = _colmajor(F, mesh.nv, "F")
+    if x0 is not None:
+        x, _, _ = _colmajor(x0.clone() if hasattr(x0, "clone") else x0, mesh.nv, "x0")
+        x = x.to(f.device)
+        if x.stride(1) != mesh.nv and nrhs > 1:
+            x = x.t().contiguous().t()
+    else:
+        x = _empty_colmajor(mesh.nv, nrhs, f.device)
+    opts = _GmresOpts(float(tol), int(restart), int(maxit), PREC[prec], PREC[check_prec], 1 if x0 is not None else 0,
+                      int(max_refine))
+    est = np.zeros(nrhs)
+    tru = np.zeros(nrhs)
+    conv = np.zeros(nrhs, dtype=np.int32)
+    rep = _GmresReport(0, 0, 0, 0, est.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       tru.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       conv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    code = load().gyps_gmres_solve(mesh.handle, float(k), nrhs, f.data_ptr(), ldf, x.data_ptr(), mesh.nv,
+                                   ctypes.byref(opts), ctypes.byref(rep), _stream(stream))
+    if code not in (0, 4) or (code == 4 and raise_on_fail):
+        _check(code)
+    report = GmresReport(rep.iterations, rep.applies, rep.check_applies, rep.refinements, est, tru, conv.astype(bool),
+                         _STATUS[code])
+    return (x[:, 0] if (hasattr(F, "dim") and F.dim() == 1) else x), report

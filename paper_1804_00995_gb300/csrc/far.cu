@@ -1,0 +1,748 @@
+// Matrix-free single layer, Sec. 5 Eq. (BEM) plus the Sec. 5.2 correction:
+//   Y = (1/4pi) Phi^T W_x G W_y Phi X + C X.
+// Steps: interp (u = W_y Phi X, a2), far (v = G u, a3), project
+// (Y = Phi^T W_x v / 4pi, a4) fused with the CSR correction (a5).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace gyps {
+
+constexpr double kInv4Pi = 0.0795774715459476678844418816862571810;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after a fixed number of polls (each poll may suspend
+// the thread for a short, hardware-defined time) instead of spinning forever.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    for (int n = 0; n < (1 << 22); ++n)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion counted on `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"((uint64_t)__cvta_generic_to_global(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ float rsqrt_mufu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_mufu(float x)
+{
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_mufu(float x)
+{
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Error-free sum: hi + lo += x (Knuth's TwoSum, 6 additions).
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
+{
+    float s = __fadd_rn(hi, x);
+    float bp = __fadd_rn(s, -hi);
+    float e = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bp)), __fadd_rn(x, -bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// ---------------------------------------------------------------- a2: interp
+// u_l = eta_l sum_m lambda_m(l) x[v_m(tri(l))]  (W_y Phi x), FP32, written into
+// the density panel of R right-hand sides, columns c0 .. c0+R-1 of X.
+template <int R>
+__global__ void interp32_kernel(const int32_t *tri, const double4_32a *pts64, const Rule rule, int64_t nq, int64_t nq_pad,
+                                const double2 *X, int64_t ldx, int c0, float *panel)
+{
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nq_pad) return;
+    int64_t tile = l / kSrcTile;
+    int p = (int)(l % kSrcTile) >> 1, lane = (int)(l & 1);
+    float *base = panel + tile * den_tile_floats(R);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        double ur = 0.0, ui = 0.0;
+        if (l < nq) {
+            int64_t t = l / rule.q;
+            int kq = (int)(l - t * rule.q);
+            double w = pts64[l].w;
+            const double2 *xc = X + (int64_t)(c0 + j) * ldx;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                double2 xv = xc[tri[3 * t + m]];
+                double lam = rule.bary[3 * kq + m];
+                ur += lam * xv.x;
+                ui += lam * xv.y;
+            }
+            ur *= w;
+            ui *= w;
+        }
+        float *u4 = base + 4 * ((int64_t)p * R + j);
+        u4[lane] = (float)ur;
+        u4[2 + lane] = (float)ui;
+        base[4 * kSrcPairs * R + 2 * ((int64_t)p * R + j) + lane] = -(float)ui;
+    }
+}
+
+// FP64 densities u64[l + j*ld] for all nrhs columns.
+__global__ void interp64_kernel(const int32_t *tri, const double4_32a *pts64, const Rule rule, int64_t nq, int64_t ld,
+                                const double2 *X, int64_t ldx, int nrhs, double2 *u64)
+{
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (l >= nq || j >= nrhs) return;
+    int64_t t = l / rule.q;
+    int kq = (int)(l - t * rule.q);
+    const double2 *xc = X + (int64_t)j * ldx;
+    double ur = 0.0, ui = 0.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        double2 xv = xc[tri[3 * t + m]];
+        double lam = rule.bary[3 * kq + m];
+        ur += lam * xv.x;
+        ui += lam * xv.y;
+    }
+    double w = pts64[l].w;
+    u64[l + j * ld] = make_double2(w * ur, w * ui);
+}
+
+// ---------------------------------------------------------------- a3: far, FP32
+// v[t] += sum_l G(x_t, y_l) u_l, G = exp(ik r)/r, G = ik for l == t.
+//
+// Work = (target tile) x (source tile) items, split evenly over a persistent
+// grid; each CTA walks a contiguous run of items (source tile fastest) and
+// flushes its target accumulators with FP64 atomics whenever the target tile
+// changes.  Source tiles (positions + densities) are staged by 1-D bulk copies
+// into a 3-stage shared-memory ring guarded by mbarriers.  Every thread owns T
+// targets and processes source points in pairs with packed f32x2 arithmetic;
+// rsqrt, sin and cos run on the MUFU unit after reducing the phase k r to
+// [-pi, pi] in turns.  Per-tile FP32 partial sums are folded into a TwoSum
+// (hi, lo) pair so that the rounding error does not grow with the number of
+// source tiles.
+struct FarArgs {
+    const float *pos_panel;
+    const float *den_panel;
+    const float4 *tgt;
+    double2 *v;
+    int64_t ldv;
+    int64_t t_begin, t_end;
+    int64_t n_src_tiles, n_tgt_tiles;
+    float kk;  // k / (2 pi): phase in turns per unit distance
+    float k;
+    int *err;
+};
+
+template <int R, int T>
+struct FarCfg {
+    static constexpr int NT = 128;
+    static constexpr int TT = NT * T;
+    static constexpr int STAGES = 3;
+    static constexpr int POS_BYTES = kPosTileFloats * 4;
+    static constexpr int DEN_BYTES = kSrcPairs * 6 * R * 4;
+    static constexpr int STAGE_BYTES = POS_BYTES + DEN_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 64;
+};
+
+template <int R, int T, bool CHECK>
+__device__ __forceinline__ void far_tile(const float *sp, const float2 (&tx)[T], const float2 (&ty)[T],
+                                         const float2 (&tz)[T], const int64_t (&tid)[T], int64_t src0, float kk, float k,
+                                         float2 (&are)[T][R], float2 (&aim)[T][R])
+{
+    const float4 *XY = reinterpret_cast<const float4 *>(sp);
+    const float2 *Z = reinterpret_cast<const float2 *>(sp + 4 * kSrcPairs);
+    const float4 *U = reinterpret_cast<const float4 *>(sp + 6 * kSrcPairs);
+    const float2 *N = reinterpret_cast<const float2 *>(sp + 6 * kSrcPairs + 4 * kSrcPairs * R);
+    const float2 kk2 = make_float2(kk, kk);
+    const float2 magic = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23: round to integer
+    const float2 nmagic = make_float2(-12582912.0f, -12582912.0f);
+    const float2 neg1 = make_float2(-1.0f, -1.0f);
+    const float2 twopi = make_float2(6.28318530717958647692f, 6.28318530717958647692f);
+#pragma unroll 2
+    for (int p = 0; p < kSrcPairs; ++p) {
+        const float4 xy = XY[p];
+        const float2 z = Z[p];
+        const float2 sx = make_float2(xy.x, xy.y), sy = make_float2(xy.z, xy.w);
+        float2 ure[R], uim[R], unim[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            float4 u = U[p * R + j];
+            ure[j] = make_float2(u.x, u.y);
+            uim[j] = make_float2(u.z, u.w);
+            unim[j] = N[p * R + j];
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            float2 dx = __fadd2_rn(tx[t], sx);
+            float2 dy = __fadd2_rn(ty[t], sy);
+            float2 dz = __fadd2_rn(tz[t], z);
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            float2 rs = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+            float2 ph = __fmul2_rn(__fmul2_rn(r2, rs), kk2);        // k r / (2 pi)
+            float2 nr = __fadd2_rn(__fadd2_rn(ph, magic), nmagic);  // nearest integer
+            float2 ang = __fmul2_rn(__ffma2_rn(nr, neg1, ph), twopi);  // in [-pi, pi]
+            float2 sn = make_float2(sin_mufu(ang.x), sin_mufu(ang.y));
+            float2 cs = make_float2(cos_mufu(ang.x), cos_mufu(ang.y));
+            float2 gre = __fmul2_rn(cs, rs), gim = __fmul2_rn(sn, rs);
+            if (CHECK) {
+                if (src0 + 2 * p == tid[t]) {
+                    gre.x = 0.0f;
+                    gim.x = k;
+                }
+                if (src0 + 2 * p + 1 == tid[t]) {
+                    gre.y = 0.0f;
+                    gim.y = k;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                are[t][j] = __ffma2_rn(gre, ure[j], are[t][j]);
+                are[t][j] = __ffma2_rn(gim, unim[j], are[t][j]);
+                aim[t][j] = __ffma2_rn(gre, uim[j], aim[t][j]);
+                aim[t][j] = __ffma2_rn(gim, ure[j], aim[t][j]);
+            }
+        }
+    }
+}
+
+template <int R, int T>
+__global__ void __launch_bounds__(FarCfg<R, T>::NT) far32_kernel(const FarArgs a)
+{
+    using C = FarCfg<R, T>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE_BYTES);
+    const int tid_x = threadIdx.x;
+
+    const int64_t items = a.n_tgt_tiles * a.n_src_tiles;
+    const int64_t beg = items * blockIdx.x / gridDim.x;
+    const int64_t end = items * (blockIdx.x + 1) / gridDim.x;
+    if (beg >= end) return;
+
+    if (tid_x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    auto issue = [&](int64_t item) {
+        int s = (int)((item - beg) % C::STAGES);
+        int64_t st = item % a.n_src_tiles;
+        uint32_t bar = smem_addr(&bars[s]);
+        uint32_t dst = smem_addr(smem + s * C::STAGE_BYTES);
+        mbar_expect_tx(bar, C::STAGE_BYTES);
+        bulk_g2s(dst, a.pos_panel + st * kPosTileFloats, C::POS_BYTES, bar);
+        bulk_g2s(dst + C::POS_BYTES, a.den_panel + st * den_tile_floats(R), C::DEN_BYTES, bar);
+    };
+    int64_t issued = beg;  // next item to issue
+    if (tid_x == 0)
+        for (; issued < end && issued < beg + C::STAGES - 1; ++issued) issue(issued);
+
+    float2 tx[T], ty[T], tz[T];
+    int64_t tid[T];
+    float2 are[T][R], aim[T][R];
+    float hre[T][R], lre[T][R], him[T][R], lim[T][R];
+    int64_t cur_tt = -1;
+
+    auto flush = [&]() {
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            if (tid[t] < a.t_end) {
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    double *dst = reinterpret_cast<double *>(a.v + tid[t] + j * a.ldv);
+                    atomicAdd(dst, (double)hre[t][j] + (double)lre[t][j]);
+                    atomicAdd(dst + 1, (double)him[t][j] + (double)lim[t][j]);
+                }
+            }
+        }
+    };
+
+    bool failed = false;
+    int64_t i = beg;
+    for (; i < end; ++i) {
+        if (tid_x == 0 && issued < end && issued == i + C::STAGES - 1) {
+            issue(issued);
+            ++issued;
+        }
+        const int64_t tt = i / a.n_src_tiles, st = i % a.n_src_tiles;
+        const int64_t tb = a.t_begin + tt * C::TT;
+        const int64_t te = min(tb + (int64_t)C::TT, a.t_end);
+        if (tt != cur_tt) {
+            if (cur_tt >= 0) flush();
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                int64_t g = tb + tid_x + t * C::NT;
+                tid[t] = g;
+                float4 p = a.tgt[min(g, a.t_end - 1)];
+                tx[t] = make_float2(p.x, p.x);
+                ty[t] = make_float2(p.y, p.y);
+                tz[t] = make_float2(p.z, p.z);
+#pragma unroll
+                for (int j = 0; j < R; ++j) hre[t][j] = lre[t][j] = him[t][j] = lim[t][j] = 0.0f;
+            }
+            cur_tt = tt;
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int j = 0; j < R; ++j) are[t][j] = aim[t][j] = make_float2(0.0f, 0.0f);
+
+        const int s = (int)((i - beg) % C::STAGES);
+        const uint32_t parity = (uint32_t)(((i - beg) / C::STAGES) & 1);
+        bool ok = mbar_wait_bounded(smem_addr(&bars[s]), parity);
+        if (ok) {
+            const float *sp = reinterpret_cast<const float *>(smem + s * C::STAGE_BYTES);
+            const int64_t src0 = st * kSrcTile;
+            if (tb < src0 + kSrcTile && src0 < te)
+                far_tile<R, T, true>(sp, tx, ty, tz, tid, src0, a.kk, a.k, are, aim);
+            else
+                far_tile<R, T, false>(sp, tx, ty, tz, tid, src0, a.kk, a.k, are, aim);
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    two_sum_acc(hre[t][j], lre[t][j], __fadd_rn(are[t][j].x, are[t][j].y));
+                    two_sum_acc(him[t][j], lim[t][j], __fadd_rn(aim[t][j].x, aim[t][j].y));
+                }
+        }
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+    }
+    if (failed) {
+        // Report, then wait (bounded) for the copies still in flight before the
+        // shared memory they target is released.
+        if (tid_x == 0) {
+            atomicExch(a.err, 1);
+            for (int64_t j = i; j < issued; ++j) {
+                int s = (int)((j - beg) % C::STAGES);
+                mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)(((j - beg) / C::STAGES) & 1));
+            }
+        }
+        __syncthreads();
+        return;
+    }
+    flush();
+}
+
+// ---------------------------------------------------------------- a3: far, FP64
+// The plain FP64 form: one thread per target, all sources streamed through
+// shared memory, exp(ikr)/r from FP64 sincos and rsqrt.
+template <int R>
+__global__ void __launch_bounds__(128) far64_kernel(const double4_32a *pts, const double2 *u64, int64_t ldu, int c0, int64_t nq,
+                                                    double k, int64_t t_begin, int64_t t_end, double2 *v, int64_t ldv)
+{
+    __shared__ double4_32a sp[128];
+    __shared__ double2 su[128][R];
+    const int64_t tg = t_begin + (int64_t)blockIdx.x * 128 + threadIdx.x;
+    const double4_32a x = pts[min(tg, t_end - 1)];
+    double ar[R], ai[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) ar[j] = ai[j] = 0.0;
+    for (int64_t s0 = 0; s0 < nq; s0 += 128) {
+        int64_t l = s0 + threadIdx.x;
+        if (l < nq) {
+            sp[threadIdx.x] = pts[l];
+#pragma unroll
+            for (int j = 0; j < R; ++j) su[threadIdx.x][j] = u64[l + (int64_t)(c0 + j) * ldu];
+        }
+        __syncthreads();
+        const int n = (int)min((int64_t)128, nq - s0);
+        for (int ll = 0; ll < n; ++ll) {
+            double4_32a y = sp[ll];
+            double gr, gi;
+            if (s0 + ll == tg) {
+                gr = 0.0;
+                gi = k;
+            } else {
+                double dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+                double r2 = dx * dx + dy * dy + dz * dz;
+                double ri = rsqrt(r2);
+                double sn, cs;
+                sincos(k * (r2 * ri), &sn, &cs);
+                gr = cs * ri;
+                gi = sn * ri;
+            }
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                double2 uu = su[ll][j];
+                ar[j] += gr * uu.x - gi * uu.y;
+                ai[j] += gr * uu.y + gi * uu.x;
+            }
+        }
+        __syncthreads();
+    }
+    if (tg < t_end) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) v[tg + (int64_t)(c0 + j) * ldv] = make_double2(ar[j], ai[j]);
+    }
+}
+
+// ---------------------------------------------------------------- a4 + a5
+// y_i = (1/4pi) sum_{k in supp phi_i} w_k lambda_i(x_k) v_k  [+ sum_c C_ic x_c]
+__global__ void project_kernel(const int32_t *v2t_ptr, const int32_t *v2t, const double4_32a *pts64, const Rule rule,
+                               int64_t nv, const double2 *v, int64_t ldv, const int32_t *c_rowptr,
+                               const int32_t *c_col, const double *c_val, const double2 *X, int64_t ldx, double2 *Y,
+                               int64_t ldy, int with_near)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= nv) return;
+    const double2 *vc = v + (int64_t)j * ldv;
+    double yr = 0.0, yi = 0.0;
+    for (int32_t e = v2t_ptr[i]; e < v2t_ptr[i + 1]; ++e) {
+        int32_t te = v2t[e];
+        int64_t t = te / 3;
+        int m = te - 3 * (int)t;
+        for (int kq = 0; kq < rule.q; ++kq) {
+            int64_t kidx = t * rule.q + kq;
+            double c = pts64[kidx].w * rule.bary[3 * kq + m];
+            double2 vv = vc[kidx];
+            yr += c * vv.x;
+            yi += c * vv.y;
+        }
+    }
+    yr *= kInv4Pi;
+    yi *= kInv4Pi;
+    if (with_near) {
+        const double2 *xc = X + (int64_t)j * ldx;
+        for (int32_t c = c_rowptr[i]; c < c_rowptr[i + 1]; ++c) {
+            double cv = c_val[c];
+            double2 xv = xc[c_col[c]];
+            yr += cv * xv.x;
+            yi += cv * xv.y;
+        }
+    }
+    Y[i + (int64_t)j * ldy] = make_double2(yr, yi);
+}
+
+// Y += C X (CSR, real C, complex X), one thread per (row, column).
+__global__ void near_spmv_kernel(const int32_t *c_rowptr, const int32_t *c_col, const double *c_val, int64_t nv,
+                                 const double2 *X, int64_t ldx, double2 *Y, int64_t ldy)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= nv) return;
+    const double2 *xc = X + (int64_t)j * ldx;
+    double yr = 0.0, yi = 0.0;
+    for (int32_t c = c_rowptr[i]; c < c_rowptr[i + 1]; ++c) {
+        double cv = c_val[c];
+        double2 xv = xc[c_col[c]];
+        yr += cv * xv.x;
+        yi += cv * xv.y;
+    }
+    double2 *y = Y + i + (int64_t)j * ldy;
+    *y = make_double2(y->x + yr, y->y + yi);
+}
+
+// Correction restricted to test triangles [pa_begin, pa_end) of the pair list:
+// Y[v_i(a)] += sum_j block_ab[i][j] X[v_j(b)] (atomics: rows are shared).
+__global__ void near_partial_kernel(const int32_t *pair_a, const int32_t *pair_b, const double *blocks,
+                                    const int32_t *tri, int64_t p_begin, int64_t p_end, const double2 *X, int64_t ldx,
+                                    double2 *Y, int64_t ldy)
+{
+    int64_t p = p_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (p >= p_end) return;
+    const int64_t a = pair_a[p], b = pair_b[p];
+    const double2 *xc = X + (int64_t)j * ldx;
+    double2 xb[3];
+    for (int c = 0; c < 3; ++c) xb[c] = xc[tri[3 * b + c]];
+    for (int r = 0; r < 3; ++r) {
+        double yr = 0.0, yi = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double bv = blocks[9 * p + 3 * r + c];
+            yr += bv * xb[c].x;
+            yi += bv * xb[c].y;
+        }
+        double *y = reinterpret_cast<double *>(Y + tri[3 * a + r] + (int64_t)j * ldy);
+        atomicAdd(y, yr);
+        atomicAdd(y + 1, yi);
+    }
+}
+
+cudaError_t launch_near_spmv(const Mesh &m, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
+                             cudaStream_t s)
+{
+    dim3 g((unsigned)((m.nv + 127) / 128), (unsigned)nrhs);
+    near_spmv_kernel<<<g, 128, 0, s>>>(m.d_c_rowptr, m.d_c_col, m.d_c_val, m.nv, X, ldx, Y, ldy);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- drivers
+template <int R, int T>
+static gyps_status run_far32(Mesh *m, double k, const double2 *X, int64_t ldx, int c0, double2 *v, int64_t ldv,
+                             int64_t t_begin, int64_t t_end, cudaStream_t s)
+{
+    using C = FarCfg<R, T>;
+    float *panel = reinterpret_cast<float *>(m->ws_den);
+    interp32_kernel<R><<<(unsigned)((m->nq_pad + 255) / 256), 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq,
+                                                                           m->nq_pad, X, ldx, c0, panel);
+    GYPS_CUDA(cudaGetLastError());
+    GYPS_CUDA(cudaFuncSetAttribute(far32_kernel<R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    int occ = 0;
+    GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, far32_kernel<R, T>, C::NT, C::SMEM));
+    occ = std::max(occ, 1);
+    FarArgs a;
+    a.pos_panel = m->d_pos_panel;
+    a.den_panel = panel;
+    a.tgt = m->d_pts32;
+    a.v = v + (int64_t)c0 * ldv;
+    a.ldv = ldv;
+    a.t_begin = t_begin;
+    a.t_end = t_end;
+    a.n_src_tiles = m->n_src_tiles;
+    a.n_tgt_tiles = (t_end - t_begin + C::TT - 1) / C::TT;
+    a.kk = (float)(k / kTwoPi);
+    a.k = (float)k;
+    a.err = m->d_err;
+    int64_t items = a.n_tgt_tiles * a.n_src_tiles;
+    int64_t grid = std::min<int64_t>((int64_t)m->num_sms * occ, items);
+    far32_kernel<R, T><<<(unsigned)grid, C::NT, C::SMEM, s>>>(a);
+    GYPS_CUDA(cudaGetLastError());
+    return GYPS_OK;
+}
+
+template <int R>
+static gyps_status run_far64(Mesh *m, double k, const double2 *u64, int64_t ldu, int c0, double2 *v, int64_t ldv,
+                             int64_t t_begin, int64_t t_end, cudaStream_t s)
+{
+    unsigned grid = (unsigned)((t_end - t_begin + 127) / 128);
+    far64_kernel<R><<<grid, 128, 0, s>>>(m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, v, ldv);
+    GYPS_CUDA(cudaGetLastError());
+    return GYPS_OK;
+}
+
+// Splits nrhs into register-resident chunks of 8, 4, 2 and 1 columns.
+static int chunk_width(int left) { return left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1; }
+
+gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
+                         int prec, uint32_t flags, int64_t tri_begin, int64_t tri_end, cudaStream_t s)
+{
+    if (prec == GYPS_PREC_AUTO) prec = GYPS_PREC_FP32;
+    if (prec == GYPS_PREC_TC_BF16X3)
+        return set_error(GYPS_ERR_UNSUPPORTED, "tensor-core precision is not available in this build");
+    if (prec != GYPS_PREC_FP32 && prec != GYPS_PREC_FP64) return set_error(GYPS_ERR_INVALID, "unknown precision");
+    const bool full = (tri_begin == 0 && tri_end == m->nt);
+    const int64_t t_begin = tri_begin * m->q, t_end = tri_end * m->q;
+
+    // v: nq x nrhs FP64 accumulators (zeroed: the FP32 kernel adds into it,
+    // and targets outside a partial range must read as zero)
+    const int64_t ldv = m->nq;
+    GYPS_TRY(grow(m, &m->ws_v, &m->ws_v_bytes, (size_t)(ldv * nrhs) * sizeof(double2)));
+    double2 *v = reinterpret_cast<double2 *>(m->ws_v);
+    GYPS_CUDA(cudaMemsetAsync(v, 0, (size_t)(ldv * nrhs) * sizeof(double2), s));
+
+    if (t_end > t_begin) {
+        if (prec == GYPS_PREC_FP32) {
+            GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(m->n_src_tiles * den_tile_floats(8)) * sizeof(float)));
+            for (int c0 = 0; c0 < nrhs;) {
+                int w = chunk_width(nrhs - c0);
+                gyps_status st;
+                switch (w) {
+                case 8: st = run_far32<8, 2>(m, k, X, ldx, c0, v, ldv, t_begin, t_end, s); break;
+                case 4: st = run_far32<4, 2>(m, k, X, ldx, c0, v, ldv, t_begin, t_end, s); break;
+                case 2: st = run_far32<2, 4>(m, k, X, ldx, c0, v, ldv, t_begin, t_end, s); break;
+                default: st = run_far32<1, 4>(m, k, X, ldx, c0, v, ldv, t_begin, t_end, s); break;
+                }
+                GYPS_TRY(st);
+                c0 += w;
+            }
+        } else {
+            const int64_t ldu = m->nq;
+            GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(ldu * nrhs) * sizeof(double2)));
+            double2 *u64 = reinterpret_cast<double2 *>(m->ws_den);
+            dim3 g((unsigned)((m->nq + 255) / 256), (unsigned)nrhs);
+            interp64_kernel<<<g, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, ldu, X, ldx, nrhs, u64);
+            GYPS_CUDA(cudaGetLastError());
+            for (int c0 = 0; c0 < nrhs;) {
+                int w = chunk_width(nrhs - c0);
+                gyps_status st;
+                switch (w) {
+                case 8: st = run_far64<8>(m, k, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
+                case 4: st = run_far64<4>(m, k, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
+                case 2: st = run_far64<2>(m, k, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
+                default: st = run_far64<1>(m, k, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
+                }
+                GYPS_TRY(st);
+                c0 += w;
+            }
+        }
+    }
+    const bool near = !(flags & GYPS_APPLY_NO_NEAR);
+    dim3 g((unsigned)((m->nv + 127) / 128), (unsigned)nrhs);
+    project_kernel<<<g, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_pts64, m->rule, m->nv, v, ldv, m->d_c_rowptr,
+                                     m->d_c_col, m->d_c_val, X, ldx, Y, ldy, (near && full) ? 1 : 0);
+    GYPS_CUDA(cudaGetLastError());
+    if (near && !full) {
+        const int32_t pp[2] = {m->h_pair_ptr[tri_begin], m->h_pair_ptr[tri_end]};
+        if (pp[1] > pp[0]) {
+            dim3 gp((unsigned)((pp[1] - pp[0] + 127) / 128), (unsigned)nrhs);
+            near_partial_kernel<<<gp, 128, 0, s>>>(m->d_pair_a, m->d_pair_b, m->d_blocks, m->d_tri, pp[0], pp[1], X, ldx,
+                                                   Y, ldy);
+            GYPS_CUDA(cudaGetLastError());
+        }
+    }
+    return GYPS_OK;
+}
+
+// Host staging of an nv x nrhs complex block with leading dimension ld.
+static gyps_status stage_in(Mesh *m, const void *src, int64_t ld, int nrhs, double2 *dst, cudaStream_t s)
+{
+    GYPS_CUDA(cudaMemcpy2DAsync(dst, m->nv * sizeof(double2), src, ld * sizeof(double2), m->nv * sizeof(double2), nrhs,
+                                cudaMemcpyHostToDevice, s));
+    return GYPS_OK;
+}
+static gyps_status stage_out(Mesh *m, const double2 *src, void *dst, int64_t ld, int nrhs, cudaStream_t s)
+{
+    GYPS_CUDA(cudaMemcpy2DAsync(dst, ld * sizeof(double2), src, m->nv * sizeof(double2), m->nv * sizeof(double2), nrhs,
+                                cudaMemcpyDeviceToHost, s));
+    return GYPS_OK;
+}
+
+gyps_status check_err_word(Mesh *m, cudaStream_t s)
+{
+    int h = 0;
+    GYPS_CUDA(cudaMemcpyAsync(&h, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GYPS_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        GYPS_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(int), s));
+        return set_error(GYPS_ERR_TIMEOUT, "a device wait ran out of polls; results are incomplete");
+    }
+    return GYPS_OK;
+}
+
+}  // namespace gyps
+
+using namespace gyps;
+
+static gyps_status check_block(const Mesh *m, int nrhs, const void *X, int64_t ldx, const char *name)
+{
+    if (!X) return set_error(GYPS_ERR_INVALID, std::string(name) + " is NULL");
+    if (nrhs < 1 || nrhs > 4096) return set_error(GYPS_ERR_INVALID, "nrhs must be in 1..4096");
+    if (ldx < m->nv) return set_error(GYPS_ERR_INVALID, std::string("leading dimension of ") + name + " < nv");
+    return GYPS_OK;
+}
+
+extern "C" gyps_status gyps_sl_apply(gyps_mesh_t h, double k, int nrhs, const void *X, int64_t ldx, void *Y,
+                                     int64_t ldy, int prec, uint32_t flags, int64_t tri_begin, int64_t tri_end,
+                                     void *stream)
+{
+    Mesh *m;
+    GYPS_TRY(check_mesh(h, &m));
+    GYPS_TRY(check_block(m, nrhs, X, ldx, "X"));
+    GYPS_TRY(check_block(m, nrhs, Y, ldy, "Y"));
+    if (!std::isfinite(k) || k < 0.0) return set_error(GYPS_ERR_INVALID, "k must be finite and >= 0");
+    if (flags & ~GYPS_APPLY_NO_NEAR) return set_error(GYPS_ERR_INVALID, "unknown flag");
+    if (tri_begin == -1 && tri_end == -1) {
+        tri_begin = 0;
+        tri_end = m->nt;
+    }
+    if (tri_begin < 0 || tri_end > m->nt || tri_begin > tri_end)
+        return set_error(GYPS_ERR_INVALID, "triangle range outside [0, nt]");
+    if (prec != GYPS_PREC_FP64 && prec != GYPS_PREC_FP32 && prec != GYPS_PREC_TC_BF16X3 && prec != GYPS_PREC_AUTO)
+        return set_error(GYPS_ERR_INVALID, "unknown precision");
+    if (prec == GYPS_PREC_TC_BF16X3 && nrhs < 16)
+        return set_error(GYPS_ERR_UNSUPPORTED, "tensor-core precision needs at least 16 right-hand sides");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dx = is_device_pointer(X), dy = is_device_pointer(Y);
+    if (dx && dy) {
+        if ((const char *)X < (const char *)Y + ldy * nrhs * 16 && (const char *)Y < (const char *)X + ldx * nrhs * 16)
+            return set_error(GYPS_ERR_INVALID, "X and Y overlap");
+        GYPS_TRY(apply_device(m, k, nrhs, (const double2 *)X, ldx, (double2 *)Y, ldy, prec, flags, tri_begin, tri_end, s));
+        return GYPS_OK;
+    }
+    // host buffers: stage through library-owned device memory, then wait
+    const size_t blk = (size_t)m->nv * nrhs * sizeof(double2);
+    GYPS_TRY(grow(m, &m->ws_stage, &m->ws_stage_bytes, 2 * blk));
+    double2 *xs = reinterpret_cast<double2 *>(m->ws_stage), *ys = xs + (size_t)m->nv * nrhs;
+    const double2 *xin = (const double2 *)X;
+    int64_t lxin = ldx;
+    if (!dx) {
+        GYPS_TRY(stage_in(m, X, ldx, nrhs, xs, s));
+        xin = xs;
+        lxin = m->nv;
+    }
+    double2 *yout = dy ? (double2 *)Y : ys;
+    int64_t lyout = dy ? ldy : m->nv;
+    GYPS_TRY(apply_device(m, k, nrhs, xin, lxin, yout, lyout, prec, flags, tri_begin, tri_end, s));
+    if (!dy) GYPS_TRY(stage_out(m, ys, Y, ldy, nrhs, s));
+    GYPS_CUDA(cudaStreamSynchronize(s));
+    return check_err_word(m, s);
+}
+
+extern "C" gyps_status gyps_near_correct(gyps_mesh_t h, int nrhs, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                                         void *stream)
+{
+    Mesh *m;
+    GYPS_TRY(check_mesh(h, &m));
+    GYPS_TRY(check_block(m, nrhs, X, ldx, "X"));
+    GYPS_TRY(check_block(m, nrhs, Y, ldy, "Y"));
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dx = is_device_pointer(X), dy = is_device_pointer(Y);
+    if (dx && dy) {
+        GYPS_CUDA(launch_near_spmv(*m, nrhs, (const double2 *)X, ldx, (double2 *)Y, ldy, s));
+        return GYPS_OK;
+    }
+    const size_t blk = (size_t)m->nv * nrhs * sizeof(double2);
+    GYPS_TRY(grow(m, &m->ws_stage, &m->ws_stage_bytes, 2 * blk));
+    double2 *xs = reinterpret_cast<double2 *>(m->ws_stage), *ys = xs + (size_t)m->nv * nrhs;
+    const double2 *xin = (const double2 *)X;
+    int64_t lxin = ldx;
+    if (!dx) {
+        GYPS_TRY(stage_in(m, X, ldx, nrhs, xs, s));
+        xin = xs;
+        lxin = m->nv;
+    }
+    double2 *yio = (double2 *)Y;
+    int64_t lyio = ldy;
+    if (!dy) {
+        GYPS_TRY(stage_in(m, Y, ldy, nrhs, ys, s));
+        yio = ys;
+        lyio = m->nv;
+    }
+    GYPS_CUDA(launch_near_spmv(*m, nrhs, xin, lxin, yio, lyio, s));
+    if (!dy) GYPS_TRY(stage_out(m, ys, Y, ldy, nrhs, s));
+    GYPS_CUDA(cudaStreamSynchronize(s));
+    return GYPS_OK;
+}

@@ -1,0 +1,122 @@
+// Internal declarations of libgyps: mesh handle, error plumbing, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gyps.h"
+
+namespace gyps {
+
+// ---------------------------------------------------------------- errors
+gyps_status set_error(gyps_status code, const std::string &msg);
+gyps_status cuda_error(cudaError_t e, const char *what);
+
+#define GYPS_CUDA(call)                                              \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return ::gyps::cuda_error(e_, #call); \
+    } while (0)
+
+#define GYPS_TRY(call)                          \
+    do {                                        \
+        gyps_status s_ = (call);                \
+        if (s_ != GYPS_OK) return s_;           \
+    } while (0)
+
+// ---------------------------------------------------------------- layout
+// Source panels of the FP32 far kernel are cut into tiles of kSrcTile points.
+// Inside a tile, points are taken in pairs (2p, 2p+1) so that one packed
+// f32x2 instruction handles both; a tile of the position panel holds
+//   float4 XY[P] = (-x0, -x1, -y0, -y1), float2 Z[P] = (-z0, -z1),   P = kSrcTile/2,
+// and a tile of the density panel for R right-hand sides holds
+//   float4 U[P][R] = (re0, re1, im0, im1), float2 N[P][R] = (-im0, -im1).
+// Padding points sit far away with zero density.
+constexpr int kSrcTile = 256;
+constexpr int kSrcPairs = kSrcTile / 2;
+constexpr int kPosTileFloats = kSrcPairs * 6;
+__host__ __device__ constexpr int64_t den_tile_floats(int R) { return (int64_t)kSrcPairs * 6 * R; }
+
+// Reference quadrature rule (barycentric points, weights summing to 1), passed
+// to kernels by value.
+struct Rule {
+    int q;
+    double bary[21];
+    double w[7];
+};
+
+// ---------------------------------------------------------------- mesh
+struct Mesh {
+    int device = 0;
+    int64_t nv = 0, nt = 0, nq = 0;
+    int q = 0;
+    Rule rule{};
+    int64_t nq_pad = 0;   // nq rounded up to kSrcTile
+    int64_t n_src_tiles = 0;
+
+    // geometry on the device
+    double *d_vtx = nullptr;      // nv x 3
+    int32_t *d_tri = nullptr;     // nt x 3
+    double4_32a *d_pts64 = nullptr;   // nq: (x, y, z, w_k)
+    float4 *d_pts32 = nullptr;    // nq: (x, y, z, w_k) rounded to FP32
+    float *d_pos_panel = nullptr; // n_src_tiles * kPosTileFloats
+
+    // vertex -> (triangle, local vertex) incidence, CSR over vertices
+    int32_t *d_v2t_ptr = nullptr; // nv + 1
+    int32_t *d_v2t = nullptr;     // 3 nt, entries 3*t + m
+
+    // singular correction (Sec. 5.2)
+    int64_t npairs = 0;
+    int32_t *d_pair_a = nullptr, *d_pair_b = nullptr;  // sorted by a
+    int32_t *d_pair_ptr = nullptr;                     // nt + 1, pairs of test triangle a
+    std::vector<int32_t> h_pair_ptr;                   // host copy
+    double *d_blocks = nullptr;                        // npairs x 9
+    int64_t c_nnz = 0;
+    int32_t *d_c_rowptr = nullptr;                     // nv + 1
+    int32_t *d_c_col = nullptr;                        // c_nnz
+    double *d_c_val = nullptr;                         // c_nnz
+    int32_t *d_c_src_ptr = nullptr;                    // c_nnz + 1
+    int32_t *d_c_src = nullptr;                        // 9 npairs: block entries per nonzero
+    std::vector<int32_t> h_c_rowptr, h_c_col;          // host copy of the pattern
+
+    // device error word (bounded waits that ran out set it)
+    int *d_err = nullptr;
+
+    // workspace grown on demand
+    void *ws_den = nullptr; size_t ws_den_bytes = 0;   // density panel / FP64 densities
+    void *ws_v = nullptr; size_t ws_v_bytes = 0;       // target accumulators
+    void *ws_stage = nullptr; size_t ws_stage_bytes = 0;  // host<->device staging
+    int64_t device_bytes = 0;
+    int num_sms = 0;
+};
+
+gyps_status grow(Mesh *m, void **buf, size_t *cap, size_t need);
+gyps_status check_mesh(gyps_mesh_t h, Mesh **out);
+gyps_status enter_device(const Mesh *m);
+bool is_device_pointer(const void *p);
+
+// ---------------------------------------------------------------- launchers
+// a1: quadrature points and the FP32 position panel
+cudaError_t launch_quad_points(const Mesh &m, cudaStream_t s);
+// a5b: correction blocks and their CSR gather
+cudaError_t launch_near_build(const Mesh &m, cudaStream_t s);
+
+// a2-a5: one matrix-free apply with device pointers
+gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
+                         int prec, uint32_t flags, int64_t tri_begin, int64_t tri_end, cudaStream_t s);
+cudaError_t launch_near_spmv(const Mesh &m, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
+                             cudaStream_t s);
+
+// a6, a7
+gyps_status assemble_device(Mesh *m, double k, int prec, double2 *V, int64_t ldv, cudaStream_t s);
+gyps_status rhs_device(Mesh *m, double k, int nrhs, const double *dirs_host, double2 *F, int64_t ldf,
+                       cudaStream_t s);
+
+// a8
+gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t ldf, double2 *X, int64_t ldx,
+                         const gyps_gmres_opts &o, gyps_gmres_report *rep, cudaStream_t s);
+
+}  // namespace gyps

@@ -1,0 +1,214 @@
+"""GPU path (through the C ABI) against the FP64 oracle on identical inputs.
+
+Tolerances (relative, per right-hand-side column, 2-norm):
+  FP64 paths 1e-10; FP32 far kernel 1e-5 (FP32 kernel values and compensated
+  FP32 sums; the near correction stays FP64).
+Sizes span several source tiles of 256 points and a ragged tail.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1804_00995_gb300 as g
+    g.load()
+    return g
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if a.ndim == 1:
+        a, b = a[:, None], b[:, None]
+    return max(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c]) for c in range(a.shape[1]))
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+MESHES = {
+    "ico2_q3": lambda: (*synth.icosphere(2), 3),
+    "ico3_q7": lambda: (*synth.icosphere(3), 7),
+    "ell2_q1": lambda: (*synth.ellipsoid(2, (0.6, 1.3, 1.9), (1.0, 2.0, 0.5), 0.7), 1),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(MESHES))
+def pair(request, g):
+    v, t, q = MESHES[request.param]()
+    return g.Mesh(v, t, q), oracle.Mesh(v, t, q)
+
+
+def test_quadrature_points(pair):
+    gm, om = pair
+    xw = to_np(gm.quad_points())
+    assert np.abs(xw[:, :3] - om.x).max() < 1e-15 * 8
+    assert np.abs(xw[:, 3] - om.w).max() <= 1e-16 * 8 * om.w.max()
+
+
+def test_near_matrix_pattern_and_values(pair):
+    gm, om = pair
+    rowptr, col, val = gm.near_csr()
+    c = om.near.tocsr()
+    c.sort_indices()
+    assert np.array_equal(rowptr, c.indptr.astype(np.int64))
+    assert np.array_equal(col, c.indices.astype(np.int32))
+    assert np.abs(val - c.data).max() <= 1e-12 * np.abs(c.data).max()
+
+
+@pytest.mark.parametrize("k", [0.0, 5.0, 16.0])
+@pytest.mark.parametrize("nrhs", [1, 3, 6])
+def test_apply_fp64(pair, g, k, nrhs):
+    gm, om = pair
+    rng = np.random.default_rng(11 + nrhs)
+    x = synth.random_complex(rng, om.nv, nrhs)
+    y = g.sl_apply(gm, k, torch.as_tensor(x).cuda(), prec="fp64")
+    assert rel(to_np(y), om.apply(k, x)) < 1e-10
+
+
+@pytest.mark.parametrize("k", [0.0, 5.0, 16.0])
+@pytest.mark.parametrize("nrhs", [1, 2, 5, 13])
+def test_apply_fp32(pair, g, k, nrhs):
+    gm, om = pair
+    rng = np.random.default_rng(23 + nrhs)
+    x = synth.random_complex(rng, om.nv, nrhs)
+    y = g.sl_apply(gm, k, torch.as_tensor(x).cuda(), prec="fp32")
+    assert rel(to_np(y), om.apply(k, x)) < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_far_part_only(pair, g, prec):
+    gm, om = pair
+    x = synth.random_complex(np.random.default_rng(5), om.nv, 2)
+    y = g.sl_apply(gm, 7.0, torch.as_tensor(x).cuda(), prec=prec, near=False)
+    assert rel(to_np(y), om.far_apply(7.0, x)) < (1e-10 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_triangle_ranges_add_up(pair, g, prec):
+    """Applies over a partition of the test triangles sum to the full apply."""
+    gm, om = pair
+    x = torch.as_tensor(synth.random_complex(np.random.default_rng(9), om.nv, 3)).cuda()
+    full = to_np(g.sl_apply(gm, 4.0, x, prec=prec))
+    cuts = [0, om.nt // 3, om.nt // 3 + 1, om.nt]
+    parts = sum(to_np(g.sl_apply(gm, 4.0, x, prec=prec, tri_range=(a, b))) for a, b in zip(cuts[:-1], cuts[1:]))
+    assert rel(parts, full) < (1e-12 if prec == "fp64" else 1e-6)
+    empty = to_np(g.sl_apply(gm, 4.0, x, prec=prec, tri_range=(5, 5)))
+    assert np.abs(empty).max() == 0.0
+
+
+def test_near_correct(pair, g):
+    gm, om = pair
+    x = synth.random_complex(np.random.default_rng(3), om.nv, 2)
+    y0 = synth.random_complex(np.random.default_rng(4), om.nv, 2)
+    y = torch.as_tensor(y0).cuda().t().contiguous().t()
+    g.near_correct(gm, torch.as_tensor(x).cuda(), y)
+    assert rel(to_np(y), y0 + om.near @ x) < 1e-13
+
+
+def test_rhs_planewave(pair, g):
+    gm, om = pair
+    dirs = synth.plane_wave_dirs(np.random.default_rng(2), 3)
+    f = g.rhs_planewave(gm, 6.0, dirs)
+    assert rel(to_np(f), om.rhs_planewave(6.0, dirs)) < 1e-13
+
+
+def test_host_buffers_match_device(pair, g):
+    gm, om = pair
+    x = synth.random_complex(np.random.default_rng(8), om.nv, 2)
+    yd = to_np(g.sl_apply(gm, 3.0, torch.as_tensor(x).cuda(), prec="fp32"))
+    yh = g.sl_apply(gm, 3.0, torch.as_tensor(x), prec="fp32").numpy()
+    assert rel(yh, yd) < 1e-12
+
+
+def test_dense_assembly_sphere642(g):
+    """Workload sphere642_k5_q3: dense 642 x 642 FP64 assembly incl. correction."""
+    v, t = synth.icosphere(3)
+    om = oracle.Mesh(v, t, 3)
+    gm = g.Mesh(v, t, 3)
+    for k in (5.0, 0.0):
+        ref = om.assemble(k)
+        got = to_np(g.sl_assemble(gm, k, prec="fp64"))
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+        got32 = to_np(g.sl_assemble(gm, k, prec="fp32"))
+        assert np.linalg.norm(got32 - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_gmres_sphere642_matches_lu(g):
+    """Workload sphere642_k5_q3: FP64 GMRES to 1e-8 against the oracle's LU solve."""
+    v, t = synth.icosphere(3)
+    om = oracle.Mesh(v, t, 3)
+    gm = g.Mesh(v, t, 3)
+    f = g.rhs_planewave(gm, 5.0, [(0.0, 0.0, 1.0)])
+    x, rep = g.gmres_solve(gm, 5.0, f, tol=1e-8, restart=200, prec="fp64", check_prec="fp64")
+    assert rep.status == "OK" and rep.true_residual[0] <= 1e-8
+    ref = oracle.solve_lu(om.assemble(5.0), om.rhs_planewave(5.0, [(0.0, 0.0, 1.0)])[:, 0])
+    assert np.linalg.norm(to_np(x)[:, 0] - ref) / np.linalg.norm(ref) < 1e-7
+    # FP32 operator with FP64 refinement reaches the same tolerance
+    x32, rep32 = g.gmres_solve(gm, 5.0, f, tol=1e-8, restart=200, prec="fp32", check_prec="fp64", max_refine=5)
+    assert rep32.status == "OK" and rep32.true_residual[0] <= 1e-8
+    assert np.linalg.norm(to_np(x32)[:, 0] - ref) / np.linalg.norm(ref) < 1e-7
+
+
+def test_tiny_meshes_and_ragged_tails(g):
+    """One triangle (3 points, one partial source tile) and a tetrahedron."""
+    v = np.array([[0.0, 0.0, 0.0], [0.3, 0.0, 0.1], [0.1, 0.25, 0.0], [0.1, 0.1, 0.3]])
+    for tri in (np.array([[0, 1, 2]], dtype=np.int32), np.array([[0, 2, 1], [0, 1, 3], [1, 2, 3], [2, 0, 3]], dtype=np.int32)):
+        nv = int(tri.max()) + 1
+        for q in (1, 3, 7):
+            om = oracle.Mesh(v[:nv], tri, q)
+            gm = g.Mesh(v[:nv], tri, q)
+            x = synth.random_complex(np.random.default_rng(q), nv, 2)
+            for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5)):
+                y = to_np(g.sl_apply(gm, 2.0, torch.as_tensor(x).cuda(), prec=prec))
+                assert rel(y, om.apply(2.0, x)) < tol
+
+
+def test_invalid_inputs(g):
+    v, t = synth.icosphere(1)
+    bad = t.copy()
+    bad[3, 1] = v.shape[0]
+    with pytest.raises(g.GypsError) as e:
+        g.Mesh(v, bad, 3)
+    assert e.value.status == "INVALID"
+    deg = t.copy()
+    deg[0, 1] = deg[0, 0]
+    with pytest.raises(g.GypsError):
+        g.Mesh(v, deg, 3)
+    gm = g.Mesh(v, t, 3)
+    x = torch.zeros((gm.nv, 1), dtype=torch.complex128, device="cuda")
+    for kbad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(g.GypsError):
+            g.sl_apply(gm, kbad, x)
+    with pytest.raises(g.GypsError):
+        g.sl_apply(gm, 1.0, x, tri_range=(0, gm.nt + 1))
+    with pytest.raises(g.GypsError) as e:
+        g.sl_apply(gm, 1.0, x, prec="tc_bf16x3")
+    assert e.value.status == "UNSUPPORTED"
+
+
+@pytest.mark.slow
+def test_sphere10242_k16_q7_sampled_rows(g):
+    """Workload sphere10242_k16_q7 at full size, launch configuration of the
+    benchmark: FP32 apply vs the oracle on 64 sampled rows; FP64 apply too."""
+    v, t = synth.icosphere(5)
+    om = oracle.Mesh(v, t, 7)
+    gm = g.Mesh(v, t, 7)
+    rng = np.random.default_rng(1804)
+    x = synth.random_complex(rng, om.nv, 1)
+    rows = np.sort(rng.choice(om.nv, 64, replace=False))
+    ref = om.apply(16.0, x, rows=rows)[rows]
+    xd = torch.as_tensor(x).cuda()
+    y32 = to_np(g.sl_apply(gm, 16.0, xd, prec="fp32"))[rows]
+    assert rel(y32, ref) < 1e-5
+    y64 = to_np(g.sl_apply(gm, 16.0, xd, prec="fp64"))[rows]
+    assert rel(y64, ref) < 1e-10
