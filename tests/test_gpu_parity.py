@@ -144,19 +144,26 @@ def test_dense_assembly_sphere642(g):
 
 
 def test_gmres_sphere642_matches_lu(g):
-    """Workload sphere642_k5_q3: FP64 GMRES to 1e-8 against the oracle's LU solve."""
+    """Workload sphere642_k5_q3: FP64 GMRES against the oracle's LU solve.  A
+    residual tol bounds the solution error by cond(V) tol, so the LU comparison
+    runs at tol 1e-12; the 1e-8 solves are judged by their residual against the
+    oracle's dense V and F."""
     v, t = synth.icosphere(3)
     om = oracle.Mesh(v, t, 3)
     gm = g.Mesh(v, t, 3)
-    f = g.rhs_planewave(gm, 5.0, [(0.0, 0.0, 1.0)])
-    x, rep = g.gmres_solve(gm, 5.0, f, tol=1e-8, restart=200, prec="fp64", check_prec="fp64")
-    assert rep.status == "OK" and rep.true_residual[0] <= 1e-8
-    ref = oracle.solve_lu(om.assemble(5.0), om.rhs_planewave(5.0, [(0.0, 0.0, 1.0)])[:, 0])
-    assert np.linalg.norm(to_np(x)[:, 0] - ref) / np.linalg.norm(ref) < 1e-7
-    # FP32 operator with FP64 refinement reaches the same tolerance
-    x32, rep32 = g.gmres_solve(gm, 5.0, f, tol=1e-8, restart=200, prec="fp32", check_prec="fp64", max_refine=5)
-    assert rep32.status == "OK" and rep32.true_residual[0] <= 1e-8
-    assert np.linalg.norm(to_np(x32)[:, 0] - ref) / np.linalg.norm(ref) < 1e-7
+    d = [(0.0, 0.0, 1.0)]
+    a = om.assemble(5.0)
+    fo = om.rhs_planewave(5.0, d)[:, 0]
+    ref = oracle.solve_lu(a, fo)
+    f = g.rhs_planewave(gm, 5.0, d)
+    x, rep = g.gmres_solve(gm, 5.0, f, tol=1e-12, restart=200, prec="fp64", check_prec="fp64")
+    assert rep.status == "OK" and rep.true_residual[0] <= 1e-12
+    assert np.linalg.norm(to_np(x)[:, 0] - ref) / np.linalg.norm(ref) < 1e-9
+    for prec in ("fp64", "fp32"):
+        x8, rep8 = g.gmres_solve(gm, 5.0, f, tol=1e-8, restart=200, prec=prec, check_prec="fp64", max_refine=5)
+        assert rep8.status == "OK" and rep8.true_residual[0] <= 1e-8
+        xo = to_np(x8)[:, 0]
+        assert np.linalg.norm(a @ xo - fo) / np.linalg.norm(fo) < 1.01e-8
 
 
 def test_tiny_meshes_and_ragged_tails(g):
