@@ -1,0 +1,365 @@
+"""Benchmark of the matrix-free Galerkin single-layer apply on GB300.
+
+One step = one gyps_sl_apply of the whole operator (interpolation W_y Phi X,
+the dense kernel product G u, the projection Phi^T W_x v / 4pi and the CSR
+singular correction C X) on the workload sphere10242_k16_q7: icosphere with
+20480 triangles (10242 vertices), 7-point rule (143360 points), k = 16, one
+right-hand side, FP32 kernel products and FP64 correction.
+
+Metric: GPairs/s = Nq^2 (target point, source point) pairs per apply divided
+by the apply's device time.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gyps|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = "sphere10242_k16_q7"
+METRIC = "GPairs/s single-layer apply (%FP32+SFU roof); GMRES time-to-1e-6 vs plain FP64"
+UNIT = "GPairs/s"
+MUFU_PER_PAIR = 3          # rsqrt, sin, cos
+MUFU_PER_CLK_PER_SM = 16   # special-function results per clock per SM
+PROFILE = os.path.join(ROOT, "profiles", "far32_sphere10242_k16_q7.md")
+FAR_SRC = os.path.join(ROOT, "paper_1804_00995_gb300", "csrc", "far.cu")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gyps", choices=["gyps", "reference"])
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--solve", action="store_true", help="also time GMRES to 1e-6 (FP32 + FP64 check)")
+    p.add_argument("--solve-fp64", action="store_true", help="also time the plain FP64 GMRES (minutes)")
+    return p.parse_args()
+
+
+def workload():
+    cfg = synth.WORKLOADS[WORKLOAD]
+    v, t = synth.icosphere(cfg["level"])
+    return v, t, cfg
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gyps_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader", "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                mx.append(float(f[2].split()[0]))
+                pw.append(float(f[3].split()[0]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- roofline
+def far_traffic_per_launch():
+    """DRAM bytes per far-kernel launch from the committed ncu summary, if it
+    was taken on the current far-kernel source (else None)."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    m_sha = re.search(r"far_source_sha256:\s*([0-9a-f]{64})", text)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b:
+        return None
+    sha = hashlib.sha256(open(FAR_SRC, "rb").read()).hexdigest()
+    if sha != m_sha.group(1):
+        return None
+    return float(m_b.group(1))
+
+
+def sm_peak_pairs(num_sms, mhz):
+    return num_sms * MUFU_PER_CLK_PER_SM / MUFU_PER_PAIR * mhz * 1e6
+
+
+# ---------------------------------------------------------------- CPU baseline
+def oracle_sample(v, t, cfg, seconds, seed=1804):
+    """Times the oracle's apply restricted to a sample of output rows: all
+    source points, the target points in the support of the sampled vertices.
+    Returns (pairs/s, cores, description, seconds)."""
+    import oracle
+    om = oracle.Mesh(v, t, cfg["q"])
+    _ = om.near  # correction built outside the timing (k-independent, once per mesh)
+    x = synth.random_complex(np.random.default_rng(seed), om.nv, 1)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(om.nv)
+    n = 8
+    t0 = time.perf_counter()
+    om.apply(cfg["k"], x, rows=np.sort(order[:n]))
+    dt = time.perf_counter() - t0
+    npts = len(om.quad_ids_of_vertices(order[:n]))
+    per_target = dt / max(npts, 1)
+    want = int(max(n, min(om.nv, n * seconds / max(dt, 1e-6))))
+    rows = np.sort(order[:want])
+    tids = om.quad_ids_of_vertices(rows)
+    t0 = time.perf_counter()
+    om.apply(cfg["k"], x, rows=rows)
+    dt = time.perf_counter() - t0
+    pairs = len(tids) * om.nq
+    desc = (f"{want} of {om.nv} output rows ({len(tids)} of {om.nq} target points x all {om.nq} sources, "
+            f"plus their correction rows), {dt:.1f} s")
+    del per_target
+    return pairs / dt, oracle.num_threads(), desc, dt
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    v, t, cfg = workload()
+    import oracle
+    om = oracle.Mesh(v, t, cfg["q"])
+    _ = om.near
+    x = synth.random_complex(np.random.default_rng(0), om.nv, 1)
+    rng = np.random.default_rng(1804)
+    # size one step so that warm-up + timed steps take about two minutes of CPU work
+    per_step = min(2.5, 120.0 / max(args.steps + args.warmup, 1))
+    probe = np.sort(rng.choice(om.nv, 8, replace=False))
+    t0 = time.perf_counter()
+    om.apply(cfg["k"], x, rows=probe)
+    dt = time.perf_counter() - t0
+    nrows = int(max(8, min(om.nv, 8 * per_step / max(dt, 1e-6))))
+    times, pairs = [], []
+    for i in range(args.warmup + args.steps):
+        rows = np.sort(rng.choice(om.nv, nrows, replace=False))
+        ntgt = len(om.quad_ids_of_vertices(rows))
+        t0 = time.perf_counter()
+        om.apply(cfg["k"], x, rows=rows)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            pairs.append(ntgt * om.nq)
+    value = sum(pairs) / sum(times) / 1e9
+    desc = f"each step {nrows} random output rows of {om.nv} (all {om.nq} sources)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mesh": "icosphere level 5", "nv": om.nv, "nq": om.nq, "k": cfg["k"],
+                   "quad_points": cfg["q"], "nrhs": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gyps(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1804_00995_gb300 import build as gb
+    if local_rank == 0:
+        gb.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1804_00995_gb300 as g
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    props = torch.cuda.get_device_properties(dev)
+    v, t, cfg = workload()
+    k = cfg["k"]
+    mesh = g.Mesh(v, t, cfg["q"])
+    nq, nv = mesh.nq, mesh.nv
+    pairs = float(nq) * nq
+    # each rank applies the operator to its own seeded right-hand side (independent problems)
+    x = torch.as_tensor(synth.random_complex(np.random.default_rng(1000 + rank), nv, 1)).to(dev)
+    y = g.sl_apply(mesh, k, x, prec="fp32")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        g.sl_apply(mesh, k, x, prec="fp32", out=y)
+    torch.cuda.synchronize(dev)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    smi_id = str(local_rank)
+    if getattr(props, "uuid", None) is not None:
+        smi_id = "GPU-" + str(props.uuid)
+    clocks = ClockSampler(smi_id)
+    mesh.profile(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        g.sl_apply(mesh, k, x, prec="fp32", out=y)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = mesh.profile_read()
+    mesh.profile(False)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = step_ms
+    if world > 1:
+        tt = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / args.steps
+    value = world * pairs / (ms_per_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (dense G u), from its own events
+    far_ms = prof["far_ms"] / max(prof["far_launches"], 1)
+    achieved = pairs / (far_ms * 1e-3) / 1e9
+    peak_mhz = None
+    try:
+        peak_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
+    except Exception:
+        peak_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak = sm_peak_pairs(props.multi_processor_count, peak_mhz) / 1e9
+    traffic = far_traffic_per_launch()
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    xh = torch.as_tensor(synth.random_complex(np.random.default_rng(2000 + rank), nv, 1)).pin_memory()
+    yh = torch.empty((1, nv), dtype=torch.complex128).pin_memory().t()
+    g.sl_apply(mesh, k, xh, prec="fp32", out=yh)
+    e2e_t = []
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g.sl_apply(mesh, k, xh, prec="fp32", out=yh)  # returns once Y is back on the host
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_mean = sum(e2e_t) / len(e2e_t)
+    if world > 1:
+        tt = torch.tensor([e2e_mean], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_mean = float(tt.item())
+    e2e_value = world * pairs / e2e_mean / 1e9
+
+    solve = None
+    if args.solve or args.solve_fp64:
+        f = g.rhs_planewave(mesh, k, [cfg["dirs"][0]])
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        xs, rep = g.gmres_solve(mesh, k, f, tol=cfg["tol"], restart=200, maxit=2000, prec="fp32",
+                                check_prec="fp64", max_refine=4)
+        torch.cuda.synchronize(dev)
+        solve = {"tol": cfg["tol"], "fp32_refined_s": time.perf_counter() - t0, "iterations": rep.iterations,
+                 "refinements": rep.refinements, "true_residual": float(rep.true_residual[0]), "status": rep.status}
+        if args.solve_fp64:
+            t0 = time.perf_counter()
+            _, rep64 = g.gmres_solve(mesh, k, f, tol=cfg["tol"], restart=200, maxit=2000, prec="fp64",
+                                     check_prec="fp64", max_refine=0)
+            torch.cuda.synchronize(dev)
+            solve.update({"fp64_s": time.perf_counter() - t0, "fp64_iterations": rep64.iterations,
+                          "fp64_true_residual": float(rep64.true_residual[0]), "fp64_status": rep64.status})
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pv, cores, desc, _ = oracle_sample(v, t, cfg, args.cpu_seconds)
+        cpu = {"value": pv / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mesh": "icosphere level 5 (20480 triangles)", "nv": nv, "nq": nq,
+                       "k": k, "quad_points": cfg["q"], "nrhs": 1, "far": "fp32", "near": "fp64",
+                       "l2": "flushed (512 MB write) before every step", "pairs_per_step": pairs,
+                       "ranks": "independent replicas, one right-hand side each"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
+                         "traffic": traffic, "kernel": "far32_kernel<1,4>",
+                         "peak_basis": f"{props.multi_processor_count} SMs x {MUFU_PER_CLK_PER_SM}/{MUFU_PER_PAIR} "
+                                       f"pairs/clk x {peak_mhz:.0f} MHz (measured sm_max_mhz)",
+                         "far_ms_per_launch": far_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nv * 16, "d2h_bytes_per_step": nv * 16},
+            "gpu_launches": int(prof["launches"]),
+            "clocks": clk,
+            "wall_s_timed_region": wall,
+        }
+        if solve is not None:
+            line["solve"] = solve
+        print(json.dumps(line), flush=True)
+    mesh.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    run_gyps(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

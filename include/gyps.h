@@ -205,6 +205,30 @@ gyps_status gyps_gmres_solve(gyps_mesh_t mesh, double k, int nrhs, const void *F
                              void *X, int64_t ldx, const gyps_gmres_opts *opts,
                              gyps_gmres_report *report, void *stream);
 
+/* Device-time profile of the matrix-free applies of one mesh. */
+typedef struct {
+    int64_t applies;      /* gyps_sl_apply calls recorded since profiling was enabled */
+    int64_t launches;     /* kernels those applies launched */
+    double interp_ms;     /* summed device time of the W_y Phi X step */
+    double far_ms;        /* ... of the dense G u step (Eq. BEM) */
+    double project_ms;    /* ... of Phi^T W_x v (+ the CSR correction C X) */
+    double near_ms;       /* ... of the correction over a partial triangle range */
+    int64_t far_launches; /* launches of the dense G u kernel */
+} gyps_profile_t;
+
+/*
+ * Turns per-stage timing of gyps_sl_apply on (enable = 1) or off (0) for one
+ * mesh; enabling resets the totals.  While on, each apply records CUDA events
+ * before and after every stage on the stream it runs on.
+ */
+gyps_status gyps_profile_enable(gyps_mesh_t mesh, int enable);
+
+/*
+ * Waits for the recorded events, adds their durations to the totals and
+ * copies the totals into out (HOST).
+ */
+gyps_status gyps_profile_read(gyps_mesh_t mesh, gyps_profile_t *out);
+
 #ifdef __cplusplus
 }
 #endif

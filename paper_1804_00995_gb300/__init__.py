@@ -46,6 +46,12 @@ class _MeshInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class _Profile(ctypes.Structure):
+    _fields_ = [("applies", ctypes.c_int64), ("launches", ctypes.c_int64), ("interp_ms", ctypes.c_double),
+                ("far_ms", ctypes.c_double), ("project_ms", ctypes.c_double), ("near_ms", ctypes.c_double),
+                ("far_launches", ctypes.c_int64)]
+
+
 class _GmresOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("check_prec", ctypes.c_int32), ("use_x0", ctypes.c_int32),
@@ -82,6 +88,8 @@ _SIGS = {
     "gyps_gmres_solve": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                           ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(_GmresOpts),
                           ctypes.POINTER(_GmresReport), ctypes.c_void_p], ctypes.c_int),
+    "gyps_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "gyps_profile_read": ([ctypes.c_void_p, ctypes.POINTER(_Profile)], ctypes.c_int),
 }
 
 
@@ -209,6 +217,16 @@ class Mesh:
         out = torch.empty((self.nq, 4), dtype=torch.float64, device=self.device)
         _check(load().gyps_quad_points(self.handle, out.data_ptr(), _stream(stream)))
         return out
+
+    def profile(self, enable: bool = True):
+        """Turns per-stage device timing of sl_apply on or off (resets totals)."""
+        _check(load().gyps_profile_enable(self.handle, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """Totals since profiling was enabled: applies, launches, per-stage ms."""
+        p = _Profile()
+        _check(load().gyps_profile_read(self.handle, ctypes.byref(p)))
+        return {f: getattr(p, f) for f, _ in _Profile._fields_}
 
     def near_csr(self):
         """Correction matrix C (CSR: rowptr int64, col int32, val float64), host numpy."""

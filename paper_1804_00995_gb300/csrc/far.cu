@@ -516,9 +516,11 @@ static gyps_status run_far32(Mesh *m, double k, const double2 *X, int64_t ldx, i
 {
     using C = FarCfg<R, T>;
     float *panel = reinterpret_cast<float *>(m->ws_den);
+    StageTimer ti(m, s, 0);
     interp32_kernel<R><<<(unsigned)((m->nq_pad + 255) / 256), 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq,
                                                                            m->nq_pad, X, ldx, c0, panel);
     GYPS_CUDA(cudaGetLastError());
+    ti.done(1);
     GYPS_CUDA(cudaFuncSetAttribute(far32_kernel<R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     int occ = 0;
     GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, far32_kernel<R, T>, C::NT, C::SMEM));
@@ -538,8 +540,10 @@ static gyps_status run_far32(Mesh *m, double k, const double2 *X, int64_t ldx, i
     a.err = m->d_err;
     int64_t items = a.n_tgt_tiles * a.n_src_tiles;
     int64_t grid = std::min<int64_t>((int64_t)m->num_sms * occ, items);
+    StageTimer tf(m, s, 1);
     far32_kernel<R, T><<<(unsigned)grid, C::NT, C::SMEM, s>>>(a);
     GYPS_CUDA(cudaGetLastError());
+    tf.done(1);
     return GYPS_OK;
 }
 
@@ -548,8 +552,10 @@ static gyps_status run_far64(Mesh *m, double k, const double2 *u64, int64_t ldu,
                              int64_t t_begin, int64_t t_end, cudaStream_t s)
 {
     unsigned grid = (unsigned)((t_end - t_begin + 127) / 128);
+    StageTimer tf(m, s, 1);
     far64_kernel<R><<<grid, 128, 0, s>>>(m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, v, ldv);
     GYPS_CUDA(cudaGetLastError());
+    tf.done(1);
     return GYPS_OK;
 }
 
@@ -569,6 +575,7 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
     // v: nq x nrhs FP64 accumulators (zeroed: the FP32 kernel adds into it,
     // and targets outside a partial range must read as zero)
     const int64_t ldv = m->nq;
+    if (m->prof) ++m->prof_applies;
     GYPS_TRY(grow(m, &m->ws_v, &m->ws_v_bytes, (size_t)(ldv * nrhs) * sizeof(double2)));
     double2 *v = reinterpret_cast<double2 *>(m->ws_v);
     GYPS_CUDA(cudaMemsetAsync(v, 0, (size_t)(ldv * nrhs) * sizeof(double2), s));
@@ -593,8 +600,10 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
             GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(ldu * nrhs) * sizeof(double2)));
             double2 *u64 = reinterpret_cast<double2 *>(m->ws_den);
             dim3 g((unsigned)((m->nq + 255) / 256), (unsigned)nrhs);
+            StageTimer ti(m, s, 0);
             interp64_kernel<<<g, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, ldu, X, ldx, nrhs, u64);
             GYPS_CUDA(cudaGetLastError());
+            ti.done(1);
             for (int c0 = 0; c0 < nrhs;) {
                 int w = chunk_width(nrhs - c0);
                 gyps_status st;
@@ -611,16 +620,20 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
     }
     const bool near = !(flags & GYPS_APPLY_NO_NEAR);
     dim3 g((unsigned)((m->nv + 127) / 128), (unsigned)nrhs);
+    StageTimer tp(m, s, 2);
     project_kernel<<<g, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_pts64, m->rule, m->nv, v, ldv, m->d_c_rowptr,
                                      m->d_c_col, m->d_c_val, X, ldx, Y, ldy, (near && full) ? 1 : 0);
     GYPS_CUDA(cudaGetLastError());
+    tp.done(1);
     if (near && !full) {
         const int32_t pp[2] = {m->h_pair_ptr[tri_begin], m->h_pair_ptr[tri_end]};
         if (pp[1] > pp[0]) {
             dim3 gp((unsigned)((pp[1] - pp[0] + 127) / 128), (unsigned)nrhs);
+            StageTimer tn(m, s, 3);
             near_partial_kernel<<<gp, 128, 0, s>>>(m->d_pair_a, m->d_pair_b, m->d_blocks, m->d_tri, pp[0], pp[1], X, ldx,
                                                    Y, ldy);
             GYPS_CUDA(cudaGetLastError());
+            tn.done(1);
         }
     }
     return GYPS_OK;
@@ -744,5 +757,49 @@ extern "C" gyps_status gyps_near_correct(gyps_mesh_t h, int nrhs, const void *X,
     GYPS_CUDA(launch_near_spmv(*m, nrhs, xin, lxin, yio, lyio, s));
     if (!dy) GYPS_TRY(stage_out(m, ys, Y, ldy, nrhs, s));
     GYPS_CUDA(cudaStreamSynchronize(s));
+    return GYPS_OK;
+}
+
+extern "C" gyps_status gyps_profile_enable(gyps_mesh_t h, int enable)
+{
+    Mesh *m;
+    GYPS_TRY(check_mesh(h, &m));
+    for (auto &r : m->prof_pending) {
+        cudaEventSynchronize(r.b);
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    m->prof_pending.clear();
+    m->prof = enable != 0;
+    for (int i = 0; i < 4; ++i) {
+        m->prof_ms[i] = 0.0;
+        m->prof_launches[i] = 0;
+    }
+    m->prof_applies = 0;
+    return GYPS_OK;
+}
+
+extern "C" gyps_status gyps_profile_read(gyps_mesh_t h, gyps_profile_t *out)
+{
+    Mesh *m;
+    GYPS_TRY(check_mesh(h, &m));
+    if (!out) return set_error(GYPS_ERR_INVALID, "out is NULL");
+    for (auto &r : m->prof_pending) {
+        GYPS_CUDA(cudaEventSynchronize(r.b));
+        float ms = 0.0f;
+        GYPS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        m->prof_ms[r.stage] += ms;
+        m->prof_launches[r.stage] += r.launches;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    m->prof_pending.clear();
+    out->applies = m->prof_applies;
+    out->launches = m->prof_launches[0] + m->prof_launches[1] + m->prof_launches[2] + m->prof_launches[3];
+    out->interp_ms = m->prof_ms[0];
+    out->far_ms = m->prof_ms[1];
+    out->project_ms = m->prof_ms[2];
+    out->near_ms = m->prof_ms[3];
+    out->far_launches = m->prof_launches[1];
     return GYPS_OK;
 }

@@ -91,6 +91,39 @@ struct Mesh {
     void *ws_stage = nullptr; size_t ws_stage_bytes = 0;  // host<->device staging
     int64_t device_bytes = 0;
     int num_sms = 0;
+
+    // optional per-stage device timing of applies (gyps_profile_*)
+    struct ProfRec {
+        cudaEvent_t a, b;
+        int stage;
+        int launches;
+    };
+    bool prof = false;
+    std::vector<ProfRec> prof_pending;
+    double prof_ms[4] = {0, 0, 0, 0};
+    int64_t prof_launches[4] = {0, 0, 0, 0};
+    int64_t prof_applies = 0;
+};
+
+// Records CUDA events around one stage of an apply when profiling is on.
+struct StageTimer {
+    Mesh *m;
+    cudaStream_t s;
+    int stage;
+    cudaEvent_t a = nullptr;
+    StageTimer(Mesh *m_, cudaStream_t s_, int stage_) : m(m_), s(s_), stage(stage_)
+    {
+        if (m->prof && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+    }
+    void done(int launches)
+    {
+        if (!a) return;
+        cudaEvent_t b;
+        if (cudaEventCreate(&b) != cudaSuccess) return;
+        cudaEventRecord(b, s);
+        m->prof_pending.push_back({a, b, stage, launches});
+        a = nullptr;
+    }
 };
 
 gyps_status grow(Mesh *m, void **buf, size_t *cap, size_t need);
