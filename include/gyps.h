@@ -205,6 +205,31 @@ gyps_status gyps_gmres_solve(gyps_mesh_t mesh, double k, int nrhs, const void *F
                              void *X, int64_t ldx, const gyps_gmres_opts *opts,
                              gyps_gmres_report *report, void *stream);
 
+/*
+ * gyps_sl_apply without any device allocation (the paper has no counterpart:
+ * this is a library service).  For callers that must not allocate device
+ * memory while they run - their device memory is owned by another allocator,
+ * or a cudaMalloc, and the device-wide synchronisation it can cause, is not
+ * acceptable inside their loop.  Computes the same
+ *     Y = (1/4pi) Phi^T W_x G W_y Phi X + C X
+ * as gyps_sl_apply with prec = GYPS_PREC_FP32, all triangles, correction on.
+ *   X, Y  DEVICE, nv x nrhs complex double2 (leading dimensions ldx, ldy >= nv),
+ *         not overlapping; host pointers are rejected (INVALID).
+ * Scratch: a fixed 8 MiB device array inside the library, held on every GPU
+ * that loads it until the process exits; one column needs about 28 bytes per
+ * quadrature point (meshes with nq up to about 290000).  A larger mesh is
+ * rejected with INVALID and a message giving the bytes needed.  Nothing is
+ * allocated: the call launches kernels and clears the accumulators it needs
+ * (cudaMemsetAsync) on `stream`, then returns.
+ * The first call on each device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array and it
+ * keeps the previous call's contents: calls whose work overlaps on the GPU
+ * (other streams, other threads) race and corrupt each other's results;
+ * order them on one stream.
+ */
+gyps_status gyps_sl_apply_noalloc(gyps_mesh_t mesh, double k, int nrhs, const void *X, int64_t ldx,
+                                  void *Y, int64_t ldy, void *stream);
+
 /* Device-time profile of the matrix-free applies of one mesh. */
 typedef struct {
     int64_t applies;      /* gyps_sl_apply calls recorded since profiling was enabled */

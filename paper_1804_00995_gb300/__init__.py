@@ -88,6 +88,8 @@ _SIGS = {
     "gyps_gmres_solve": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                           ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(_GmresOpts),
                           ctypes.POINTER(_GmresReport), ctypes.c_void_p], ctypes.c_int),
+    "gyps_sl_apply_noalloc": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                               ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "gyps_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "gyps_profile_read": ([ctypes.c_void_p, ctypes.POINTER(_Profile)], ctypes.c_int),
 }

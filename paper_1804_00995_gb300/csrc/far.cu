@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
 
 #include "internal.h"
 
@@ -801,5 +803,109 @@ extern "C" gyps_status gyps_profile_read(gyps_mesh_t h, gyps_profile_t *out)
     out->project_ms = m->prof_ms[2];
     out->near_ms = m->prof_ms[3];
     out->far_launches = m->prof_launches[1];
+    return GYPS_OK;
+}
+
+// ---------------------------------------------------------------- no-allocation apply
+// gyps_sl_apply_noalloc: the same FP32 apply as gyps_sl_apply, for callers that
+// must not allocate device memory while they run (their device memory is owned
+// by another allocator, or a cudaMalloc and the device-wide synchronisation it
+// can cause is not acceptable inside their loop).  Its scratch (the FP32
+// density panel of one column and the FP64 accumulators of the target points)
+// lives in the fixed array below instead of mesh workspace: every GPU that
+// loads the library holds these bytes until the process exits.
+namespace gyps {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch per device, looked up once per device
+// with that device current (the host-side name is only a stand-in).
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[64] = {nullptr};
+
+static gyps_status noalloc_scratch(int device, void **out)
+{
+    if (device < 0 || device >= 64) return set_error(GYPS_ERR_UNSUPPORTED, "device index above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return GYPS_OK;
+}
+
+// Bytes of scratch one column needs: FP32 panel of all source tiles plus the
+// 256-byte aligned FP64 accumulator block.
+static size_t noalloc_need(const Mesh *m, size_t *v_off)
+{
+    size_t panel = (size_t)m->n_src_tiles * (size_t)den_tile_floats(1) * sizeof(float);
+    *v_off = (panel + 255) & ~(size_t)255;
+    return *v_off + (size_t)m->nq * sizeof(double2);
+}
+
+}  // namespace gyps
+
+extern "C" gyps_status gyps_sl_apply_noalloc(gyps_mesh_t h, double k, int nrhs, const void *X, int64_t ldx, void *Y,
+                                             int64_t ldy, void *stream)
+{
+    Mesh *m;
+    GYPS_TRY(check_mesh(h, &m));
+    GYPS_TRY(check_block(m, nrhs, X, ldx, "X"));
+    GYPS_TRY(check_block(m, nrhs, Y, ldy, "Y"));
+    if (!std::isfinite(k) || k < 0.0) return set_error(GYPS_ERR_INVALID, "k must be finite and >= 0");
+    if (!is_device_pointer(X) || !is_device_pointer(Y))
+        return set_error(GYPS_ERR_INVALID, "X and Y must be device pointers (host buffers would need staging memory)");
+    if ((const char *)X < (const char *)Y + ldy * nrhs * 16 && (const char *)Y < (const char *)X + ldx * nrhs * 16)
+        return set_error(GYPS_ERR_INVALID, "X and Y overlap");
+    size_t v_off = 0;
+    const size_t need = noalloc_need(m, &v_off);
+    if (need > kNoAllocScratchBytes)
+        return set_error(GYPS_ERR_INVALID, "mesh needs " + std::to_string(need) + " scratch bytes; the fixed array holds " +
+                                               std::to_string(kNoAllocScratchBytes) + " (about 28 bytes per quadrature point)");
+    void *base = nullptr;
+    GYPS_TRY(noalloc_scratch(m->device, &base));
+    float *panel = reinterpret_cast<float *>(base);
+    double2 *v = reinterpret_cast<double2 *>(reinterpret_cast<unsigned char *>(base) + v_off);
+    cudaStream_t s = (cudaStream_t)stream;
+    using C = FarCfg<1, 4>;
+    GYPS_CUDA(cudaFuncSetAttribute(far32_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    int occ = 0;
+    GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, far32_kernel<1, 4>, C::NT, C::SMEM));
+    occ = std::max(occ, 1);
+    const double2 *Xd = (const double2 *)X;
+    double2 *Yd = (double2 *)Y;
+    for (int j = 0; j < nrhs; ++j) {
+        // the accumulators must start at zero: the previous call (or column) left its sums there
+        GYPS_CUDA(cudaMemsetAsync(v, 0, (size_t)m->nq * sizeof(double2), s));
+        interp32_kernel<1><<<(unsigned)((m->nq_pad + 255) / 256), 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq,
+                                                                               m->nq_pad, Xd, ldx, j, panel);
+        GYPS_CUDA(cudaGetLastError());
+        FarArgs a;
+        a.pos_panel = m->d_pos_panel;
+        a.den_panel = panel;
+        a.tgt = m->d_pts32;
+        a.v = v;
+        a.ldv = m->nq;
+        a.t_begin = 0;
+        a.t_end = m->nq;
+        a.n_src_tiles = m->n_src_tiles;
+        a.n_tgt_tiles = (m->nq + C::TT - 1) / C::TT;
+        a.kk = (float)(k / kTwoPi);
+        a.k = (float)k;
+        a.err = m->d_err;
+        const int64_t items = a.n_tgt_tiles * a.n_src_tiles;
+        const int64_t grid = std::min<int64_t>((int64_t)m->num_sms * occ, items);
+        far32_kernel<1, 4><<<(unsigned)grid, C::NT, C::SMEM, s>>>(a);
+        GYPS_CUDA(cudaGetLastError());
+        dim3 g((unsigned)((m->nv + 127) / 128), 1u);
+        project_kernel<<<g, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_pts64, m->rule, m->nv, v, m->nq, m->d_c_rowptr,
+                                         m->d_c_col, m->d_c_val, Xd + (int64_t)j * ldx, ldx, Yd + (int64_t)j * ldy,
+                                         ldy, 1);
+        GYPS_CUDA(cudaGetLastError());
+    }
     return GYPS_OK;
 }
