@@ -118,10 +118,18 @@ def far_traffic_per_launch():
     m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_b:
         return None
-    sha = hashlib.sha256(open(FAR_SRC, "rb").read()).hexdigest()
+    sha = far_kernel_sha()
     if sha != m_sha.group(1):
         return None
     return float(m_b.group(1))
+
+
+def far_kernel_sha():
+    """sha256 of the FP32 far-kernel section of far.cu (the code the counters describe)."""
+    src = open(FAR_SRC).read()
+    a = src.index("// ---------------------------------------------------------------- a3: far, FP32")
+    b = src.index("// ---------------------------------------------------------------- a3: far, FP64")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()
 
 
 def sm_peak_pairs(num_sms, mhz):
@@ -325,7 +333,7 @@ def run_gyps(args, rank, world, local_rank):
                        "l2": "flushed (512 MB write) before every step", "pairs_per_step": pairs,
                        "ranks": "independent replicas, one right-hand side each"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-                         "traffic": traffic, "kernel": "far32_kernel<1,4>",
+                         "traffic": traffic, "kernel": "far32_kernel<1,4,false>",
                          "peak_basis": f"{props.multi_processor_count} SMs x {MUFU_PER_CLK_PER_SM}/{MUFU_PER_PAIR} "
                                        f"pairs/clk x {peak_mhz:.0f} MHz (measured sm_max_mhz)",
                          "far_ms_per_launch": far_ms},

@@ -154,11 +154,14 @@ __global__ void interp64_kernel(const int32_t *tri, const double4_32a *pts64, co
 // flushes its target accumulators with FP64 atomics whenever the target tile
 // changes.  Source tiles (positions + densities) are staged by 1-D bulk copies
 // into a 3-stage shared-memory ring guarded by mbarriers.  Every thread owns T
-// targets and processes source points in pairs with packed f32x2 arithmetic;
-// rsqrt, sin and cos run on the MUFU unit after reducing the phase k r to
-// [-pi, pi] in turns.  Per-tile FP32 partial sums are folded into a TwoSum
-// (hi, lo) pair so that the rounding error does not grow with the number of
-// source tiles.
+// targets and processes source points in pairs with packed f32x2 arithmetic.
+// Coordinates are scaled by k, so that rs = 1/(k r) and the phase k r = r2 * rs
+// cost one multiply; the phase is reduced to [-pi, pi] by subtracting the
+// nearest multiple of 2 pi (one FFMA), then rsqrt, sin and cos run on the MUFU
+// unit; the sums carry exp(ikr)/(kr) and are multiplied by k at the flush.
+// k = 0 (Laplace) takes a path with rsqrt only.  Per-tile FP32 partial sums are
+// folded into a TwoSum (hi, lo) pair so that the rounding error does not grow
+// with the number of source tiles.
 struct FarArgs {
     const float *pos_panel;
     const float *den_panel;
@@ -167,8 +170,7 @@ struct FarArgs {
     int64_t ldv;
     int64_t t_begin, t_end;
     int64_t n_src_tiles, n_tgt_tiles;
-    float kk;  // k / (2 pi): phase in turns per unit distance
-    float k;
+    float ks;  // coordinate scale: k (1 for the Laplace kernel)
     int *err;
 };
 
@@ -183,56 +185,72 @@ struct FarCfg {
     static constexpr int SMEM = STAGES * STAGE_BYTES + 64;
 };
 
-template <int R, int T, bool CHECK>
+template <int R, int T, bool LAP, bool CHECK>
 __device__ __forceinline__ void far_tile(const float *sp, const float2 (&tx)[T], const float2 (&ty)[T],
-                                         const float2 (&tz)[T], const int64_t (&tid)[T], int64_t src0, float kk, float k,
+                                         const float2 (&tz)[T], const int64_t (&tid)[T], int64_t src0, float ks,
                                          float2 (&are)[T][R], float2 (&aim)[T][R])
 {
     const float4 *XY = reinterpret_cast<const float4 *>(sp);
     const float2 *Z = reinterpret_cast<const float2 *>(sp + 4 * kSrcPairs);
     const float4 *U = reinterpret_cast<const float4 *>(sp + 6 * kSrcPairs);
     const float2 *N = reinterpret_cast<const float2 *>(sp + 6 * kSrcPairs + 4 * kSrcPairs * R);
-    const float2 kk2 = make_float2(kk, kk);
+    const float2 ks2 = make_float2(ks, ks);
     const float2 magic = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23: round to integer
     const float2 nmagic = make_float2(-12582912.0f, -12582912.0f);
-    const float2 neg1 = make_float2(-1.0f, -1.0f);
-    const float2 twopi = make_float2(6.28318530717958647692f, 6.28318530717958647692f);
+    const float2 inv2pi = make_float2(0.159154943091895335769f, 0.159154943091895335769f);
+    const float2 m2pi = make_float2(-6.28318530717958647692f, -6.28318530717958647692f);
 #pragma unroll 2
     for (int p = 0; p < kSrcPairs; ++p) {
         const float4 xy = XY[p];
-        const float2 z = Z[p];
-        const float2 sx = make_float2(xy.x, xy.y), sy = make_float2(xy.z, xy.w);
+        float2 sx = make_float2(xy.x, xy.y), sy = make_float2(xy.z, xy.w), sz = Z[p];
+        if (!LAP) {
+            sx = __fmul2_rn(sx, ks2);
+            sy = __fmul2_rn(sy, ks2);
+            sz = __fmul2_rn(sz, ks2);
+        }
         float2 ure[R], uim[R], unim[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             float4 u = U[p * R + j];
             ure[j] = make_float2(u.x, u.y);
             uim[j] = make_float2(u.z, u.w);
-            unim[j] = N[p * R + j];
+            if (!LAP) unim[j] = N[p * R + j];
         }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             float2 dx = __fadd2_rn(tx[t], sx);
             float2 dy = __fadd2_rn(ty[t], sy);
-            float2 dz = __fadd2_rn(tz[t], z);
+            float2 dz = __fadd2_rn(tz[t], sz);
             float2 r2 = __fmul2_rn(dx, dx);
             r2 = __ffma2_rn(dy, dy, r2);
             r2 = __ffma2_rn(dz, dz, r2);
             float2 rs = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-            float2 ph = __fmul2_rn(__fmul2_rn(r2, rs), kk2);        // k r / (2 pi)
-            float2 nr = __fadd2_rn(__fadd2_rn(ph, magic), nmagic);  // nearest integer
-            float2 ang = __fmul2_rn(__ffma2_rn(nr, neg1, ph), twopi);  // in [-pi, pi]
+            if (LAP) {
+                if (CHECK) {
+                    if (src0 + 2 * p == tid[t]) rs.x = 0.0f;
+                    if (src0 + 2 * p + 1 == tid[t]) rs.y = 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    are[t][j] = __ffma2_rn(rs, ure[j], are[t][j]);
+                    aim[t][j] = __ffma2_rn(rs, uim[j], aim[t][j]);
+                }
+                continue;
+            }
+            float2 ph = __fmul2_rn(r2, rs);                            // k r
+            float2 nr = __fadd2_rn(__ffma2_rn(ph, inv2pi, magic), nmagic);  // nearest integer to k r / (2 pi)
+            float2 ang = __ffma2_rn(nr, m2pi, ph);                     // in [-pi, pi]
             float2 sn = make_float2(sin_mufu(ang.x), sin_mufu(ang.y));
             float2 cs = make_float2(cos_mufu(ang.x), cos_mufu(ang.y));
-            float2 gre = __fmul2_rn(cs, rs), gim = __fmul2_rn(sn, rs);
-            if (CHECK) {
+            float2 gre = __fmul2_rn(cs, rs), gim = __fmul2_rn(sn, rs);  // exp(ikr) / (k r)
+            if (CHECK) {  // the point paired with itself: ik / k = i
                 if (src0 + 2 * p == tid[t]) {
                     gre.x = 0.0f;
-                    gim.x = k;
+                    gim.x = 1.0f;
                 }
                 if (src0 + 2 * p + 1 == tid[t]) {
                     gre.y = 0.0f;
-                    gim.y = k;
+                    gim.y = 1.0f;
                 }
             }
 #pragma unroll
@@ -246,7 +264,7 @@ __device__ __forceinline__ void far_tile(const float *sp, const float2 (&tx)[T],
     }
 }
 
-template <int R, int T>
+template <int R, int T, bool LAP>
 __global__ void __launch_bounds__(FarCfg<R, T>::NT) far32_kernel(const FarArgs a)
 {
     using C = FarCfg<R, T>;
@@ -291,8 +309,8 @@ __global__ void __launch_bounds__(FarCfg<R, T>::NT) far32_kernel(const FarArgs a
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
                     double *dst = reinterpret_cast<double *>(a.v + tid[t] + j * a.ldv);
-                    atomicAdd(dst, (double)hre[t][j] + (double)lre[t][j]);
-                    atomicAdd(dst + 1, (double)him[t][j] + (double)lim[t][j]);
+                    atomicAdd(dst, ((double)hre[t][j] + (double)lre[t][j]) * a.ks);
+                    atomicAdd(dst + 1, ((double)him[t][j] + (double)lim[t][j]) * a.ks);
                 }
             }
         }
@@ -315,6 +333,11 @@ __global__ void __launch_bounds__(FarCfg<R, T>::NT) far32_kernel(const FarArgs a
                 int64_t g = tb + tid_x + t * C::NT;
                 tid[t] = g;
                 float4 p = a.tgt[min(g, a.t_end - 1)];
+                if (!LAP) {
+                    p.x *= a.ks;
+                    p.y *= a.ks;
+                    p.z *= a.ks;
+                }
                 tx[t] = make_float2(p.x, p.x);
                 ty[t] = make_float2(p.y, p.y);
                 tz[t] = make_float2(p.z, p.z);
@@ -335,9 +358,9 @@ __global__ void __launch_bounds__(FarCfg<R, T>::NT) far32_kernel(const FarArgs a
             const float *sp = reinterpret_cast<const float *>(smem + s * C::STAGE_BYTES);
             const int64_t src0 = st * kSrcTile;
             if (tb < src0 + kSrcTile && src0 < te)
-                far_tile<R, T, true>(sp, tx, ty, tz, tid, src0, a.kk, a.k, are, aim);
+                far_tile<R, T, LAP, true>(sp, tx, ty, tz, tid, src0, a.ks, are, aim);
             else
-                far_tile<R, T, false>(sp, tx, ty, tz, tid, src0, a.kk, a.k, are, aim);
+                far_tile<R, T, LAP, false>(sp, tx, ty, tz, tid, src0, a.ks, are, aim);
 #pragma unroll
             for (int t = 0; t < T; ++t)
 #pragma unroll
@@ -512,6 +535,39 @@ cudaError_t launch_near_spmv(const Mesh &m, int nrhs, const double2 *X, int64_t 
 }
 
 // ---------------------------------------------------------------- drivers
+template <int R, int T, bool LAP>
+static gyps_status launch_far32(Mesh *m, const FarArgs &a, cudaStream_t s)
+{
+    using C = FarCfg<R, T>;
+    GYPS_CUDA(cudaFuncSetAttribute(far32_kernel<R, T, LAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    int occ = 0;
+    GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, far32_kernel<R, T, LAP>, C::NT, C::SMEM));
+    occ = std::max(occ, 1);
+    const int64_t items = a.n_tgt_tiles * a.n_src_tiles;
+    const int64_t grid = std::min<int64_t>((int64_t)m->num_sms * occ, items);
+    far32_kernel<R, T, LAP><<<(unsigned)grid, C::NT, C::SMEM, s>>>(a);
+    GYPS_CUDA(cudaGetLastError());
+    return GYPS_OK;
+}
+
+static FarArgs far_args(const Mesh *m, const float *panel, double2 *v, int64_t ldv, int64_t t_begin, int64_t t_end,
+                        int tt_size, double k)
+{
+    FarArgs a;
+    a.pos_panel = m->d_pos_panel;
+    a.den_panel = panel;
+    a.tgt = m->d_pts32;
+    a.v = v;
+    a.ldv = ldv;
+    a.t_begin = t_begin;
+    a.t_end = t_end;
+    a.n_src_tiles = m->n_src_tiles;
+    a.n_tgt_tiles = (t_end - t_begin + tt_size - 1) / tt_size;
+    a.ks = k > 0.0 ? (float)k : 1.0f;
+    a.err = m->d_err;
+    return a;
+}
+
 template <int R, int T>
 static gyps_status run_far32(Mesh *m, double k, const double2 *X, int64_t ldx, int c0, double2 *v, int64_t ldv,
                              int64_t t_begin, int64_t t_end, cudaStream_t s)
@@ -523,28 +579,12 @@ static gyps_status run_far32(Mesh *m, double k, const double2 *X, int64_t ldx, i
                                                                            m->nq_pad, X, ldx, c0, panel);
     GYPS_CUDA(cudaGetLastError());
     ti.done(1);
-    GYPS_CUDA(cudaFuncSetAttribute(far32_kernel<R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    int occ = 0;
-    GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, far32_kernel<R, T>, C::NT, C::SMEM));
-    occ = std::max(occ, 1);
-    FarArgs a;
-    a.pos_panel = m->d_pos_panel;
-    a.den_panel = panel;
-    a.tgt = m->d_pts32;
-    a.v = v + (int64_t)c0 * ldv;
-    a.ldv = ldv;
-    a.t_begin = t_begin;
-    a.t_end = t_end;
-    a.n_src_tiles = m->n_src_tiles;
-    a.n_tgt_tiles = (t_end - t_begin + C::TT - 1) / C::TT;
-    a.kk = (float)(k / kTwoPi);
-    a.k = (float)k;
-    a.err = m->d_err;
-    int64_t items = a.n_tgt_tiles * a.n_src_tiles;
-    int64_t grid = std::min<int64_t>((int64_t)m->num_sms * occ, items);
+    FarArgs a = far_args(m, panel, v + (int64_t)c0 * ldv, ldv, t_begin, t_end, C::TT, k);
     StageTimer tf(m, s, 1);
-    far32_kernel<R, T><<<(unsigned)grid, C::NT, C::SMEM, s>>>(a);
-    GYPS_CUDA(cudaGetLastError());
+    if (k > 0.0)
+        GYPS_TRY((launch_far32<R, T, false>(m, a, s)));
+    else
+        GYPS_TRY((launch_far32<R, T, true>(m, a, s)));
     tf.done(1);
     return GYPS_OK;
 }
@@ -872,10 +912,6 @@ extern "C" gyps_status gyps_sl_apply_noalloc(gyps_mesh_t h, double k, int nrhs, 
     double2 *v = reinterpret_cast<double2 *>(reinterpret_cast<unsigned char *>(base) + v_off);
     cudaStream_t s = (cudaStream_t)stream;
     using C = FarCfg<1, 4>;
-    GYPS_CUDA(cudaFuncSetAttribute(far32_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    int occ = 0;
-    GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, far32_kernel<1, 4>, C::NT, C::SMEM));
-    occ = std::max(occ, 1);
     const double2 *Xd = (const double2 *)X;
     double2 *Yd = (double2 *)Y;
     for (int j = 0; j < nrhs; ++j) {
@@ -884,23 +920,11 @@ extern "C" gyps_status gyps_sl_apply_noalloc(gyps_mesh_t h, double k, int nrhs, 
         interp32_kernel<1><<<(unsigned)((m->nq_pad + 255) / 256), 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq,
                                                                                m->nq_pad, Xd, ldx, j, panel);
         GYPS_CUDA(cudaGetLastError());
-        FarArgs a;
-        a.pos_panel = m->d_pos_panel;
-        a.den_panel = panel;
-        a.tgt = m->d_pts32;
-        a.v = v;
-        a.ldv = m->nq;
-        a.t_begin = 0;
-        a.t_end = m->nq;
-        a.n_src_tiles = m->n_src_tiles;
-        a.n_tgt_tiles = (m->nq + C::TT - 1) / C::TT;
-        a.kk = (float)(k / kTwoPi);
-        a.k = (float)k;
-        a.err = m->d_err;
-        const int64_t items = a.n_tgt_tiles * a.n_src_tiles;
-        const int64_t grid = std::min<int64_t>((int64_t)m->num_sms * occ, items);
-        far32_kernel<1, 4><<<(unsigned)grid, C::NT, C::SMEM, s>>>(a);
-        GYPS_CUDA(cudaGetLastError());
+        FarArgs a = far_args(m, panel, v, m->nq, 0, m->nq, C::TT, k);
+        if (k > 0.0)
+            GYPS_TRY((launch_far32<1, 4, false>(m, a, s)));
+        else
+            GYPS_TRY((launch_far32<1, 4, true>(m, a, s)));
         dim3 g((unsigned)((m->nv + 127) / 128), 1u);
         project_kernel<<<g, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_pts64, m->rule, m->nv, v, m->nq, m->d_c_rowptr,
                                          m->d_c_col, m->d_c_val, Xd + (int64_t)j * ldx, ldx, Yd + (int64_t)j * ldy,

@@ -219,3 +219,23 @@ def test_sphere10242_k16_q7_sampled_rows(g):
     assert rel(y32, ref) < 1e-5
     y64 = to_np(g.sl_apply(gm, 16.0, xd, prec="fp64"))[rows]
     assert rel(y64, ref) < 1e-10
+
+
+@pytest.mark.slow
+def test_sphere10242_k16_q7_gmres_against_mie(g):
+    """Workload sphere10242_k16_q7: sound-soft scattering, FP32 operator in the
+    Krylov loop, FP64 true residual <= 1e-6, density close to the Mie series
+    (mass-weighted relative L2 error; discretisation error, kh ~ 0.5)."""
+    v, t = synth.icosphere(5)
+    gm = g.Mesh(v, t, 7)
+    d = (1.0, 0.0, 0.0)
+    f = g.rhs_planewave(gm, 16.0, [d])
+    x, rep = g.gmres_solve(gm, 16.0, f, tol=1e-6, restart=200, maxit=1000, prec="fp32", check_prec="fp64",
+                           max_refine=4)
+    assert rep.status == "OK" and rep.true_residual[0] <= 1e-6
+    lam = to_np(x)[:, 0]
+    ref = oracle.mie_density(16.0, d, v)
+    mm = oracle.mass_matrix(v, t, 7)
+    e = lam - ref
+    err = np.sqrt(np.real(e.conj() @ (mm @ e)) / np.real(ref.conj() @ (mm @ ref)))
+    assert err < 0.05, err
