@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gyps", choices=["gyps", "reference"])
+    p.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch12_r64"])
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--solve", action="store_true", help="also time GMRES to 1e-6 (FP32 + FP64 check)")
@@ -349,8 +350,57 @@ def run_gyps(args, rank, world, local_rank):
     mesh.close()
 
 
+def run_batch(args):
+    """Workload batch12_r64: 12 meshes (icospheres levels 2-6 and 7 random
+    ellipsoids, 320-81920 triangles, q = 3), k_i ~ U[2, 24], 64 right-hand
+    sides each, one graph replay per step (one persistent far launch)."""
+    import torch
+
+    import paper_1804_00995_gb300 as g
+    from paper_1804_00995_gb300 import build as gb
+    gb.build()
+    dev = torch.device("cuda", 0)
+    items, _ = synth.batch_workload(nrhs=64)
+    meshes = [g.Mesh(it["vtx"], it["tri"], 3) for it in items]
+    t0 = time.perf_counter()
+    b = g.Batch([(m, it["k"]) for m, it in zip(meshes, items)], 64, graph=True, autotune=True)
+    t_create = time.perf_counter() - t0
+    for i, m in enumerate(meshes):
+        b.X[i].copy_(torch.as_tensor(synth.random_complex(np.random.default_rng(i), m.nv, 64)))
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        b.apply()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        b.apply()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(c) for a, c in ev) / args.steps
+    pairs = b.info["pairs"]
+    line = {
+        "metric": "GPairs/s batched single-layer apply", "value": pairs / (ms * 1e-3) / 1e9, "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "pair_rhs_per_s": pairs * 64 / (ms * 1e-3),
+        "config": {"workload": "batch12_r64", "meshes": [(it["kind"], it["level"], int(it["tri"].shape[0]),
+                                                             round(float(it["k"]), 3)) for it in items],
+                   "nq_total": int(sum(m.nq for m in meshes)), "nrhs": 64, "quad_points": 3,
+                   "pairs_per_rhs": pairs, "l2": "flushed (512 MB write) before every step"},
+        "batch": dict(b.info), "create_s": t_create,
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
 def main():
     args = parse()
+    if args.workload == "batch12_r64":
+        run_batch(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -205,6 +205,64 @@ gyps_status gyps_gmres_solve(gyps_mesh_t mesh, double k, int nrhs, const void *F
                              void *X, int64_t ldx, const gyps_gmres_opts *opts,
                              gyps_gmres_report *report, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched apply: several meshes (uneven sizes, their own k), each with nrhs
+ * right-hand sides, Y_i = V_i X_i as in gyps_sl_apply with GYPS_PREC_FP32
+ * (all triangles, correction on).  The kernel products of all meshes run as
+ * one persistent launch over a single list of equal-cost work items
+ * (mesh, RHS chunk, target tile, source tile); with one interpolation and one
+ * projection launch around it, the whole batch is captured once into a CUDA
+ * graph and replayed by gyps_batch_apply.  The RHS chunk width and targets per
+ * thread come from the autotuner (timed candidates, cached in the JSON file
+ * $GYPS_TUNE_CACHE, default ~/.cache/gyps_tune.json) or a default.
+ * ------------------------------------------------------------------------ */
+typedef struct gyps_batch_s *gyps_batch_t;
+
+typedef struct {
+    gyps_mesh_t mesh;  /* created by gyps_mesh_create, on the batch's device */
+    double k;          /* wavenumber of this mesh (finite, >= 0) */
+    const void *X;     /* DEVICE, nv x nrhs complex double2, leading dimension ldx */
+    int64_t ldx;
+    void *Y;           /* DEVICE, nv x nrhs complex double2, leading dimension ldy */
+    int64_t ldy;
+} gyps_batch_item;
+
+#define GYPS_BATCH_NO_GRAPH 0x1u /* launch the kernels on each apply instead of a captured graph */
+#define GYPS_BATCH_AUTOTUNE 0x2u /* time the candidate shapes now when the cache has no entry */
+
+typedef struct {
+    int32_t nmesh, nrhs;
+    int32_t rhs_chunk;          /* R: right-hand sides per pass of the kernel product */
+    int32_t targets_per_thread; /* T */
+    int32_t grid;               /* persistent CTAs */
+    int32_t uses_graph;
+    int32_t tuned;              /* 0 default shape, 1 timed now, 2 read from the cache */
+    int64_t work_items;
+    double pairs;               /* sum over meshes of nq^2 (per right-hand side) */
+} gyps_batch_info_t;
+
+/*
+ * Binds the items (meshes, k, X and Y buffers: the graph keeps these pointers)
+ * and prepares the batch: per-mesh workspace (FP32 density panels, FP64
+ * accumulators), the work list, the shape choice and the graph.  X and Y must
+ * stay valid until gyps_batch_destroy; refill X and call gyps_batch_apply.
+ *   items  HOST array of nitems (1..4096).  nrhs 1..4096, shared by all items.
+ *   flags  GYPS_BATCH_NO_GRAPH | GYPS_BATCH_AUTOTUNE.
+ * Errors: INVALID (argument, host buffers, meshes on different devices), OOM, CUDA.
+ */
+gyps_status gyps_batch_create(const gyps_batch_item *items, int nitems, int nrhs, uint32_t flags,
+                              void *stream, gyps_batch_t *out);
+
+/* Y_i = V_i X_i for every item, asynchronously on `stream`. */
+gyps_status gyps_batch_apply(gyps_batch_t batch, void *stream);
+
+/* Shape and size of a batch. info: HOST. */
+gyps_status gyps_batch_info(gyps_batch_t batch, gyps_batch_info_t *info);
+
+/* Synchronises the device, releases the batch; TIMEOUT if a device wait of one
+ * of its applies ran out of polls.  NULL is accepted. */
+gyps_status gyps_batch_destroy(gyps_batch_t batch);
+
 /*
  * gyps_sl_apply without any device allocation (the paper has no counterpart:
  * this is a library service).  For callers that must not allocate device

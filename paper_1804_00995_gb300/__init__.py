@@ -52,6 +52,17 @@ class _Profile(ctypes.Structure):
                 ("far_launches", ctypes.c_int64)]
 
 
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("mesh", ctypes.c_void_p), ("k", ctypes.c_double), ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64),
+                ("Y", ctypes.c_void_p), ("ldy", ctypes.c_int64)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("nmesh", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
+                ("targets_per_thread", ctypes.c_int32), ("grid", ctypes.c_int32), ("uses_graph", ctypes.c_int32),
+                ("tuned", ctypes.c_int32), ("work_items", ctypes.c_int64), ("pairs", ctypes.c_double)]
+
+
 class _GmresOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("check_prec", ctypes.c_int32), ("use_x0", ctypes.c_int32),
@@ -88,6 +99,11 @@ _SIGS = {
     "gyps_gmres_solve": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                           ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(_GmresOpts),
                           ctypes.POINTER(_GmresReport), ctypes.c_void_p], ctypes.c_int),
+    "gyps_batch_create": ([ctypes.POINTER(_BatchItem), ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p,
+                           ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "gyps_batch_apply": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "gyps_batch_info": ([ctypes.c_void_p, ctypes.POINTER(_BatchInfo)], ctypes.c_int),
+    "gyps_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "gyps_sl_apply_noalloc": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "gyps_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
@@ -281,6 +297,52 @@ def rhs_planewave(mesh: Mesh, k: float, dirs, device=None, stream=None):
     _check(load().gyps_rhs_planewave(mesh.handle, float(k), dirs.shape[0], dirs.ctypes.data, f.data_ptr(), mesh.nv,
                                      _stream(stream)))
     return f
+
+
+class Batch:
+    """gyps_batch_create / apply: Y_i = V_i X_i for many meshes in one persistent launch.
+
+    items: list of (mesh, k); X, Y are allocated here as column-major
+    complex128 (nv_i, nrhs) device tensors (``self.X[i]``, ``self.Y[i]``) and
+    bound to the batch: fill ``X[i]`` in place, call ``apply()``.
+    """
+
+    def __init__(self, items, nrhs: int, graph: bool = True, autotune: bool = False, stream=None):
+        torch = _torch()
+        self.meshes = [m for m, _ in items]
+        self.ks = [float(k) for _, k in items]
+        self.X = [_empty_colmajor(m.nv, nrhs, m.device) for m in self.meshes]
+        self.Y = [_empty_colmajor(m.nv, nrhs, m.device) for m in self.meshes]
+        for x in self.X:
+            x.zero_()
+        arr = (_BatchItem * len(items))()
+        for i, m in enumerate(self.meshes):
+            arr[i] = _BatchItem(m.handle.value, self.ks[i], self.X[i].data_ptr(), m.nv, self.Y[i].data_ptr(), m.nv)
+        flags = (0 if graph else 0x1) | (0x2 if autotune else 0)
+        h = ctypes.c_void_p()
+        _check(load().gyps_batch_create(arr, len(items), int(nrhs), flags, _stream(stream), ctypes.byref(h)))
+        self._h = h
+        info = _BatchInfo()
+        _check(load().gyps_batch_info(self._h, ctypes.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in _BatchInfo._fields_}
+        del torch
+
+    def apply(self, stream=None):
+        _check(load().gyps_batch_apply(self._h, _stream(stream)))
+        return self.Y
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            code = _lib.gyps_batch_destroy(self._h)
+            self._h = None
+            _check(code)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 @dataclass

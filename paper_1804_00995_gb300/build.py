@@ -46,7 +46,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     nvcc = os.path.join(cuda, "bin", "nvcc")
     objdir = os.path.join(BUILD, "obj")
     os.makedirs(objdir, exist_ok=True)
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
     jobs = []
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")

@@ -141,3 +141,37 @@ WORKLOADS = {
     "sphere10242_k16_q7": dict(level=5, q=7, k=16.0, dirs=[(1.0, 0.0, 0.0)], tol=1e-6),
     "sphere163842_k64_q3_r16": dict(level=7, q=3, k=64.0, ndirs=16, seed=7, tol=1e-6),
 }
+
+
+def j_zeros_near(k: float, delta: float, nmax: int = 80) -> bool:
+    """True when k lies within delta of a zero of a spherical Bessel function
+    j_n (n <= nmax): the unit sphere's single layer is singular there."""
+    from scipy.special import spherical_jn
+    xs = np.linspace(max(k - delta, 1e-6), k + delta, 41)
+    for n in range(nmax + 1):
+        v = spherical_jn(n, xs)
+        if np.any(np.sign(v[:-1]) != np.sign(v[1:])):
+            return True
+    return False
+
+
+def batch_workload(seed: int = 1804, nrhs: int = 64, levels=(2, 3, 4, 5, 6), n_ellipsoids: int = 7,
+                   ell_levels=(2, 6), k_range=(2.0, 24.0)):
+    """The uneven batch: icospheres of the given levels plus random-axis
+    ellipsoids (level U{ell_levels}, semi-axes U[0.5, 2]); k_i ~ U[k_range],
+    redrawn for spheres within 0.02 of a zero of some j_n; nrhs plane-wave
+    directions uniform on the sphere.  Returns a list of dicts and the directions."""
+    rng = np.random.default_rng(seed)
+    items = []
+    for lv in levels:
+        v, t = icosphere(lv)
+        k = rng.uniform(*k_range)
+        while j_zeros_near(k, 0.02):
+            k = rng.uniform(*k_range)
+        items.append(dict(kind="sphere", level=lv, vtx=v, tri=t, k=k))
+    for _ in range(n_ellipsoids):
+        lv = int(rng.integers(ell_levels[0], ell_levels[1] + 1))
+        v, t, ax = random_ellipsoid(rng, lv)
+        items.append(dict(kind="ellipsoid", level=lv, vtx=v, tri=t, k=rng.uniform(*k_range), axes=ax))
+    dirs = plane_wave_dirs(rng, nrhs)
+    return items, dirs
