@@ -89,6 +89,8 @@ struct Mesh {
     void *ws_den = nullptr; size_t ws_den_bytes = 0;   // density panel / FP64 densities
     void *ws_v = nullptr; size_t ws_v_bytes = 0;       // target accumulators
     void *ws_stage = nullptr; size_t ws_stage_bytes = 0;  // host<->device staging
+    void *ws_tc = nullptr; size_t ws_tc_bytes = 0;        // tensor-core source panel
+    float pad = 0.0f;                                     // distance of padding points
     int64_t device_bytes = 0;
     int num_sms = 0;
 
@@ -140,6 +142,8 @@ cudaError_t launch_near_build(const Mesh &m, cudaStream_t s);
 // a2-a5: one matrix-free apply with device pointers
 gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
                          int prec, uint32_t flags, int64_t tri_begin, int64_t tri_end, cudaStream_t s);
+gyps_status far_tc(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, double2 *v, int64_t ldv,
+                   cudaStream_t s);
 cudaError_t launch_near_spmv(const Mesh &m, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
                              cudaStream_t s);
 

@@ -359,7 +359,7 @@ static void free_mesh(Mesh *m)
     if (!m) return;
     void *ptrs[] = {m->d_vtx, m->d_tri, m->d_pts64, m->d_pts32, m->d_pos_panel, m->d_v2t_ptr, m->d_v2t,
                     m->d_pair_a, m->d_pair_b, m->d_pair_ptr, m->d_blocks, m->d_c_rowptr, m->d_c_col,
-                    m->d_c_val, m->d_c_src_ptr, m->d_c_src, m->d_err, m->ws_den, m->ws_v, m->ws_stage};
+                    m->d_c_val, m->d_c_src_ptr, m->d_c_src, m->d_err, m->ws_den, m->ws_v, m->ws_stage, m->ws_tc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -393,6 +393,7 @@ static gyps_status create(const double *vtx, int64_t nv, const int32_t *tri, int
     double ext = 0.0;
     for (int64_t i = 0; i < 3 * nv; ++i) ext = std::max(ext, std::fabs(vtx[i]));
     const float pad = (float)(1.0e3 * (1.0 + ext));
+    m->pad = pad;
 
     m->rule.q = q;
     reference_rule(q, m->rule.bary, m->rule.w);

@@ -1,0 +1,58 @@
+"""Tensor-core form of the kernel product (bf16 hi+lo split, three products,
+FP32 accumulation in tensor memory) against the FP64 oracle and the FP32
+CUDA-core apply.  Tolerance 1e-4 relative per column (split bf16 products)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TC_TOL = 1e-4
+
+
+def rel(a, b):
+    return max(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c]) for c in range(a.shape[1]))
+
+
+@pytest.mark.parametrize("level,q,k,nrhs", [(1, 3, 5.0, 16), (2, 3, 16.0, 16), (2, 7, 9.0, 20), (3, 3, 30.0, 32)])
+def test_tc_apply_vs_oracle(level, q, k, nrhs):
+    import paper_1804_00995_gb300 as g
+    v, t = synth.icosphere(level)
+    gm = g.Mesh(v, t, q)
+    om = oracle.Mesh(v, t, q)
+    x = synth.random_complex(np.random.default_rng(level * 10 + nrhs), om.nv, nrhs)
+    xd = torch.as_tensor(x).cuda()
+    y = g.sl_apply(gm, k, xd, prec="tc_bf16x3").cpu().numpy()
+    assert np.isfinite(y).all()
+    ref = om.apply(k, x)
+    assert rel(y, ref) < TC_TOL
+    y32 = g.sl_apply(gm, k, xd, prec="fp32").cpu().numpy()
+    assert rel(y, y32) < TC_TOL
+    # auto picks the tensor cores at nrhs >= 16
+    ya = g.sl_apply(gm, k, xd, prec="auto").cpu().numpy()
+    assert rel(ya, y) < 1e-12
+
+
+def test_tc_far_part_ellipsoid():
+    import paper_1804_00995_gb300 as g
+    v, t = synth.ellipsoid(2, (0.6, 1.4, 1.9), (1.0, -1.0, 0.3), 1.1)
+    gm = g.Mesh(v, t, 3)
+    om = oracle.Mesh(v, t, 3)
+    x = synth.random_complex(np.random.default_rng(4), om.nv, 16)
+    y = g.sl_apply(gm, 11.0, torch.as_tensor(x).cuda(), prec="tc_bf16x3", near=False).cpu().numpy()
+    assert rel(y, om.far_apply(11.0, x)) < TC_TOL
+
+
+def test_tc_rejects_laplace_and_partial_ranges():
+    import paper_1804_00995_gb300 as g
+    v, t = synth.icosphere(1)
+    gm = g.Mesh(v, t, 3)
+    x = torch.zeros((gm.nv, 16), dtype=torch.complex128, device="cuda")
+    for kw in (dict(k=0.0), dict(k=2.0, tri_range=(0, 10))):
+        kk = kw.pop("k")
+        with pytest.raises(g.GypsError) as e:
+            g.sl_apply(gm, kk, x, prec="tc_bf16x3", **kw)
+        assert e.value.status == "UNSUPPORTED"
