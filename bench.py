@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gyps", choices=["gyps", "reference"])
     p.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch12_r64"])
+    p.add_argument("--nrhs", type=int, default=1, help="right-hand sides per apply (the workload has 1)")
+    p.add_argument("--prec", default="fp32", choices=["fp32", "tc_bf16x3", "auto"],
+                   help="kernel-product arithmetic (tc_bf16x3: tensor cores, needs nrhs >= 16)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--solve", action="store_true", help="also time GMRES to 1e-6 (FP32 + FP64 check)")
@@ -229,14 +232,15 @@ def run_gyps(args, rank, world, local_rank):
     nq, nv = mesh.nq, mesh.nv
     pairs = float(nq) * nq
     # each rank applies the operator to its own seeded right-hand side (independent problems)
-    x = torch.as_tensor(synth.random_complex(np.random.default_rng(1000 + rank), nv, 1)).to(dev)
-    y = g.sl_apply(mesh, k, x, prec="fp32")
+    nrhs, prec = args.nrhs, args.prec
+    x = torch.as_tensor(synth.random_complex(np.random.default_rng(1000 + rank), nv, nrhs)).to(dev)
+    y = g.sl_apply(mesh, k, x, prec=prec)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(args.warmup):
         flush.zero_()
-        g.sl_apply(mesh, k, x, prec="fp32", out=y)
+        g.sl_apply(mesh, k, x, prec=prec, out=y)
     torch.cuda.synchronize(dev)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -254,7 +258,7 @@ def run_gyps(args, rank, world, local_rank):
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        g.sl_apply(mesh, k, x, prec="fp32", out=y)
+        g.sl_apply(mesh, k, x, prec=prec, out=y)
         ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
@@ -274,25 +278,28 @@ def run_gyps(args, rank, world, local_rank):
 
     # roofline of the dominant kernel (dense G u), from its own events
     far_ms = prof["far_ms"] / max(prof["far_launches"], 1)
-    achieved = pairs / (far_ms * 1e-3) / 1e9
+    # one launch covers all right-hand sides of a pass: pairs per launch = Nq^2 x (passes per apply)^-1
+    launches_per_apply = prof["far_launches"] / max(prof["applies"], 1)
+    achieved = pairs / (far_ms * launches_per_apply * 1e-3) / 1e9
     peak_mhz = None
     try:
         peak_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
     except Exception:
         peak_mhz = clk.get("sm_max_mhz") or 2070.0
     peak = sm_peak_pairs(props.multi_processor_count, peak_mhz) / 1e9
-    traffic = far_traffic_per_launch()
+    traffic = far_traffic_per_launch() if (prec == "fp32" and nrhs == 1) else None
 
     # end to end through the public API with host buffers (pinned), copies inside
-    xh = torch.as_tensor(synth.random_complex(np.random.default_rng(2000 + rank), nv, 1)).pin_memory()
-    yh = torch.empty((1, nv), dtype=torch.complex128).pin_memory().t()
-    g.sl_apply(mesh, k, xh, prec="fp32", out=yh)
+    xh = torch.as_tensor(synth.random_complex(np.random.default_rng(2000 + rank), nv, nrhs)).t().contiguous().t()
+    xh = xh.pin_memory().t().contiguous().t() if nrhs == 1 else xh
+    yh = torch.empty((nrhs, nv), dtype=torch.complex128).pin_memory().t()
+    g.sl_apply(mesh, k, xh, prec=prec, out=yh)
     e2e_t = []
     for i in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        g.sl_apply(mesh, k, xh, prec="fp32", out=yh)  # returns once Y is back on the host
+        g.sl_apply(mesh, k, xh, prec=prec, out=yh)  # returns once Y is back on the host
         e2e_t.append(time.perf_counter() - t0)
     e2e_mean = sum(e2e_t) / len(e2e_t)
     if world > 1:
@@ -328,18 +335,21 @@ def run_gyps(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16x3+f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "mesh": "icosphere level 5 (20480 triangles)", "nv": nv, "nq": nq,
-                       "k": k, "quad_points": cfg["q"], "nrhs": 1, "far": "fp32", "near": "fp64",
+                       "k": k, "quad_points": cfg["q"], "nrhs": nrhs, "far": prec, "near": "fp64",
                        "l2": "flushed (512 MB write) before every step", "pairs_per_step": pairs,
                        "ranks": "independent replicas, one right-hand side each"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-                         "traffic": traffic, "kernel": "far32_kernel<1,4,false>",
+                         "traffic": traffic,
+                         "kernel": "far32_kernel<1,4,false>" if prec == "fp32" else "far_tc_kernel",
                          "peak_basis": f"{props.multi_processor_count} SMs x {MUFU_PER_CLK_PER_SM}/{MUFU_PER_PAIR} "
                                        f"pairs/clk x {peak_mhz:.0f} MHz (measured sm_max_mhz)",
                          "far_ms_per_launch": far_ms},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nv * 16, "d2h_bytes_per_step": nv * 16},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nv * 16 * nrhs,
+                    "d2h_bytes_per_step": nv * 16 * nrhs},
+            "pair_rhs_per_s": pairs * nrhs / (ms_per_step * 1e-3),
             "gpu_launches": int(prof["launches"]),
             "clocks": clk,
             "wall_s_timed_region": wall,

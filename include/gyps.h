@@ -207,14 +207,16 @@ gyps_status gyps_gmres_solve(gyps_mesh_t mesh, double k, int nrhs, const void *F
 
 /* ------------------------------------------------------------------------
  * Batched apply: several meshes (uneven sizes, their own k), each with nrhs
- * right-hand sides, Y_i = V_i X_i as in gyps_sl_apply with GYPS_PREC_FP32
- * (all triangles, correction on).  The kernel products of all meshes run as
- * one persistent launch over a single list of equal-cost work items
- * (mesh, RHS chunk, target tile, source tile); with one interpolation and one
- * projection launch around it, the whole batch is captured once into a CUDA
- * graph and replayed by gyps_batch_apply.  The RHS chunk width and targets per
- * thread come from the autotuner (timed candidates, cached in the JSON file
- * $GYPS_TUNE_CACHE, default ~/.cache/gyps_tune.json) or a default.
+ * right-hand sides, Y_i = V_i X_i as in gyps_sl_apply (all triangles, correction
+ * on).  Two forms: (a) the FP32 CUDA-core kernel products of all meshes as one
+ * persistent launch over a single list of equal-cost work items (mesh, RHS
+ * chunk, target tile, source tile), with one interpolation and one projection
+ * launch around it; (b) with 16 or more right-hand sides and every k > 0, the
+ * tensor-core apply (GYPS_PREC_TC_BF16X3) of each mesh in turn.  The batch is
+ * captured once into a CUDA graph and replayed by gyps_batch_apply.  The form,
+ * RHS chunk width and targets per thread come from the autotuner (timed
+ * candidates, cached in the JSON file $GYPS_TUNE_CACHE, default
+ * ~/.cache/gyps_tune.json) or a default (tensor cores when allowed).
  * ------------------------------------------------------------------------ */
 typedef struct gyps_batch_s *gyps_batch_t;
 
@@ -237,6 +239,8 @@ typedef struct {
     int32_t grid;               /* persistent CTAs */
     int32_t uses_graph;
     int32_t tuned;              /* 0 default shape, 1 timed now, 2 read from the cache */
+    int32_t tensor_cores;       /* 1: tensor-core applies per mesh (>= 16 RHS, every k > 0) */
+    int32_t reserved;
     int64_t work_items;
     double pairs;               /* sum over meshes of nq^2 (per right-hand side) */
 } gyps_batch_info_t;

@@ -60,7 +60,8 @@ class _BatchItem(ctypes.Structure):
 class _BatchInfo(ctypes.Structure):
     _fields_ = [("nmesh", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
                 ("targets_per_thread", ctypes.c_int32), ("grid", ctypes.c_int32), ("uses_graph", ctypes.c_int32),
-                ("tuned", ctypes.c_int32), ("work_items", ctypes.c_int64), ("pairs", ctypes.c_double)]
+                ("tuned", ctypes.c_int32), ("tensor_cores", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("work_items", ctypes.c_int64), ("pairs", ctypes.c_double)]
 
 
 class _GmresOpts(ctypes.Structure):

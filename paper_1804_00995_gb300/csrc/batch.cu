@@ -309,6 +309,7 @@ struct Batch {
     cudaGraphExec_t exec = nullptr;
     int tuned = 0;  // 0 default, 1 measured now, 2 read from the cache
     std::vector<Mesh *> meshes;
+    std::vector<gyps_batch_item> items_host;  // bound buffers (tensor-core mode applies per mesh)
     ~Batch()
     {
         if (exec) cudaGraphExecDestroy(exec);
@@ -336,6 +337,14 @@ static int tile_targets(int R, int T) { return 128 * T; }
 
 static gyps_status enqueue(Batch *b, cudaStream_t s)
 {
+    if (b->R == 0) {  // tensor-core mode: the tensor-core apply of every mesh, in order
+        for (size_t i = 0; i < b->meshes.size(); ++i) {
+            const gyps_batch_item &it = b->items_host[i];
+            GYPS_TRY(apply_device(b->meshes[i], it.k, b->nrhs, (const double2 *)it.X, it.ldx, (double2 *)it.Y, it.ldy,
+                                  GYPS_PREC_TC_BF16X3, 0, 0, b->meshes[i]->nt, s));
+        }
+        return GYPS_OK;
+    }
     GYPS_CUDA(cudaMemsetAsync(b->d_v, 0, b->v_bytes, s));
     const unsigned gi = (unsigned)((b->total_src + 255) / 256);
     switch (b->R) {
@@ -366,6 +375,17 @@ static gyps_status configure(Batch *b, const std::vector<gyps_batch_item> &items
 {
     b->R = R;
     b->T = T;
+    b->items_host = items;
+    if (R == 0) {  // tensor-core mode: per-mesh workspaces live in the meshes
+        b->pairs = 0.0;
+        b->items = 0;
+        for (auto *m : b->meshes) {
+            b->pairs += (double)m->nq * (double)m->nq;
+            b->items += ((m->nq + 127) / 128) * ((m->nq + 4095) / 4096);
+        }
+        b->grid = 0;
+        return GYPS_OK;
+    }
     const int tt = tile_targets(R, T);
     const int nchunk = b->nrhs / R;
     std::vector<FarSeg> fs;
@@ -524,7 +544,7 @@ static bool tune_lookup(const std::string &key, int *R, int *T)
         size_t lb = line.find('[', p);
         if (lb == std::string::npos) continue;
         int r = 0, t = 0;
-        if (std::sscanf(line.c_str() + lb, "[%d, %d", &r, &t) == 2 && r > 0 && t > 0) {
+        if (std::sscanf(line.c_str() + lb, "[%d, %d", &r, &t) == 2 && r >= 0 && t >= 0) {
             *R = r;
             *T = t;
             return true;
@@ -577,9 +597,11 @@ static std::string tune_key(const Batch *b)
 }
 
 // Candidate (R, T) shapes: R divides nrhs; T chosen so the registers fit.
-static std::vector<std::pair<int, int>> candidates(int nrhs)
+// (0, 0) stands for the tensor-core form (16 or more right-hand sides, k > 0).
+static std::vector<std::pair<int, int>> candidates(int nrhs, bool tc_ok)
 {
     std::vector<std::pair<int, int>> c;
+    if (tc_ok && nrhs >= 16) c.push_back({0, 0});
     if (nrhs % 8 == 0) c.push_back({8, 2});
     if (nrhs % 4 == 0) {
         c.push_back({4, 2});
@@ -655,13 +677,15 @@ extern "C" gyps_status gyps_batch_create(const gyps_batch_item *items, int nitem
     gyps_status st = GYPS_OK;
     if (cudaMalloc((void **)&b->d_err, sizeof(int)) != cudaSuccess) st = set_error(GYPS_ERR_OOM, "error word");
     if (st == GYPS_OK) cudaMemset(b->d_err, 0, sizeof(int));
-    int R = 0, T = 0;
+    bool tc_ok = true;
+    for (const auto &it : its) tc_ok = tc_ok && it.k > 0.0;
+    int R = -1, T = -1;
     const std::string key = (st == GYPS_OK) ? tune_key(b) : std::string();
-    if (st == GYPS_OK && tune_lookup(key, &R, &T) && nrhs % R == 0) {
+    if (st == GYPS_OK && tune_lookup(key, &R, &T) && ((R == 0 && tc_ok && nrhs >= 16) || (R > 0 && nrhs % R == 0))) {
         b->tuned = 2;
     } else if (st == GYPS_OK && (flags & GYPS_BATCH_AUTOTUNE)) {
         double best = 1e300;
-        for (auto c : candidates(nrhs)) {
+        for (auto c : candidates(nrhs, tc_ok)) {
             st = configure(b, its, c.first, c.second);
             double ms = 0.0;
             if (st == GYPS_OK) st = time_config(b, s, &ms);
@@ -677,13 +701,24 @@ extern "C" gyps_status gyps_batch_create(const gyps_batch_item *items, int nitem
             b->tuned = 1;
         }
     } else if (st == GYPS_OK) {
-        auto c = candidates(nrhs).front();  // widest chunk
+        auto c = candidates(nrhs, tc_ok).front();  // tensor cores if possible, else the widest chunk
         R = c.first;
         T = c.second;
     }
     if (st == GYPS_OK) st = configure(b, its, R, T);
     b->use_graph = !(flags & GYPS_BATCH_NO_GRAPH);
-    if (st == GYPS_OK && b->use_graph) st = capture(b);
+    if (st == GYPS_OK && b->use_graph) {
+        // one direct run first: workspaces are allocated before the capture
+        st = enqueue(b, s);
+        if (st == GYPS_OK) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = cuda_error(e, "batch warm-up");
+        }
+        if (st == GYPS_OK && capture(b) != GYPS_OK) {
+            cudaGetLastError();
+            b->use_graph = false;  // launch directly when the work cannot be captured
+        }
+    }
     if (st != GYPS_OK) {
         cudaDeviceSynchronize();
         delete b;
@@ -719,6 +754,7 @@ extern "C" gyps_status gyps_batch_info(gyps_batch_t h, gyps_batch_info_t *info)
     info->pairs = b->pairs;
     info->uses_graph = b->use_graph ? 1 : 0;
     info->tuned = b->tuned;
+    info->tensor_cores = b->R == 0 ? 1 : 0;
     return GYPS_OK;
 }
 

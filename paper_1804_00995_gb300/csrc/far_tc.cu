@@ -25,8 +25,6 @@ constexpr int KS = 32;          // sources per chunk
 constexpr int KC = 2 * KS;      // K extent per chunk: Gr for the chunk, then Gi
 constexpr int NTHR = 256;       // 8 warps, two per target row (each half the chunk)
 constexpr int SEG_CHUNKS = 128; // chunks per work item (4096 sources)
-constexpr int SRC_STAGES = 4;
-constexpr int A_STAGES = 2;
 constexpr int POS_BYTES = 384;  // float4 XY[16] + float2 Z[16] (negated, scaled by k)
 constexpr uint32_t CORE_LBO = 128;            // bytes between core matrices along K
 constexpr uint32_t CORE_SBO = (KC / 8) * 128; // bytes between 8-row groups
@@ -46,10 +44,6 @@ struct Cfg {
     static constexpr int B_BYTES = N * KC * 2;            // bf16 panel, one of hi / lo
     static constexpr int CHUNK_BYTES = POS_BYTES + 2 * B_BYTES;
     static constexpr int A_BYTES = M * KC * 2;            // bf16 kernel tile, one of hi / lo
-    static constexpr int A_OFF = 0;                       // A[stage][hi, lo]
-    static constexpr int SRC_OFF = A_STAGES * 2 * A_BYTES;
-    static constexpr int BAR_OFF = SRC_OFF + SRC_STAGES * CHUNK_BYTES;
-    static constexpr int SMEM = BAR_OFF + 128;
     static constexpr int TMEM_COLS = N < 32 ? 32 : N;
 };
 
@@ -105,6 +99,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -207,11 +209,15 @@ struct TcArgs {
     int *err;
 };
 
-template <int R, bool CHECK>
+// Kernel tile of one generator thread: target `row`, the GPR sources of its
+// slice of the chunk, split into bf16 hi/lo and stored at K = s (Gr) and
+// K = KS + s (Gi).
+template <int GPR, bool CHECK>
 __device__ __forceinline__ void gen_chunk(const unsigned char *src, unsigned char *a_hi, unsigned char *a_lo,
                                           float2 tx, float2 ty, float2 tz, int64_t tgt, int64_t src0, int row,
-                                          int half)
+                                          int slice)
 {
+    constexpr int SRC_PER = KS / GPR;  // sources per thread (8 or 16)
     const float4 *XY = reinterpret_cast<const float4 *>(src);
     const float2 *Z = reinterpret_cast<const float2 *>(src + 256);
     const float2 magic = make_float2(12582912.0f, 12582912.0f);
@@ -219,11 +225,11 @@ __device__ __forceinline__ void gen_chunk(const unsigned char *src, unsigned cha
     const float2 inv2pi = make_float2(0.159154943091895335769f, 0.159154943091895335769f);
     const float2 m2pi = make_float2(-6.28318530717958647692f, -6.28318530717958647692f);
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {  // two groups of 8 sources (one core-matrix row each)
+    for (int q = 0; q < SRC_PER / 8; ++q) {  // groups of 8 sources = one core-matrix row
         uint32_t hr[4], lr[4], hi_[4], li[4];
 #pragma unroll
         for (int p4 = 0; p4 < 4; ++p4) {
-            const int pp = half * 8 + q * 4 + p4;  // source pair within the chunk
+            const int pp = (slice * SRC_PER + q * 8) / 2 + p4;  // source pair within the chunk
             const float4 xy = XY[pp];
             const float2 sz = Z[pp];
             float2 dx = __fadd2_rn(tx, make_float2(xy.x, xy.y));
@@ -251,7 +257,7 @@ __device__ __forceinline__ void gen_chunk(const unsigned char *src, unsigned cha
             split2(gre, hr[p4], lr[p4]);
             split2(gim, hi_[p4], li[p4]);
         }
-        const int kre = half * 16 + q * 8;  // K position of the group's first source (Gr part)
+        const int kre = slice * SRC_PER + q * 8;
         const uint32_t ore = core_off(row, kre), oim = core_off(row, KS + kre);
         *reinterpret_cast<uint4 *>(a_hi + ore) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
         *reinterpret_cast<uint4 *>(a_lo + ore) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
@@ -260,16 +266,46 @@ __device__ __forceinline__ void gen_chunk(const unsigned char *src, unsigned cha
     }
 }
 
-template <int R>
-__global__ void __launch_bounds__(NTHR) far_tc_kernel(const TcArgs a)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another thread reported a failure.
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort)
+{
+    for (int n = 0; n < (1 << 22); ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((n & 255) == 255 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+// Warp-specialised kernel: GPR generator threads per target row (warps
+// 0 .. 4 GPR - 1) and one control warp (the last) whose lane 0 issues the bulk
+// copies of the density panel and the tensor-core products.  Hand-offs:
+//   src_full[s]  copy of chunk n landed (count 1 + tx bytes)
+//   a_full[s]    all generators wrote the kernel tile of chunk n (count 128 GPR)
+//   mma_done[s]  products of chunk n finished (tcgen05.commit): tile and copy stage free
+//   acc_full     all products of a work item finished: accumulator ready
+//   acc_empty    every generator read the accumulator (count 128 GPR)
+template <int R, int GPR, int SS, int A_STAGES>
+__global__ void __launch_bounds__(M * GPR + 32) far_tc_kernel(const TcArgs a)
 {
     using C = Cfg<R>;
+    constexpr int NGEN = M * GPR;
+    constexpr int SRC_OFF = A_STAGES * 2 * C::A_BYTES;
+    constexpr int BAR_OFF = SRC_OFF + SS * C::CHUNK_BYTES;
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *src_full = reinterpret_cast<uint64_t *>(smem + C::BAR_OFF);   // [SRC_STAGES]
-    uint64_t *mma_done = src_full + SRC_STAGES;                             // [A_STAGES]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + A_STAGES);
-    const int th = threadIdx.x, warp = th >> 5;
-    const int row = th & (M - 1), half = th >> 7;
+    uint64_t *src_full = reinterpret_cast<uint64_t *>(smem + BAR_OFF);  // [SS]
+    uint64_t *a_full = src_full + SS;                                   // [A_STAGES]
+    uint64_t *mma_done = a_full + A_STAGES;                             // [A_STAGES]
+    uint64_t *acc_full = mma_done + A_STAGES;
+    uint64_t *acc_empty = acc_full + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int th = threadIdx.x, warp = th >> 5, lane = th & 31;
 
     const int64_t items = a.n_tiles * a.n_segs;
     const int64_t ibeg = items * blockIdx.x / gridDim.x;
@@ -277,8 +313,14 @@ __global__ void __launch_bounds__(NTHR) far_tc_kernel(const TcArgs a)
     if (ibeg >= iend) return;
 
     if (th == 0) {
-        for (int s = 0; s < SRC_STAGES; ++s) mbar_init(smem_addr(&src_full[s]), 1);
-        for (int s = 0; s < A_STAGES; ++s) mbar_init(smem_addr(&mma_done[s]), 1);
+        for (int s = 0; s < SS; ++s) mbar_init(smem_addr(&src_full[s]), 1);
+        for (int s = 0; s < A_STAGES; ++s) {
+            mbar_init(smem_addr(&a_full[s]), NGEN);
+            mbar_init(smem_addr(&mma_done[s]), 1);
+        }
+        mbar_init(smem_addr(acc_full), 1);
+        mbar_init(smem_addr(acc_empty), NGEN);
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(smem_addr(tmem_slot), C::TMEM_COLS);
@@ -286,133 +328,185 @@ __global__ void __launch_bounds__(NTHR) far_tc_kernel(const TcArgs a)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    constexpr uint32_t idesc = idesc_bf16(M, C::N);
 
-    // chunk counter n over this CTA's items: item = ibeg + (n / chunks per item) is not uniform
-    // (the last segment of a row of tiles is shorter), so walk items explicitly.
-    auto seg_chunks = [&](int64_t item) {
-        const int64_t sg = item % a.n_segs;
-        return (int)min((int64_t)SEG_CHUNKS, a.n_chunks - sg * SEG_CHUNKS);
-    };
-    auto chunk_index = [&](int64_t item, int c) { return (item % a.n_segs) * SEG_CHUNKS + c; };
+    // kernel parameters in registers (no reference to the parameter block)
+    const int64_t n_segs = a.n_segs, n_chunks = a.n_chunks, nq = a.nq;
+    const unsigned char *panel = a.panel;
+    const float ks = a.ks;
 
-    // producer cursor (thread 0): next (item, chunk) whose panel to fetch
-    int64_t p_item = ibeg;
-    int p_c = 0;
-    int64_t issued = 0;  // chunks issued so far
-    auto issue_next = [&]() {
-        if (p_item >= iend) return;
-        const int s = (int)(issued % SRC_STAGES);
-        const uint32_t bar = smem_addr(&src_full[s]);
-        mbar_expect_tx(bar, C::CHUNK_BYTES);
-        bulk_g2s(smem_addr(smem + C::SRC_OFF + s * C::CHUNK_BYTES),
-                 a.panel + chunk_index(p_item, p_c) * (int64_t)C::CHUNK_BYTES, C::CHUNK_BYTES, bar);
-        ++issued;
-        if (++p_c == seg_chunks(p_item)) {
-            p_c = 0;
-            ++p_item;
-        }
-    };
-    if (th == 0) {
-        issue_next();
-        issue_next();
-    }
-
-    bool failed = false;
-    int64_t n = 0;  // chunks consumed
-    for (int64_t item = ibeg; item < iend && !failed; ++item) {
-        const int64_t tile = item / a.n_segs;
-        const int64_t t0 = tile * M;
-        const int64_t tgt = t0 + row;
-        const float4 p = a.tgt[min(tgt, a.nq - 1)];
-        const float2 tx = make_float2(p.x * a.ks, p.x * a.ks);
-        const float2 ty = make_float2(p.y * a.ks, p.y * a.ks);
-        const float2 tz = make_float2(p.z * a.ks, p.z * a.ks);
-        const int nc = seg_chunks(item);
-        for (int c = 0; c < nc; ++c, ++n) {
-            const int sa = (int)(n % A_STAGES), ss = (int)(n % SRC_STAGES);
+    if (warp == NGEN / 32) {
+        // ------------------------------------------------------------ control warp
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(M, C::N);
+            // copy producer: item, chunk within it, chunks in it
+            int64_t p_item = ibeg;
+            int64_t p_seg = p_item % n_segs;
+            int p_c = 0;
+            int p_nc = (int)min((int64_t)SEG_CHUNKS, n_chunks - p_seg * SEG_CHUNKS);
+            int issued = 0, c_stage = 0;
+            uint32_t c_par = 0;
+            int n = 0;  // chunks whose products were issued
+            int sa = 0, ss = 0;
+            uint32_t pa = 0, ps = 0;
             bool ok = true;
-            if (n >= A_STAGES) ok = mbar_wait_bounded(smem_addr(&mma_done[sa]), (uint32_t)(((n - A_STAGES) / A_STAGES) & 1));
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-            tc_fence_after();
-            if (th == 0) issue_next();  // into the source stage freed by chunk n - 2
-            ok = mbar_wait_bounded(smem_addr(&src_full[ss]), (uint32_t)((n / SRC_STAGES) & 1));
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-            const unsigned char *src = smem + C::SRC_OFF + ss * C::CHUNK_BYTES;
-            unsigned char *a_hi = smem + C::A_OFF + sa * 2 * C::A_BYTES;
-            unsigned char *a_lo = a_hi + C::A_BYTES;
-            const int64_t gchunk = chunk_index(item, c);
-            const int64_t src0 = gchunk * KS;
-            if (t0 < src0 + KS && src0 < t0 + M)
-                gen_chunk<R, true>(src, a_hi, a_lo, tx, ty, tz, tgt, src0, row, half);
-            else
-                gen_chunk<R, false>(src, a_hi, a_lo, tx, ty, tz, tgt, src0, row, half);
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-            if (th == 0) {
-                tc_fence_after();
-                const uint32_t ah = smem_addr(a_hi), al = smem_addr(a_lo);
-                const uint32_t bh = smem_addr(src + POS_BYTES), bl = bh + C::B_BYTES;
+            for (int64_t item = ibeg; item < iend && ok; ++item) {
+                const int64_t seg = item % n_segs;
+                const int nc = (int)min((int64_t)SEG_CHUNKS, n_chunks - seg * SEG_CHUNKS);
+                if (item > ibeg) ok = wait_or_abort(smem_addr(acc_empty), (uint32_t)((item - ibeg - 1) & 1), abort);
+                for (int c = 0; c < nc && ok; ++c) {
+                    // copies run up to SS - 1 chunks ahead; a copy stage is free once the
+                    // products of the chunk that used it (SS chunks earlier) finished
+                    while (p_item < iend && issued < n + SS) {
+                        if (issued >= SS) {
+                            const int prev = issued - SS;  // last user of this copy stage
+                            if (prev >= n) break;         // its products are not issued yet
+                            ok = wait_or_abort(smem_addr(&mma_done[prev % A_STAGES]),
+                                               (uint32_t)((prev / A_STAGES) & 1), abort);
+                            if (!ok) break;
+                        }
+                        const uint32_t bar = smem_addr(&src_full[c_stage]);
+                        mbar_expect_tx(bar, C::CHUNK_BYTES);
+                        bulk_g2s(smem_addr(smem + SRC_OFF + c_stage * C::CHUNK_BYTES),
+                                 panel + (p_seg * SEG_CHUNKS + p_c) * (int64_t)C::CHUNK_BYTES, C::CHUNK_BYTES, bar);
+                        ++issued;
+                        if (++c_stage == SS) {
+                            c_stage = 0;
+                            c_par ^= 1;
+                        }
+                        if (++p_c == p_nc) {
+                            p_c = 0;
+                            if (++p_item < iend) {
+                                p_seg = p_item % n_segs;
+                                p_nc = (int)min((int64_t)SEG_CHUNKS, n_chunks - p_seg * SEG_CHUNKS);
+                            }
+                        }
+                    }
+                    if (!ok) break;
+                    ok = wait_or_abort(smem_addr(&a_full[sa]), pa, abort) &&
+                         wait_or_abort(smem_addr(&src_full[ss]), ps, abort);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t ah = smem_addr(smem + sa * 2 * C::A_BYTES), al = ah + C::A_BYTES;
+                    const uint32_t bh = smem_addr(smem + SRC_OFF + ss * C::CHUNK_BYTES + POS_BYTES);
+                    const uint32_t bl = bh + C::B_BYTES;
 #pragma unroll
-                for (int ks = 0; ks < KC / 16; ++ks) {
-                    const uint32_t off = ks * 2 * CORE_LBO;
-                    const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-                    mma_bf16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc0);
-                    mma_bf16(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
-                    mma_bf16(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+                    for (int kk = 0; kk < KC / 16; ++kk) {
+                        const uint32_t off = kk * 2 * CORE_LBO;
+                        const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
+                        mma_bf16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc0);
+                        mma_bf16(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
+                        mma_bf16(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+                    }
+                    mma_commit(smem_addr(&mma_done[sa]));
+                    if (c == nc - 1) mma_commit(smem_addr(acc_full));
+                    ++n;
+                    if (++sa == A_STAGES) {
+                        sa = 0;
+                        pa ^= 1;
+                    }
+                    if (++ss == SS) {
+                        ss = 0;
+                        ps ^= 1;
+                    }
                 }
-                mma_commit(smem_addr(&mma_done[sa]));
+            }
+            if (!ok) {
+                atomicExch(a.err, 1);
+                *abort = 1;
+            }
+            // drain: copies and products in flight must land before the CTA exits
+            for (int j = n; j < issued; ++j)
+                mbar_wait_bounded(smem_addr(&src_full[j % SS]), (uint32_t)((j / SS) & 1));
+            if (n > 0) {
+                const int nl = n - 1;
+                mbar_wait_bounded(smem_addr(&mma_done[nl % A_STAGES]), (uint32_t)((nl / A_STAGES) & 1));
             }
         }
-        if (failed) break;
-        // epilogue of this item: wait for its last MMAs, read the accumulator
-        const int64_t nl = n - 1;
-        const bool ok = mbar_wait_bounded(smem_addr(&mma_done[nl % A_STAGES]), (uint32_t)((nl / A_STAGES) & 1));
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        tc_fence_after();
-        {
-            const int quad = warp & 3, colh = warp >> 2;
-            const int64_t trow = t0 + quad * 32 + (th & 31);
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ generator warps
+        const int row = th & (M - 1), slice = th / M;
+        int n = 0, sa = 0, ss = 0;
+        uint32_t pa = 0, ps = 0;  // parity of the current use of stage sa / ss
+        bool ok = true;
+        int64_t item_count = 0;
+        for (int64_t item = ibeg; item < iend && ok; ++item, ++item_count) {
+            const int64_t tile = item / n_segs;
+            const int64_t seg = item - tile * n_segs;
+            const int64_t t0 = tile * M;
+            const int64_t tgt = t0 + row;
+            const float4 p = a.tgt[min(tgt, nq - 1)];
+            const float2 tx = make_float2(p.x * ks, p.x * ks);
+            const float2 ty = make_float2(p.y * ks, p.y * ks);
+            const float2 tz = make_float2(p.z * ks, p.z * ks);
+            const int nc = (int)min((int64_t)SEG_CHUNKS, n_chunks - seg * SEG_CHUNKS);
+            int64_t src0 = seg * SEG_CHUNKS * KS;
+            for (int c = 0; c < nc; ++c, ++n, src0 += KS) {
+                if (n >= A_STAGES) ok = wait_or_abort(smem_addr(&mma_done[sa]), pa ^ 1u, abort);
+                ok = ok && wait_or_abort(smem_addr(&src_full[ss]), ps, abort);
+                if (!ok) break;
+                const unsigned char *src = smem + SRC_OFF + ss * C::CHUNK_BYTES;
+                unsigned char *a_hi = smem + sa * 2 * C::A_BYTES;
+                unsigned char *a_lo = a_hi + C::A_BYTES;
+                if (t0 < src0 + KS && src0 < t0 + M)
+                    gen_chunk<GPR, true>(src, a_hi, a_lo, tx, ty, tz, tgt, src0, row, slice);
+                else
+                    gen_chunk<GPR, false>(src, a_hi, a_lo, tx, ty, tz, tgt, src0, row, slice);
+                fence_async_smem();
+                mbar_arrive(smem_addr(&a_full[sa]));
+                if (++sa == A_STAGES) {
+                    sa = 0;
+                    pa ^= 1;
+                }
+                if (++ss == SS) {
+                    ss = 0;
+                    ps ^= 1;
+                }
+            }
+            if (!ok) break;
+            // epilogue: this item's accumulator
+            ok = wait_or_abort(smem_addr(acc_full), (uint32_t)(item_count & 1), abort);
+            if (!ok) break;
+            tc_fence_after();
+            constexpr int GROUPS = NGEN / 32 / 4;      // warps sharing one lane quadrant
+            constexpr int COLS = C::N / GROUPS;        // accumulator columns per warp
+            const int quad = warp & 3, grp = warp >> 2;
+            const int64_t trow = t0 + quad * 32 + lane;
+            constexpr int LD = COLS >= 16 ? 16 : 8;  // columns per tcgen05.ld
+            static_assert(COLS % LD == 0, "accumulator columns per warp");
 #pragma unroll
-            for (int cb = 0; cb < R / 16; ++cb) {
+            for (int cb = 0; cb < COLS / LD; ++cb) {
                 uint32_t r[16];
-                const int col0 = colh * R + cb * 16;
-                tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col0, r);
-                tmem_ld_wait();
-                if (trow < a.nq) {
+                const int col0 = grp * COLS + cb * LD;
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col0;
+                if (LD == 16) {
+                    tmem_ld16(taddr, r);
+                } else {
+                    uint32_t r8[8];
+                    tmem_ld8(taddr, r8);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int jj = cb * 16 + i;  // right-hand side within the pass
+                    for (int i = 0; i < 8; ++i) r[i] = r8[i];
+                }
+                tmem_ld_wait();
+                if (trow < nq) {
+#pragma unroll
+                    for (int i = 0; i < LD; ++i) {
+                        const int col = col0 + i;
+                        const int part = col >= R ? 1 : 0;  // Re columns first, then Im
+                        const int jj = col - part * R;
                         if (jj < a.ncols) {
-                            double *dst = reinterpret_cast<double *>(a.v + trow + (int64_t)jj * a.ldv) + colh;
-                            atomicAdd(dst, (double)__uint_as_float(r[i]) * (double)a.ks);
+                            double *dst = reinterpret_cast<double *>(a.v + trow + (int64_t)jj * a.ldv) + part;
+                            atomicAdd(dst, (double)__uint_as_float(r[i]) * (double)ks);
                         }
                     }
                 }
             }
+            tc_fence_before();
+            mbar_arrive(smem_addr(acc_empty));
         }
-        tc_fence_before();
-        __syncthreads();  // every warp has read the accumulator before the next item overwrites it
-        tc_fence_after();
-    }
-    if (failed && th == 0) {
-        atomicExch(a.err, 1);
-        // let the copies and products in flight finish before shared and tensor memory go away
-        for (int64_t j = n; j < issued; ++j)
-            mbar_wait_bounded(smem_addr(&src_full[j % SRC_STAGES]), (uint32_t)((j / SRC_STAGES) & 1));
-        if (n > 0) {
-            const int64_t nl = n - 1;
-            mbar_wait_bounded(smem_addr(&mma_done[nl % A_STAGES]), (uint32_t)((nl / A_STAGES) & 1));
+        if (!ok) {
+            atomicExch(a.err, 1);
+            *abort = 1;
         }
     }
     tc_fence_before();
@@ -423,6 +517,37 @@ __global__ void __launch_bounds__(NTHR) far_tc_kernel(const TcArgs a)
     }
 }
 
+template <int R, int GPR, int SS, int A_STAGES>
+gyps_status run_pass_cfg(Mesh *m, const TcArgs &a0, int64_t n_chunks, const double2 *X, int64_t ldx, int nrhs,
+                         double2 *v, cudaStream_t s, unsigned char *panel)
+{
+    using C = Cfg<R>;
+    constexpr int SMEM = A_STAGES * 2 * C::A_BYTES + SS * C::CHUNK_BYTES + 128;
+    constexpr int NT = M * GPR + 32;
+    GYPS_CUDA(cudaFuncSetAttribute(far_tc_kernel<R, GPR, SS, A_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+    int occ = 0;
+    GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, far_tc_kernel<R, GPR, SS, A_STAGES>, NT, SMEM));
+    occ = std::max(occ, 1);
+    TcArgs a = a0;
+    const int64_t items = a.n_tiles * a.n_segs;
+    const int64_t grid = std::min<int64_t>((int64_t)m->num_sms * occ, items);
+    for (int c0 = 0; c0 < nrhs; c0 += R) {
+        StageTimer ti(m, s, 0);
+        dim3 gi((unsigned)((n_chunks * KS + 255) / 256), (unsigned)R);
+        tc_interp_kernel<R><<<gi, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, n_chunks * KS, X, ldx, c0, nrhs,
+                                                a.ks, m->pad, panel);
+        GYPS_CUDA(cudaGetLastError());
+        ti.done(1);
+        a.v = v + (int64_t)c0 * a.ldv;
+        a.ncols = std::min(R, nrhs - c0);
+        StageTimer tf(m, s, 1);
+        far_tc_kernel<R, GPR, SS, A_STAGES><<<(unsigned)grid, NT, SMEM, s>>>(a);
+        GYPS_CUDA(cudaGetLastError());
+        tf.done(1);
+    }
+    return GYPS_OK;
+}
+
 template <int R>
 gyps_status run(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, double2 *v, int64_t ldv, cudaStream_t s)
 {
@@ -431,38 +556,20 @@ gyps_status run(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, doub
     const size_t panel_bytes = (size_t)n_chunks * C::CHUNK_BYTES;
     GYPS_TRY(grow(m, &m->ws_tc, &m->ws_tc_bytes, panel_bytes));
     unsigned char *panel = reinterpret_cast<unsigned char *>(m->ws_tc);
-    const float ks = (float)k;
-    GYPS_CUDA(cudaFuncSetAttribute(far_tc_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    int occ = 0;
-    GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, far_tc_kernel<R>, NTHR, C::SMEM));
-    occ = std::max(occ, 1);
     TcArgs a;
     a.panel = panel;
     a.tgt = m->d_pts32;
+    a.v = v;
     a.ldv = ldv;
     a.nq = m->nq;
     a.n_chunks = n_chunks;
     a.n_tiles = (m->nq + M - 1) / M;
     a.n_segs = (n_chunks + SEG_CHUNKS - 1) / SEG_CHUNKS;
-    a.ks = ks;
+    a.ncols = 0;
+    a.ks = (float)k;
     a.err = m->d_err;
-    const int64_t items = a.n_tiles * a.n_segs;
-    const int64_t grid = std::min<int64_t>((int64_t)m->num_sms * occ, items);
-    for (int c0 = 0; c0 < nrhs; c0 += R) {
-        StageTimer ti(m, s, 0);
-        dim3 gi((unsigned)((n_chunks * KS + 255) / 256), (unsigned)R);
-        tc_interp_kernel<R><<<gi, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, n_chunks * KS, X, ldx, c0, nrhs,
-                                                ks, m->pad, panel);
-        GYPS_CUDA(cudaGetLastError());
-        ti.done(1);
-        a.v = v + (int64_t)c0 * ldv;
-        a.ncols = std::min(R, nrhs - c0);
-        StageTimer tf(m, s, 1);
-        far_tc_kernel<R><<<(unsigned)grid, NTHR, C::SMEM, s>>>(a);
-        GYPS_CUDA(cudaGetLastError());
-        tf.done(1);
-    }
-    return GYPS_OK;
+    // four generator threads per target row (16 generator warps), copy stages as shared memory allows
+    return run_pass_cfg<R, 4, (R == 16 ? 4 : 3), 4>(m, a, n_chunks, X, ldx, nrhs, v, s, panel);
 }
 
 }  // namespace tc
@@ -470,6 +577,14 @@ gyps_status run(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, doub
 gyps_status far_tc(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, double2 *v, int64_t ldv,
                    cudaStream_t s)
 {
+    // widest pass that the right-hand sides fill: every pass regenerates the kernel tiles
+    if (nrhs >= 64) {
+        const int full = nrhs / 64 * 64;
+        GYPS_TRY(tc::run<64>(m, k, X, ldx, full, v, ldv, s));
+        if (full == nrhs) return GYPS_OK;
+        return far_tc(m, k, X + (int64_t)full * ldx, ldx, nrhs - full, v + (int64_t)full * ldv, ldv, s);
+    }
+    if (nrhs > 16) return tc::run<32>(m, k, X, ldx, nrhs, v, ldv, s);
     return tc::run<16>(m, k, X, ldx, nrhs, v, ldv, s);
 }
 

@@ -73,3 +73,23 @@ def test_batch_rejects_host_buffers():
     arr[0] = g._BatchItem(m.handle.value, 1.0, xh.ctypes.data, m.nv, xh.ctypes.data, m.nv)
     h = ctypes.c_void_p()
     assert g.load().gyps_batch_create(arr, 1, 1, 0, None, ctypes.byref(h)) == 1
+
+
+def test_batch_tensor_core_mode():
+    """>= 16 right-hand sides and every k > 0: the default form is the
+    tensor-core apply of each mesh (tolerance of the split bf16 products)."""
+    import paper_1804_00995_gb300 as g
+    specs = [s for s in small_batch() if s[3] > 0.0]
+    meshes = [g.Mesh(v, t, q) for v, t, q, _ in specs]
+    b = g.Batch([(m, k) for m, (_, _, _, k) in zip(meshes, specs)], 16)
+    assert b.info["tensor_cores"] == 1
+    xs = []
+    for i, m in enumerate(meshes):
+        x = synth.random_complex(np.random.default_rng(40 + i), m.nv, 16)
+        b.X[i].copy_(torch.as_tensor(x))
+        xs.append(x)
+    ys = b.apply()
+    torch.cuda.synchronize()
+    for i, (v, t, q, k) in enumerate(specs):
+        assert rel(ys[i].cpu().numpy(), oracle.Mesh(v, t, q).apply(k, xs[i])) < 1e-4
+    b.close()
