@@ -61,6 +61,7 @@ typedef enum {
 #define GYPS_APPLY_NO_NEAR 0x1u /* far part (1/4pi) Phi^T W G W Phi only, no correction C */
 
 typedef struct gyps_mesh_s *gyps_mesh_t;
+typedef struct gyps_precond_s *gyps_precond_t;
 
 typedef struct {
     int64_t nv;          /* vertices = P1 degrees of freedom */
@@ -176,6 +177,7 @@ typedef struct {
     int32_t check_prec;  /* gyps_prec of the true-residual check (GYPS_PREC_FP64 normally) */
     int32_t use_x0;      /* 1: X holds the initial guess on entry; 0: start from zero */
     int32_t max_refine;  /* refinement sweeps when the check exceeds tol (0 = none) */
+    gyps_precond_t precond; /* NULL, or a learned preconditioner: flexible GMRES with z = M(q) */
 } gyps_gmres_opts;
 
 /* GMRES report, HOST.  Arrays are caller-owned, length nrhs, may be NULL. */
@@ -184,6 +186,8 @@ typedef struct {
     int32_t applies;         /* operator applies in the working precision */
     int32_t check_applies;   /* applies in check_prec */
     int32_t refinements;     /* refinement sweeps done */
+    int32_t precond_fallback;/* 1 when the preconditioner was dropped (non-finite output or a
+                                full cycle that did not halve the residual) */
     double *est_residual;    /* last Arnoldi residual estimate per column (relative) */
     double *true_residual;   /* ||F - V X||/||F|| with check_prec, per column */
     int32_t *converged;      /* 1 where true_residual <= tol */
@@ -198,6 +202,12 @@ typedef struct {
  * above tol and refinements remain, GMRES is run on the residual equation
  * and the correction added (mixed-precision iterative refinement).
  *   F, X  nv x nrhs complex double2 (device or host).  report: HOST or NULL.
+ * With opts->precond set, the Krylov loop is flexible GMRES: each basis vector
+ * q_j is mapped by the learned preconditioner, z_j = M(q_j), the operator is
+ * applied to z_j and the update is X += Z y.  A non-finite z_j, or a full
+ * cycle that does not halve the residual of any column, drops the
+ * preconditioner for the rest of the solve (unpreconditioned GMRES from the
+ * current iterate) and the report says so.  The check-precision residual judges the result either way.
  * Returns NOT_CONVERGED (X = last iterate) when a column misses tol, NAN
  * when a non-finite value appears.
  */
@@ -291,6 +301,51 @@ gyps_status gyps_batch_destroy(gyps_batch_t batch);
  */
 gyps_status gyps_sl_apply_noalloc(gyps_mesh_t mesh, double k, int nrhs, const void *X, int64_t ldx,
                                   void *Y, int64_t ldy, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Learned preconditioner (no counterpart in the paper): a message-passing
+ * network on the P1 mesh graph mapping a residual r to z ~ V^{-1} r, for
+ * flexible GMRES.  Per vertex i the inputs are r_i / rms(r) (re, im), the
+ * centred and scaled coordinates, the unit vertex normal and k h (h: mean edge
+ * length); h0 = relu(W_in f + b_in); `layers` times
+ * h += relu(Ws h + Wn mean_{j ~ i} h_j + b); y = W_out h + b_out (2 values);
+ * z_i = (y_i0 + i y_i1) rms(r) / h^3.  bf16 weights in the forward, FP32
+ * activations and sums, FP32 master weights and Adam moments.
+ * ------------------------------------------------------------------------ */
+
+/* hidden must be 64; layers 1..16; weights from a counter-based generator
+ * seeded by `seed` (uniform, scaled by 1/sqrt(fan in)), biases zero. */
+gyps_status gyps_precond_create(int hidden, int layers, uint64_t seed, gyps_precond_t *out);
+gyps_status gyps_precond_destroy(gyps_precond_t p);
+
+/* Size and Adam step count of the network. Any output pointer may be NULL. */
+gyps_status gyps_precond_info(gyps_precond_t p, int *hidden, int *layers, int64_t *nparams, int64_t *steps);
+
+/* Copies the FP32 parameters out of (direction 0) or into (direction 1) the
+ * network; host buffer of gyps_precond_info's nparams floats, in the order
+ * W_in (9 x H), b_in, per layer Ws (H x H), Wn (H x H), b (H), W_out (H x 2),
+ * b_out (2); matrices input-major. */
+gyps_status gyps_precond_params(gyps_precond_t p, float *host, int64_t n, int direction);
+
+/* Z = M(R) for nrhs residuals of one mesh.  R, Z: DEVICE, nv x nrhs complex
+ * double2.  Asynchronous on stream. */
+gyps_status gyps_precond_apply(gyps_precond_t p, gyps_mesh_t mesh, double k, int nrhs, const void *R, int64_t ldr,
+                               void *Z, int64_t ldz, void *stream);
+
+/* One minibatch of training: nrhs (1..64) residuals R of one mesh and their
+ * corrections E (E ~ V^{-1} R), loss = mean over columns of |M(r)-e|^2/|e|^2.
+ * Computes the gradient; with lr > 0 takes one Adam step (beta 0.9, 0.999,
+ * eps 1e-8).  loss (HOST, may be NULL) receives the loss before the step,
+ * grad (HOST, nparams floats, may be NULL) the gradient.  R, E: device or host.
+ * Synchronous. */
+gyps_status gyps_precond_train_step(gyps_precond_t p, gyps_mesh_t mesh, double k, int nrhs, const void *R,
+                                    int64_t ldr, const void *E, int64_t lde, double lr, double *loss,
+                                    float *grad, void *stream);
+
+/* Checkpoint: parameters and Adam moments with a JSON header (format
+ * "gyps-mpnn-1").  load checks the shape and rejects non-finite values. */
+gyps_status gyps_precond_save(gyps_precond_t p, const char *path);
+gyps_status gyps_precond_load(gyps_precond_t p, const char *path);
 
 /* Device-time profile of the matrix-free applies of one mesh. */
 typedef struct {

@@ -67,12 +67,13 @@ class _BatchInfo(ctypes.Structure):
 class _GmresOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("check_prec", ctypes.c_int32), ("use_x0", ctypes.c_int32),
-                ("max_refine", ctypes.c_int32)]
+                ("max_refine", ctypes.c_int32), ("precond", ctypes.c_void_p)]
 
 
 class _GmresReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("applies", ctypes.c_int32), ("check_applies", ctypes.c_int32),
-                ("refinements", ctypes.c_int32), ("est_residual", ctypes.POINTER(ctypes.c_double)),
+                ("refinements", ctypes.c_int32), ("precond_fallback", ctypes.c_int32),
+                ("est_residual", ctypes.POINTER(ctypes.c_double)),
                 ("true_residual", ctypes.POINTER(ctypes.c_double)), ("converged", ctypes.POINTER(ctypes.c_int32))]
 
 
@@ -107,6 +108,19 @@ _SIGS = {
     "gyps_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "gyps_sl_apply_noalloc": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
+    "gyps_precond_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)],
+                            ctypes.c_int),
+    "gyps_precond_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "gyps_precond_info": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "gyps_precond_params": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
+    "gyps_precond_apply": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
+    "gyps_precond_train_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "gyps_precond_save": ([ctypes.c_void_p, ctypes.c_char_p], ctypes.c_int),
+    "gyps_precond_load": ([ctypes.c_void_p, ctypes.c_char_p], ctypes.c_int),
     "gyps_profile_enable": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "gyps_profile_read": ([ctypes.c_void_p, ctypes.POINTER(_Profile)], ctypes.c_int),
 }
@@ -346,12 +360,81 @@ class Batch:
             pass
 
 
+class Precond:
+    """Learned message-passing preconditioner (gyps_precond_*): z = M(r) ~ V^{-1} r."""
+
+    def __init__(self, hidden: int = 64, layers: int = 4, seed: int = 995):
+        h = ctypes.c_void_p()
+        _check(load().gyps_precond_create(int(hidden), int(layers), int(seed), ctypes.byref(h)))
+        self._h = h
+        hid, lay, npar, steps = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().gyps_precond_info(self._h, ctypes.byref(hid), ctypes.byref(lay), ctypes.byref(npar),
+                                        ctypes.byref(steps)))
+        self.hidden, self.layers, self.nparams = hid.value, lay.value, npar.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def steps(self) -> int:
+        s = ctypes.c_int64()
+        _check(load().gyps_precond_info(self._h, None, None, None, ctypes.byref(s)))
+        return s.value
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.nparams, dtype=np.float32)
+        _check(load().gyps_precond_params(self._h, out.ctypes.data, self.nparams, 0))
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        _check(load().gyps_precond_params(self._h, p.ctypes.data, p.size, 1))
+
+    def apply(self, mesh: "Mesh", k: float, R, stream=None):
+        r, nrhs, ldr = _colmajor(R, mesh.nv, "R")
+        z = _empty_colmajor(mesh.nv, nrhs, r.device)
+        _check(load().gyps_precond_apply(self._h, mesh.handle, float(k), nrhs, r.data_ptr(), ldr, z.data_ptr(),
+                                         mesh.nv, _stream(stream)))
+        return z
+
+    def train_step(self, mesh: "Mesh", k: float, R, E, lr: float, want_grad: bool = False, stream=None):
+        """Loss (and gradient) on the minibatch; one Adam step when lr > 0."""
+        r, nrhs, ldr = _colmajor(R, mesh.nv, "R")
+        e, nrhs_e, lde = _colmajor(E, mesh.nv, "E")
+        if nrhs_e != nrhs:
+            raise ValueError("R and E must have the same number of columns")
+        loss = ctypes.c_double()
+        grad = np.zeros(self.nparams, dtype=np.float32) if want_grad else None
+        _check(load().gyps_precond_train_step(self._h, mesh.handle, float(k), nrhs, r.data_ptr(), ldr, e.data_ptr(),
+                                              lde, float(lr), ctypes.byref(loss),
+                                              grad.ctypes.data if grad is not None else None, _stream(stream)))
+        return (loss.value, grad) if want_grad else loss.value
+
+    def save(self, path: str) -> None:
+        _check(load().gyps_precond_save(self._h, str(path).encode()))
+
+    def load(self, path: str) -> None:
+        _check(load().gyps_precond_load(self._h, str(path).encode()))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.gyps_precond_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 @dataclass
 class GmresReport:
     iterations: int
     applies: int
     check_applies: int
     refinements: int
+    precond_fallback: int
     est_residual: np.ndarray
     true_residual: np.ndarray
     converged: np.ndarray
@@ -360,7 +443,7 @@ class GmresReport:
 
 def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, maxit: int = 1000,
                 prec: str = "fp32", check_prec: str = "fp64", x0=None, max_refine: int = 3, raise_on_fail=False,
-                stream=None):
+                precond: "Precond" = None, stream=None):
     """Solves V X = F (gyps_gmres_solve).  Returns (X, GmresReport)."""
     f, nrhs, ldf = _colmajor(F, mesh.nv, "F")
     if x0 is not None:
@@ -371,17 +454,17 @@ def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, 
     else:
         x = _empty_colmajor(mesh.nv, nrhs, f.device)
     opts = _GmresOpts(float(tol), int(restart), int(maxit), PREC[prec], PREC[check_prec], 1 if x0 is not None else 0,
-                      int(max_refine))
+                      int(max_refine), precond.handle.value if precond is not None else None)
     est = np.zeros(nrhs)
     tru = np.zeros(nrhs)
     conv = np.zeros(nrhs, dtype=np.int32)
-    rep = _GmresReport(0, 0, 0, 0, est.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+    rep = _GmresReport(0, 0, 0, 0, 0, est.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                        tru.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                        conv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     code = load().gyps_gmres_solve(mesh.handle, float(k), nrhs, f.data_ptr(), ldf, x.data_ptr(), mesh.nv,
                                    ctypes.byref(opts), ctypes.byref(rep), _stream(stream))
     if code not in (0, 4) or (code == 4 and raise_on_fail):
         _check(code)
-    report = GmresReport(rep.iterations, rep.applies, rep.check_applies, rep.refinements, est, tru, conv.astype(bool),
-                         _STATUS[code])
+    report = GmresReport(rep.iterations, rep.applies, rep.check_applies, rep.refinements, rep.precond_fallback, est,
+                         tru, conv.astype(bool), _STATUS[code])
     return (x[:, 0] if (hasattr(F, "dim") and F.dim() == 1) else x), report

@@ -150,6 +150,7 @@ struct Work {
     double2 *W = nullptr;    // nv x nrhs
     double2 *R = nullptr;    // nv x nrhs
     double2 *D = nullptr;    // nv x nrhs (refinement correction)
+    double2 *Z = nullptr;    // m blocks of nv x nrhs: preconditioned basis (flexible GMRES)
     double2 *h = nullptr;    // (m + 1) x nrhs
     double *nrm = nullptr;   // nrhs
     double *scl = nullptr;   // nrhs
@@ -161,6 +162,7 @@ struct Work {
         cudaFree(W);
         cudaFree(R);
         cudaFree(D);
+        cudaFree(Z);
         cudaFree(h);
         cudaFree(nrm);
         cudaFree(scl);
@@ -177,6 +179,27 @@ struct Solver {
     Work w;
     int64_t nv;
     int iters = 0, applies = 0, check_applies = 0;
+    gyps_precond_t P = nullptr;  // learned preconditioner (flexible GMRES) while pre_on
+    bool pre_on = false;
+    int fallback = 0;
+
+    // Column norms without the non-finite check (the preconditioned cycle
+    // handles a non-finite value by dropping the preconditioner).
+    gyps_status norms_raw(const double2 *A, std::vector<double> &out, bool *finite)
+    {
+        GYPS_CUDA(cudaMemsetAsync(w.nrm, 0, nrhs * sizeof(double), s));
+        znorm2_kernel<<<grid_r, 256, 0, s>>>(A, nv, w.nrm);
+        GYPS_CUDA(cudaGetLastError());
+        GYPS_CUDA(cudaMemcpyAsync(w.hn, w.nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GYPS_CUDA(cudaStreamSynchronize(s));
+        out.resize(nrhs);
+        *finite = true;
+        for (int c = 0; c < nrhs; ++c) {
+            out[c] = std::sqrt(w.hn[c]);
+            *finite = *finite && std::isfinite(out[c]);
+        }
+        return GYPS_OK;
+    }
     dim3 grid_v, grid_r;
 
     gyps_status norms(const double2 *A, std::vector<double> &out)
@@ -252,10 +275,27 @@ struct Solver {
             }
             int j = 0;
             bool cycle_converged = false;  // every column reached tol by its Arnoldi estimate
+            bool dropped = false;          // preconditioner dropped inside this cycle
+            const bool cycle_pre = pre_on;
             for (; j < m && budget > 0; ++j) {
                 double2 *qj = w.Q + (size_t)j * nv * nrhs;
                 double2 *qn = w.Q + (size_t)(j + 1) * nv * nrhs;
-                GYPS_TRY(apply_device(this->m, k, nrhs, qj, nv, w.W, nv, prec, 0, 0, this->m->nt, s));
+                const double2 *vin = qj;
+                if (pre_on) {  // flexible GMRES: z_j = M(q_j), w = V z_j
+                    double2 *zj = w.Z + (size_t)j * nv * nrhs;
+                    GYPS_TRY(precond_apply_device(P, this->m, k, nrhs, qj, nv, zj, nv, s));
+                    std::vector<double> zn;
+                    bool zfinite = true;
+                    GYPS_TRY(norms_raw(zj, zn, &zfinite));
+                    if (!zfinite) {  // the network produced a non-finite value: drop it, redo the cycle
+                        pre_on = false;
+                        fallback = 1;
+                        dropped = true;
+                        break;
+                    }
+                    vin = zj;
+                }
+                GYPS_TRY(apply_device(this->m, k, nrhs, vin, nv, w.W, nv, prec, 0, 0, this->m->nt, s));
                 ++applies;
                 ++iters;
                 --budget;
@@ -272,7 +312,18 @@ struct Solver {
                     for (size_t e = 0; e < (size_t)(j + 1) * nrhs; ++e) hsum[e] += cplx(w.hh[e].x, w.hh[e].y);
                 }
                 std::vector<double> hn;
-                GYPS_TRY(norms(w.W, hn));
+                if (pre_on) {
+                    bool finite = true;
+                    GYPS_TRY(norms_raw(w.W, hn, &finite));
+                    if (!finite) {  // the network produced a non-finite value: drop it, redo the cycle
+                        pre_on = false;
+                        fallback = 1;
+                        dropped = true;
+                        break;
+                    }
+                } else {
+                    GYPS_TRY(norms(w.W, hn));
+                }
                 std::vector<double> inv2(nrhs);
                 for (int c = 0; c < nrhs; ++c) inv2[c] = (active[c] && hn[c] > 0.0) ? 1.0 / hn[c] : 0.0;
                 GYPS_TRY(scale_into(w.W, inv2, qn));
@@ -311,7 +362,8 @@ struct Solver {
                     break;
                 }
             }
-            // y = H^{-1} g per column (upper triangular), X += Q y
+            if (dropped) continue;  // discard the cycle, restart from the current X without M
+            // y = H^{-1} g per column (upper triangular), X += Q y (or Z y, flexible)
             const int nvec = std::max(1, j);
             std::vector<double2> y((size_t)nvec * nrhs, make_double2(0.0, 0.0));
             for (int c = 0; c < nrhs; ++c) {
@@ -324,13 +376,21 @@ struct Solver {
                 for (int i = 0; i < jc[c]; ++i) y[(size_t)i * nrhs + c] = make_double2(yc[i].real(), yc[i].imag());
             }
             GYPS_CUDA(cudaMemcpyAsync(w.h, y.data(), y.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
-            zupdate_kernel<<<grid_v, 256, 0, s>>>(w.Q, nvec, w.h, nv, nrhs, X, ldx);
+            zupdate_kernel<<<grid_v, 256, 0, s>>>(cycle_pre ? w.Z : w.Q, nvec, w.h, nv, nrhs, X, ldx);
             GYPS_CUDA(cudaGetLastError());
             GYPS_CUDA(cudaStreamSynchronize(s));  // y leaves scope
             // The estimate decides: a residual recomputed with an FP32 operator
             // carries that operator's rounding and could never go below its
             // floor; the caller's check-precision residual judges the result.
             if (cycle_converged) return GYPS_OK;
+            if (cycle_pre) {  // a full preconditioned cycle that did not halve the residual: drop M
+                bool progress = false;
+                for (int c = 0; c < nrhs; ++c) progress = progress || (beta[c] > tol_abs[c] && est[c] < 0.5 * beta[c]);
+                if (!progress) {
+                    pre_on = false;
+                    fallback = 1;
+                }
+            }
         }
     }
 };
@@ -354,6 +414,11 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
     GYPS_CUDA(cudaMalloc((void **)&S.w.W, blk));
     GYPS_CUDA(cudaMalloc((void **)&S.w.R, blk));
     GYPS_CUDA(cudaMalloc((void **)&S.w.D, blk));
+    if (o.precond) {
+        GYPS_CUDA(cudaMalloc((void **)&S.w.Z, blk * o.restart));
+        S.P = o.precond;
+        S.pre_on = true;
+    }
     GYPS_CUDA(cudaMalloc((void **)&S.w.h, (size_t)(o.restart + 1) * nrhs * sizeof(double2)));
     GYPS_CUDA(cudaMalloc((void **)&S.w.nrm, nrhs * sizeof(double)));
     GYPS_CUDA(cudaMalloc((void **)&S.w.scl, nrhs * sizeof(double)));
@@ -421,6 +486,7 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
         rep->applies = S.applies;
         rep->check_applies = S.check_applies;
         rep->refinements = refinements;
+        rep->precond_fallback = S.fallback;
         for (int c = 0; c < nrhs; ++c) {
             double f = fn[c] > 0 ? fn[c] : 1.0;
             if (rep->est_residual) rep->est_residual[c] = est[c] / f;

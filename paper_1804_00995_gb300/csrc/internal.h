@@ -91,6 +91,10 @@ struct Mesh {
     void *ws_stage = nullptr; size_t ws_stage_bytes = 0;  // host<->device staging
     void *ws_tc = nullptr; size_t ws_tc_bytes = 0;        // tensor-core source panel
     float pad = 0.0f;                                     // distance of padding points
+    // mesh graph for the learned preconditioner (built on first use)
+    int32_t *d_adj_ptr = nullptr, *d_adj = nullptr;       // vertex neighbours over mesh edges
+    float *d_vfeat = nullptr;                             // nv x 6: centred coordinates, unit normal
+    double h_mean = 0.0;                                  // mean edge length
     int64_t device_bytes = 0;
     int num_sms = 0;
 
@@ -151,6 +155,10 @@ cudaError_t launch_near_spmv(const Mesh &m, int nrhs, const double2 *X, int64_t 
 gyps_status assemble_device(Mesh *m, double k, int prec, double2 *V, int64_t ldv, cudaStream_t s);
 gyps_status rhs_device(Mesh *m, double k, int nrhs, const double *dirs_host, double2 *F, int64_t ldf,
                        cudaStream_t s);
+
+// a11: learned preconditioner Z = M(R) (device pointers)
+gyps_status precond_apply_device(gyps_precond_t p, Mesh *m, double k, int nrhs, const double2 *R, int64_t ldr,
+                                 double2 *Z, int64_t ldz, cudaStream_t s);
 
 // a8
 gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t ldf, double2 *X, int64_t ldx,
