@@ -45,7 +45,8 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gyps", choices=["gyps", "reference"])
-    p.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch12_r64", "precond_ellipsoids"])
+    p.add_argument("--workload", default=WORKLOAD,
+                   choices=[WORKLOAD, "batch12_r64", "precond_ellipsoids", "sphere163842_k64_q3_r16"])
     p.add_argument("--precond-meshes", type=int, default=125, help="training meshes (16 solves each)")
     p.add_argument("--precond-steps", type=int, default=3000)
     p.add_argument("--precond-test", type=int, default=8)
@@ -458,8 +459,59 @@ def run_precond(args):
     print(json.dumps(line), flush=True)
 
 
+def run_large(args):
+    """Workload sphere163842_k64_q3_r16: icosphere with 327680 triangles,
+    q = 3 (983040 points), k = 64, 16 plane waves (directions seed 7); one step
+    = one tensor-core apply of all 16 columns (kernel products on tensor cores,
+    FP64 correction); inputs (983040 x 16 density panel) exceed L2."""
+    import torch
+
+    import paper_1804_00995_gb300 as g
+    from paper_1804_00995_gb300 import build as gb
+    gb.build()
+    cfg = synth.WORKLOADS["sphere163842_k64_q3_r16"]
+    v, t = synth.icosphere(cfg["level"])
+    mesh = g.Mesh(v, t, cfg["q"])
+    dirs = synth.plane_wave_dirs(np.random.default_rng(cfg["seed"]), cfg["ndirs"])
+    x = g.rhs_planewave(mesh, cfg["k"], dirs)
+    y = g.sl_apply(mesh, cfg["k"], x, prec=args.prec if args.prec != "fp32" else "tc_bf16x3")
+    prec = args.prec if args.prec != "fp32" else "tc_bf16x3"
+    for _ in range(args.warmup):
+        g.sl_apply(mesh, cfg["k"], x, prec=prec, out=y)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    mesh.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        g.sl_apply(mesh, cfg["k"], x, prec=prec, out=y)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    prof = mesh.profile_read()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    pairs = float(mesh.nq) ** 2
+    props = torch.cuda.get_device_properties(0)
+    peak = sm_peak_pairs(props.multi_processor_count, 2070.0) / 1e9
+    far_ms = prof["far_ms"] / max(prof["far_launches"], 1) * prof["far_launches"] / max(prof["applies"], 1)
+    line = {
+        "metric": "GPairs/s single-layer apply, 16 right-hand sides", "value": pairs / (ms * 1e-3) / 1e9,
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "dtype": "bf16x3+f32" if prec == "tc_bf16x3" else "f32", "data": "synthetic",
+        "pair_rhs_per_s": pairs * 16 / (ms * 1e-3),
+        "config": {"workload": "sphere163842_k64_q3_r16", "nv": mesh.nv, "nq": mesh.nq, "k": cfg["k"], "nrhs": 16,
+                   "far": prec, "near": "fp64", "l2": "inputs larger than L2"},
+        "roofline": {"bound": "alu", "achieved": pairs / (far_ms * 1e-3) / 1e9, "peak": peak, "unit": UNIT,
+                     "frac": pairs / (far_ms * 1e-3) / 1e9 / peak, "traffic": None, "kernel": "far_tc_kernel"},
+        "gpu_launches": int(prof["launches"]),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "sphere163842_k64_q3_r16":
+        run_large(args)
+        return
     if args.workload == "batch12_r64":
         run_batch(args)
         return

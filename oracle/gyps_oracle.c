@@ -11,6 +11,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -86,10 +87,14 @@ int or_kernel_matvec(int64_t nt, const double *xt, const int64_t *tid,
                      int64_t ns, const double *ys, double k, int64_t nrhs,
                      const double *u, double *v)
 {
-    #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t t = 0; t < nt; ++t) {
-        for (int64_t j = 0; j < nrhs; ++j) {
-            double ar = 0.0, ai = 0.0;
+    #pragma omp parallel
+    {
+        /* one kernel value per (t, l), used for every right-hand side; each
+           column still sums over l in increasing order */
+        double *acc = (double *)calloc((size_t)(2 * nrhs), sizeof(double));
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t t = 0; t < nt; ++t) {
+            for (int64_t j = 0; j < 2 * nrhs; ++j) acc[j] = 0.0;
             for (int64_t l = 0; l < ns; ++l) {
                 double gr, gi;
                 if (tid != NULL && tid[t] == l) {
@@ -98,13 +103,18 @@ int or_kernel_matvec(int64_t nt, const double *xt, const int64_t *tid,
                 } else {
                     helmholtz_g(xt + 3 * t, ys + 3 * l, k, &gr, &gi);
                 }
-                double ur = u[2 * (j * ns + l)], ui = u[2 * (j * ns + l) + 1];
-                ar += gr * ur - gi * ui;
-                ai += gr * ui + gi * ur;
+                for (int64_t j = 0; j < nrhs; ++j) {
+                    double ur = u[2 * (j * ns + l)], ui = u[2 * (j * ns + l) + 1];
+                    acc[2 * j] += gr * ur - gi * ui;
+                    acc[2 * j + 1] += gr * ui + gi * ur;
+                }
             }
-            v[2 * (j * nt + t)] = ar;
-            v[2 * (j * nt + t) + 1] = ai;
+            for (int64_t j = 0; j < nrhs; ++j) {
+                v[2 * (j * nt + t)] = acc[2 * j];
+                v[2 * (j * nt + t) + 1] = acc[2 * j + 1];
+            }
         }
+        free(acc);
     }
     return 0;
 }

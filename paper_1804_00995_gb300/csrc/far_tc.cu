@@ -126,8 +126,9 @@ __device__ __forceinline__ uint32_t bf16x2(float a, float b)
 __device__ __forceinline__ void split2(float2 x, uint32_t &hi, uint32_t &lo)
 {
     hi = bf16x2(x.y, x.x);
-    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
-    lo = bf16x2(__fadd_rn(x.y, -h1), __fadd_rn(x.x, -h0));
+    const float2 nh = make_float2(-__uint_as_float(hi << 16), -__uint_as_float(hi & 0xFFFF0000u));
+    const float2 l = __fadd2_rn(x, nh);  // exact: x - hi fits in FP32
+    lo = bf16x2(l.y, l.x);
 }
 
 // ---------------------------------------------------------------- panel
@@ -568,7 +569,8 @@ gyps_status run(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, doub
     a.ncols = 0;
     a.ks = (float)k;
     a.err = m->d_err;
-    // four generator threads per target row (16 generator warps), copy stages as shared memory allows
+    // four generator threads per target row (16 generator warps per CTA), four tile stages, one CTA
+    // per SM (two CTAs with two stages each measured no faster at 16 right-hand sides)
     return run_pass_cfg<R, 4, (R == 16 ? 4 : 3), 4>(m, a, n_chunks, X, ldx, nrhs, v, s, panel);
 }
 

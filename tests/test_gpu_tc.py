@@ -56,3 +56,20 @@ def test_tc_rejects_laplace_and_partial_ranges():
         with pytest.raises(g.GypsError) as e:
             g.sl_apply(gm, kk, x, prec="tc_bf16x3", **kw)
         assert e.value.status == "UNSUPPORTED"
+
+
+@pytest.mark.slow
+def test_sphere163842_k64_q3_r16_sampled_rows():
+    """Workload sphere163842_k64_q3_r16 at full size (983040 points, 16 plane
+    waves, seed 7): tensor-core apply vs the oracle on 48 sampled rows."""
+    import paper_1804_00995_gb300 as g
+    v, t = synth.icosphere(7)
+    gm = g.Mesh(v, t, 3)
+    om = oracle.Mesh(v, t, 3)
+    dirs = synth.plane_wave_dirs(np.random.default_rng(7), 16)
+    f = g.rhs_planewave(gm, 64.0, dirs)
+    y = g.sl_apply(gm, 64.0, f, prec="tc_bf16x3").cpu().numpy()
+    fh = f.cpu().numpy()
+    rows = np.sort(np.random.default_rng(64).choice(om.nv, 48, replace=False))
+    ref = om.apply(64.0, fh, rows=rows)[rows]
+    assert rel(y[rows], ref) < TC_TOL
