@@ -37,6 +37,7 @@ MUFU_PER_PAIR = 3          # rsqrt, sin, cos
 MUFU_PER_CLK_PER_SM = 16   # special-function results per clock per SM
 PROFILE = os.path.join(ROOT, "profiles", "far32_sphere10242_k16_q7.md")
 FAR_SRC = os.path.join(ROOT, "paper_1804_00995_gb300", "csrc", "far.cu")
+FAR_TILE_SRC = os.path.join(ROOT, "paper_1804_00995_gb300", "csrc", "far_tile.cuh")
 
 
 def parse():
@@ -134,11 +135,13 @@ def far_traffic_per_launch():
 
 
 def far_kernel_sha():
-    """sha256 of the FP32 far-kernel section of far.cu (the code the counters describe)."""
+    """sha256 of the FP32 far-kernel code the counters describe: the tile body
+    in far_tile.cuh and the FP32 section of far.cu."""
+    tile = open(FAR_TILE_SRC).read()
     src = open(FAR_SRC).read()
     a = src.index("// ---------------------------------------------------------------- a3: far, FP32")
     b = src.index("// ---------------------------------------------------------------- a3: far, FP64")
-    return hashlib.sha256(src[a:b].encode()).hexdigest()
+    return hashlib.sha256((tile + src[a:b]).encode()).hexdigest()
 
 
 def sm_peak_pairs(num_sms, mhz):
