@@ -2,13 +2,16 @@
 // 16 or more right-hand sides.  In real arithmetic the complex product is
 //   [Re v | Im v] = [Gr | Gi] * [[Ur, Ui], [-Ui, Ur]],
 // a (128 targets) x (2 Ks) by (2 Ks) x (2 R) contraction per source chunk of Ks
-// points.  The CUDA cores generate the kernel tile G = exp(ikr)/(kr) in FP32
-// (the MUFU path of the FP32 kernel), split every value into bf16 hi + lo and
-// store both in shared memory in the canonical K-major layout; one thread issues
-// tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulation in tensor memory) for
-// the three split products hi*hi + hi*lo + lo*hi against the bf16 hi/lo panel of
-// the densities, which 1-D bulk copies stage per chunk.  The epilogue reads the
-// accumulator with tcgen05.ld and adds k * (Re, Im) into the FP64 sums.
+// points.  Sixteen generator warps compute the kernel tile G = exp(ikr)/(kr) in
+// FP32 on the CUDA cores (the MUFU path of the FP32 kernel), split every value
+// into bf16 hi + lo and write both straight into tensor memory (tcgen05.st, one
+// lane per target).  A product warp issues tcgen05.mma (kind::f16, bf16 inputs,
+// FP32 accumulation in tensor memory) with the tile as operand A and the bf16
+// hi/lo panel of the densities as operand B: per 16-wide K step one product
+// A_hi x [B_hi | B_lo] (the two panels stacked along N) and one A_lo x B_hi, the
+// three split terms hi*hi + hi*lo + lo*hi.  A copy warp stages the panel chunks
+// by 1-D bulk copies.  The epilogue reads the accumulators with tcgen05.ld and
+// adds k * (Re, Im) into the FP64 sums.
 #include <algorithm>
 #include <cmath>
 
@@ -20,31 +23,46 @@
 namespace gyps {
 namespace tc {
 
-constexpr int M = 128;          // targets per tile = tensor-memory lanes
-constexpr int KS = 32;          // sources per chunk
-constexpr int KC = 2 * KS;      // K extent per chunk: Gr for the chunk, then Gi
-constexpr int NTHR = 256;       // 8 warps, two per target row (each half the chunk)
-constexpr int SEG_CHUNKS = 128; // chunks per work item (4096 sources)
-constexpr int POS_BYTES = 384;  // float4 XY[16] + float2 Z[16] (negated, scaled by k)
-constexpr uint32_t CORE_LBO = 128;            // bytes between core matrices along K
-constexpr uint32_t CORE_SBO = (KC / 8) * 128; // bytes between 8-row groups
+constexpr int M = 128;                          // targets per tile = tensor-memory lanes
+constexpr int KS = 64;                          // sources per chunk
+constexpr int KC = 2 * KS;                      // K extent per chunk: Gr for the chunk, then Gi
+constexpr int GPR = 4;                          // generator threads per target row
+constexpr int NGEN = M * GPR;                   // 16 generator warps
+constexpr int NT = NGEN + 64;                   // + product warp + copy warp
+constexpr int SEG_CHUNKS = 64;                  // chunks per work item (4096 sources)
+constexpr int POS_XY = KS / 2 * 16;             // float4 (-x0, -x1, -y0, -y1) per source pair
+constexpr int POS_BYTES = POS_XY + KS / 2 * 8;  // + float2 (-z0, -z1) per pair (scaled by k)
+constexpr uint32_t CORE_LBO = 128;              // bytes between core matrices along K
+constexpr uint32_t CORE_SBO = (KC / 8) * 128;   // bytes between 8-row groups
+constexpr int A_COLS = KC / 2;                  // tensor-memory columns of one bf16 tile (hi or lo)
 
 // Byte offset of element (row, k) of a rows x KC bf16 block in the canonical
 // K-major layout without swizzle: 8 x 16-byte core matrices, K-adjacent core
-// matrices 128 bytes apart, 8-row groups CORE_SBO apart.
+// matrices 128 bytes apart, 8-row groups CORE_SBO apart.  A block of 2 N rows
+// made of two N-row blocks placed one after the other is again canonical.
 __host__ __device__ constexpr uint32_t core_off(int row, int k)
 {
     return (uint32_t)(row >> 3) * CORE_SBO + (uint32_t)(k >> 3) * CORE_LBO + (uint32_t)(row & 7) * 16u +
            (uint32_t)(k & 7) * 2u;
 }
 
+// Per right-hand-side count R: panel chunk layout, tensor-memory plan
+// (accumulator [hi*hi + lo*hi | hi*lo] in columns [0, 2N), then A_STAGES tile
+// stages of 2 A_COLS columns), copy stages SS.
 template <int R>
 struct Cfg {
-    static constexpr int N = 2 * R;                       // accumulator columns: Re then Im
+    static constexpr int N = 2 * R;                       // columns of one product: Re then Im
     static constexpr int B_BYTES = N * KC * 2;            // bf16 panel, one of hi / lo
     static constexpr int CHUNK_BYTES = POS_BYTES + 2 * B_BYTES;
-    static constexpr int A_BYTES = M * KC * 2;            // bf16 kernel tile, one of hi / lo
-    static constexpr int TMEM_COLS = N < 32 ? 32 : N;
+    static constexpr int ACC = 2 * N;
+    static constexpr int A_STAGES = (512 - ACC) / (2 * A_COLS) >= 3 ? 3 : 2;
+    static constexpr int SS = R == 16 ? 6 : R == 32 ? 5 : 3;
+    static constexpr int BAR_BYTES = (2 * SS + 2 * A_STAGES + 2) * 8 + 8;
+    static constexpr int SMEM = SS * CHUNK_BYTES + (BAR_BYTES + 15) / 16 * 16;
+    static_assert(ACC + A_STAGES * 2 * A_COLS <= 512, "tensor memory holds 512 columns");
+    static_assert(A_STAGES >= 2 && SS > A_STAGES, "pipeline depth");
+    static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+    static_assert(CHUNK_BYTES % 16 == 0 && POS_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -64,12 +82,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+// D (tensor memory) (+)= A (tensor memory) x B (shared-memory descriptor)^T
+__device__ __forceinline__ void mma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
 
@@ -112,7 +131,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&r)[4])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
+                 "r"(r[2]), "r"(r[3])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // {upper, lower} halves = bf16(a), bf16(b), round to nearest
 __device__ __forceinline__ uint32_t bf16x2(float a, float b)
@@ -129,6 +155,23 @@ __device__ __forceinline__ void split2(float2 x, uint32_t &hi, uint32_t &lo)
     const float2 nh = make_float2(-__uint_as_float(hi << 16), -__uint_as_float(hi & 0xFFFF0000u));
     const float2 l = __fadd2_rn(x, nh);  // exact: x - hi fits in FP32
     lo = bf16x2(l.y, l.x);
+}
+
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another thread reported a failure.
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort)
+{
+    for (int n = 0; n < (1 << 22); ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((n & 255) == 255 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
 }
 
 // ---------------------------------------------------------------- panel
@@ -157,7 +200,7 @@ __global__ void tc_interp_kernel(const int32_t *tri, const double4_32a *pts64, c
             z = (float)p.z * ks;
         }
         float *xy = reinterpret_cast<float *>(base);
-        float *zz = reinterpret_cast<float *>(base + 256);
+        float *zz = reinterpret_cast<float *>(base + POS_XY);
         const int pp = s >> 1, lane = s & 1;
         xy[4 * pp + lane] = -x;
         xy[4 * pp + 2 + lane] = -y;
@@ -210,23 +253,22 @@ struct TcArgs {
     int *err;
 };
 
-// Kernel tile of one generator thread: target `row`, the GPR sources of its
-// slice of the chunk, split into bf16 hi/lo and stored at K = s (Gr) and
-// K = KS + s (Gi).
-template <int GPR, bool CHECK>
-__device__ __forceinline__ void gen_chunk(const unsigned char *src, unsigned char *a_hi, unsigned char *a_lo,
-                                          float2 tx, float2 ty, float2 tz, int64_t tgt, int64_t src0, int row,
-                                          int slice)
+// Kernel tile of one generator thread (its row = its tensor-memory lane) for
+// its slice of the chunk (KS / GPR sources): bf16 hi/lo of Gr at K = s and of
+// Gi at K = KS + s; bf16 pairs (2c, 2c + 1) of K share column c.
+template <bool CHECK>
+__device__ __forceinline__ void gen_chunk(const unsigned char *src, uint32_t ta_hi, uint32_t ta_lo, float2 tx,
+                                          float2 ty, float2 tz, int64_t tgt, int64_t src0, int slice)
 {
-    constexpr int SRC_PER = KS / GPR;  // sources per thread (8 or 16)
+    constexpr int SRC_PER = KS / GPR;
     const float4 *XY = reinterpret_cast<const float4 *>(src);
-    const float2 *Z = reinterpret_cast<const float2 *>(src + 256);
+    const float2 *Z = reinterpret_cast<const float2 *>(src + POS_XY);
     const float2 magic = make_float2(12582912.0f, 12582912.0f);
     const float2 nmagic = make_float2(-12582912.0f, -12582912.0f);
     const float2 inv2pi = make_float2(0.159154943091895335769f, 0.159154943091895335769f);
     const float2 m2pi = make_float2(-6.28318530717958647692f, -6.28318530717958647692f);
 #pragma unroll
-    for (int q = 0; q < SRC_PER / 8; ++q) {  // groups of 8 sources = one core-matrix row
+    for (int q = 0; q < SRC_PER / 8; ++q) {  // groups of 8 sources = 4 tensor-memory columns
         uint32_t hr[4], lr[4], hi_[4], li[4];
 #pragma unroll
         for (int p4 = 0; p4 < 4; ++p4) {
@@ -258,204 +300,203 @@ __device__ __forceinline__ void gen_chunk(const unsigned char *src, unsigned cha
             split2(gre, hr[p4], lr[p4]);
             split2(gim, hi_[p4], li[p4]);
         }
-        const int kre = slice * SRC_PER + q * 8;
-        const uint32_t ore = core_off(row, kre), oim = core_off(row, KS + kre);
-        *reinterpret_cast<uint4 *>(a_hi + ore) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-        *reinterpret_cast<uint4 *>(a_lo + ore) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-        *reinterpret_cast<uint4 *>(a_hi + oim) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
-        *reinterpret_cast<uint4 *>(a_lo + oim) = make_uint4(li[0], li[1], li[2], li[3]);
+        const uint32_t cre = (uint32_t)(slice * SRC_PER + q * 8) / 2, cim = cre + KS / 2;
+        tmem_st4(ta_hi + cre, hr);
+        tmem_st4(ta_hi + cim, hi_);
+        tmem_st4(ta_lo + cre, lr);
+        tmem_st4(ta_lo + cim, li);
     }
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Bounded wait that also gives up as soon as another thread reported a failure.
-__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort)
-{
-    for (int n = 0; n < (1 << 22); ++n) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((n & 255) == 255 && *abort) return false;
-    }
-    *abort = 1;
-    return false;
-}
-
-// Warp-specialised kernel: GPR generator threads per target row (warps
-// 0 .. 4 GPR - 1) and one control warp (the last) whose lane 0 issues the bulk
-// copies of the density panel and the tensor-core products.  Hand-offs:
-//   src_full[s]  copy of chunk n landed (count 1 + tx bytes)
-//   a_full[s]    all generators wrote the kernel tile of chunk n (count 128 GPR)
-//   mma_done[s]  products of chunk n finished (tcgen05.commit): tile and copy stage free
-//   acc_full     all products of a work item finished: accumulator ready
-//   acc_empty    every generator read the accumulator (count 128 GPR)
-template <int R, int GPR, int SS, int A_STAGES>
-__global__ void __launch_bounds__(M * GPR + 32) far_tc_kernel(const TcArgs a)
+// Warp-specialised persistent kernel, one CTA per SM (it takes all 512 columns
+// of tensor memory).  Work items (target tile, source segment) in
+// segment-major order, CTA b taking items b, b + grid, ...: the CTAs in flight
+// read the same source segment, which stays in L2.  Roles and hand-offs:
+//   generator warps 0..15  (row = lane quadrant of the warp, GPR slices per row)
+//   product warp 16        lane 0 issues the products and the commits
+//   copy warp 17           lane 0 issues the bulk copies of the panel
+//   src_full[s]   copy of the chunk landed in stage s (count 1 + tx bytes)
+//   src_empty[s]  products that read stage s finished (tcgen05.commit)
+//   a_full[t]     every generator warp stored its part of tile stage t (count 16)
+//   mma_done[t]   products that read tile stage t finished (tcgen05.commit)
+//   acc_full      all products of a work item finished: accumulator ready
+//   acc_empty     every generator warp read the accumulator (count 16)
+// Every wait is bounded; a wait that runs out sets the error word and the
+// abort flag, after which every role stops, waits (bounded) for its copies and
+// products in flight, and the CTA frees its tensor memory.
+template <int R>
+__global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
 {
     using C = Cfg<R>;
-    constexpr int NGEN = M * GPR;
-    constexpr int SRC_OFF = A_STAGES * 2 * C::A_BYTES;
-    constexpr int BAR_OFF = SRC_OFF + SS * C::CHUNK_BYTES;
+    constexpr int SS = C::SS, AS = C::A_STAGES;
+    constexpr int BAR_OFF = SS * C::CHUNK_BYTES;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *src_full = reinterpret_cast<uint64_t *>(smem + BAR_OFF);  // [SS]
-    uint64_t *a_full = src_full + SS;                                   // [A_STAGES]
-    uint64_t *mma_done = a_full + A_STAGES;                             // [A_STAGES]
-    uint64_t *acc_full = mma_done + A_STAGES;
+    uint64_t *src_empty = src_full + SS;                                // [SS]
+    uint64_t *a_full = src_empty + SS;                                  // [AS]
+    uint64_t *mma_done = a_full + AS;                                   // [AS]
+    uint64_t *acc_full = mma_done + AS;
     uint64_t *acc_empty = acc_full + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 1);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
     const int th = threadIdx.x, warp = th >> 5, lane = th & 31;
 
-    const int64_t items = a.n_tiles * a.n_segs;
-    const int64_t ibeg = items * blockIdx.x / gridDim.x;
-    const int64_t iend = items * (blockIdx.x + 1) / gridDim.x;
-    if (ibeg >= iend) return;
+    const int64_t n_tiles = a.n_tiles, n_segs = a.n_segs, n_chunks = a.n_chunks, nq = a.nq;
+    const int64_t items = n_tiles * n_segs;
+    const int64_t ifirst = blockIdx.x, istep = gridDim.x;
+    const int64_t icount = items > ifirst ? (items - ifirst + istep - 1) / istep : 0;
+    if (icount <= 0) return;
+    auto seg_of = [n_tiles](int64_t i) { return i / n_tiles; };
+    auto chunks_of = [n_chunks](int64_t seg) { return (int)min((int64_t)SEG_CHUNKS, n_chunks - seg * SEG_CHUNKS); };
 
     if (th == 0) {
-        for (int s = 0; s < SS; ++s) mbar_init(smem_addr(&src_full[s]), 1);
-        for (int s = 0; s < A_STAGES; ++s) {
-            mbar_init(smem_addr(&a_full[s]), NGEN);
+        for (int s = 0; s < SS; ++s) {
+            mbar_init(smem_addr(&src_full[s]), 1);
+            mbar_init(smem_addr(&src_empty[s]), 1);
+        }
+        for (int s = 0; s < AS; ++s) {
+            mbar_init(smem_addr(&a_full[s]), NGEN / 32);
             mbar_init(smem_addr(&mma_done[s]), 1);
         }
         mbar_init(smem_addr(acc_full), 1);
-        mbar_init(smem_addr(acc_empty), NGEN);
+        mbar_init(smem_addr(acc_empty), NGEN / 32);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(smem_addr(tmem_slot), C::TMEM_COLS);
+    if (warp == 0) tmem_alloc(smem_addr(tmem_slot), 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-
-    // kernel parameters in registers (no reference to the parameter block)
-    const int64_t n_segs = a.n_segs, n_chunks = a.n_chunks, nq = a.nq;
-    const unsigned char *panel = a.panel;
-    const float ks = a.ks;
+    bool ok = true;
 
     if (warp == NGEN / 32) {
-        // ------------------------------------------------------------ control warp
-        if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(M, C::N);
-            // copy producer: item, chunk within it, chunks in it
-            int64_t p_item = ibeg;
-            int64_t p_seg = p_item % n_segs;
-            int p_c = 0;
-            int p_nc = (int)min((int64_t)SEG_CHUNKS, n_chunks - p_seg * SEG_CHUNKS);
-            int issued = 0, c_stage = 0;
-            uint32_t c_par = 0;
-            int n = 0;  // chunks whose products were issued
-            int sa = 0, ss = 0;
-            uint32_t pa = 0, ps = 0;
-            bool ok = true;
-            for (int64_t item = ibeg; item < iend && ok; ++item) {
-                const int64_t seg = item % n_segs;
-                const int nc = (int)min((int64_t)SEG_CHUNKS, n_chunks - seg * SEG_CHUNKS);
-                if (item > ibeg) ok = wait_or_abort(smem_addr(acc_empty), (uint32_t)((item - ibeg - 1) & 1), abort);
-                for (int c = 0; c < nc && ok; ++c) {
-                    // copies run up to SS - 1 chunks ahead; a copy stage is free once the
-                    // products of the chunk that used it (SS chunks earlier) finished
-                    while (p_item < iend && issued < n + SS) {
-                        if (issued >= SS) {
-                            const int prev = issued - SS;  // last user of this copy stage
-                            if (prev >= n) break;         // its products are not issued yet
-                            ok = wait_or_abort(smem_addr(&mma_done[prev % A_STAGES]),
-                                               (uint32_t)((prev / A_STAGES) & 1), abort);
-                            if (!ok) break;
-                        }
-                        const uint32_t bar = smem_addr(&src_full[c_stage]);
-                        mbar_expect_tx(bar, C::CHUNK_BYTES);
-                        bulk_g2s(smem_addr(smem + SRC_OFF + c_stage * C::CHUNK_BYTES),
-                                 panel + (p_seg * SEG_CHUNKS + p_c) * (int64_t)C::CHUNK_BYTES, C::CHUNK_BYTES, bar);
-                        ++issued;
-                        if (++c_stage == SS) {
-                            c_stage = 0;
-                            c_par ^= 1;
-                        }
-                        if (++p_c == p_nc) {
-                            p_c = 0;
-                            if (++p_item < iend) {
-                                p_seg = p_item % n_segs;
-                                p_nc = (int)min((int64_t)SEG_CHUNKS, n_chunks - p_seg * SEG_CHUNKS);
-                            }
-                        }
-                    }
-                    if (!ok) break;
-                    ok = wait_or_abort(smem_addr(&a_full[sa]), pa, abort) &&
-                         wait_or_abort(smem_addr(&src_full[ss]), ps, abort);
-                    if (!ok) break;
-                    tc_fence_after();
-                    const uint32_t ah = smem_addr(smem + sa * 2 * C::A_BYTES), al = ah + C::A_BYTES;
-                    const uint32_t bh = smem_addr(smem + SRC_OFF + ss * C::CHUNK_BYTES + POS_BYTES);
-                    const uint32_t bl = bh + C::B_BYTES;
+        // ------------------------------------------------------------ product warp
+        const bool leader = lane == 0;
+        constexpr uint32_t idesc2 = idesc_bf16(M, 2 * C::N), idesc1 = idesc_bf16(M, C::N);
+        // descriptor of the hi panel of stage 0 at K = 0; stage and K offsets add to
+        // its address field (shared addresses stay below 256 KB: no carry out of it)
+        const uint64_t bdesc0 = smem_desc(smem_addr(smem + POS_BYTES));
+        int n = 0, sa = 0, ss = 0;
+        uint32_t pa = 0, ps = 0;
+        for (int64_t it = 0; it < icount && ok; ++it) {
+            const int nc = chunks_of(seg_of(ifirst + it * istep));
+            if (it > 0)
+                ok = __all_sync(0xffffffffu, wait_or_abort(smem_addr(acc_empty), (uint32_t)((it - 1) & 1), abort));
+            for (int c = 0; c < nc && ok; ++c) {
+                ok = wait_or_abort(smem_addr(&a_full[sa]), pa, abort) &&
+                     wait_or_abort(smem_addr(&src_full[ss]), ps, abort);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t ah = tmem + (uint32_t)(C::ACC + sa * 2 * A_COLS), al = ah + A_COLS;
+                const uint64_t bdh = bdesc0 + (uint64_t)((ss * C::CHUNK_BYTES) >> 4);
+                if (leader) {
 #pragma unroll
                     for (int kk = 0; kk < KC / 16; ++kk) {
-                        const uint32_t off = kk * 2 * CORE_LBO;
-                        const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
-                        mma_bf16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc0);
-                        mma_bf16(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
-                        mma_bf16(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+                        const uint64_t boff = (uint64_t)(kk * 2 * CORE_LBO) >> 4;  // 16 K = two core matrices
+                        const uint32_t aoff = kk * 8;                              // 16 K = 8 columns
+                        // [hi*hi | hi*lo] += A_hi [B_hi | B_lo]; then hi*hi += A_lo B_hi
+                        mma_bf16_ta(tmem, ah + aoff, bdh + boff, idesc2, (c > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16_ta(tmem, al + aoff, bdh + boff, idesc1, 1u);
                     }
                     mma_commit(smem_addr(&mma_done[sa]));
+                    mma_commit(smem_addr(&src_empty[ss]));
                     if (c == nc - 1) mma_commit(smem_addr(acc_full));
-                    ++n;
-                    if (++sa == A_STAGES) {
-                        sa = 0;
-                        pa ^= 1;
-                    }
-                    if (++ss == SS) {
-                        ss = 0;
-                        ps ^= 1;
-                    }
+                }
+                __syncwarp();
+                ++n;
+                if (++sa == AS) {
+                    sa = 0;
+                    pa ^= 1;
+                }
+                if (++ss == SS) {
+                    ss = 0;
+                    ps ^= 1;
                 }
             }
+        }
+        if (leader) {
             if (!ok) {
                 atomicExch(a.err, 1);
                 *abort = 1;
             }
-            // drain: copies and products in flight must land before the CTA exits
-            for (int j = n; j < issued; ++j)
-                mbar_wait_bounded(smem_addr(&src_full[j % SS]), (uint32_t)((j / SS) & 1));
-            if (n > 0) {
+            if (n > 0) {  // the last products must finish before the tensor memory is freed
                 const int nl = n - 1;
-                mbar_wait_bounded(smem_addr(&mma_done[nl % A_STAGES]), (uint32_t)((nl / A_STAGES) & 1));
+                mbar_wait_bounded(smem_addr(&mma_done[nl % AS]), (uint32_t)((nl / AS) & 1));
             }
+        }
+        __syncwarp();
+    } else if (warp == NGEN / 32 + 1) {
+        // ------------------------------------------------------------ copy warp
+        const bool leader = lane == 0;
+        const unsigned char *panel = a.panel;
+        int j = 0;  // copies issued
+        for (int64_t it = 0; it < icount && ok; ++it) {
+            const int64_t seg = seg_of(ifirst + it * istep);
+            const int nc = chunks_of(seg);
+            for (int c = 0; c < nc; ++c, ++j) {
+                const int s = j % SS;
+                if (j >= SS) {  // the products of chunk j - SS, the stage's last user, finished
+                    ok = __all_sync(0xffffffffu,
+                                    wait_or_abort(smem_addr(&src_empty[s]), (uint32_t)((j / SS - 1) & 1), abort));
+                    if (!ok) break;
+                }
+                if (leader) {
+                    const uint32_t bar = smem_addr(&src_full[s]);
+                    mbar_expect_tx(bar, C::CHUNK_BYTES);
+                    bulk_g2s(smem_addr(smem + s * C::CHUNK_BYTES),
+                             panel + (seg * SEG_CHUNKS + c) * (int64_t)C::CHUNK_BYTES, C::CHUNK_BYTES, bar);
+                }
+                __syncwarp();
+            }
+        }
+        if (leader) {
+            if (!ok) {
+                atomicExch(a.err, 1);
+                *abort = 1;
+            }
+            // copies in flight must land before the CTA exits
+            for (int jj = max(0, j - SS); jj < j; ++jj)
+                mbar_wait_bounded(smem_addr(&src_full[jj % SS]), (uint32_t)((jj / SS) & 1));
         }
         __syncwarp();
     } else {
         // ------------------------------------------------------------ generator warps
         const int row = th & (M - 1), slice = th / M;
+        const int quad = warp & 3;  // lane quadrant of tensor memory this warp may access
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+        const float ks = a.ks;
         int n = 0, sa = 0, ss = 0;
-        uint32_t pa = 0, ps = 0;  // parity of the current use of stage sa / ss
-        bool ok = true;
-        int64_t item_count = 0;
-        for (int64_t item = ibeg; item < iend && ok; ++item, ++item_count) {
-            const int64_t tile = item / n_segs;
-            const int64_t seg = item - tile * n_segs;
+        uint32_t pa = 0, ps = 0;
+        for (int64_t it = 0; it < icount && ok; ++it) {
+            const int64_t item = ifirst + it * istep;
+            const int64_t seg = seg_of(item), tile = item - seg * n_tiles;
             const int64_t t0 = tile * M;
             const int64_t tgt = t0 + row;
             const float4 p = a.tgt[min(tgt, nq - 1)];
             const float2 tx = make_float2(p.x * ks, p.x * ks);
             const float2 ty = make_float2(p.y * ks, p.y * ks);
             const float2 tz = make_float2(p.z * ks, p.z * ks);
-            const int nc = (int)min((int64_t)SEG_CHUNKS, n_chunks - seg * SEG_CHUNKS);
+            const int nc = chunks_of(seg);
             int64_t src0 = seg * SEG_CHUNKS * KS;
             for (int c = 0; c < nc; ++c, ++n, src0 += KS) {
-                if (n >= A_STAGES) ok = wait_or_abort(smem_addr(&mma_done[sa]), pa ^ 1u, abort);
+                if (n >= AS) ok = wait_or_abort(smem_addr(&mma_done[sa]), pa ^ 1u, abort);
                 ok = ok && wait_or_abort(smem_addr(&src_full[ss]), ps, abort);
+                ok = __all_sync(0xffffffffu, ok);  // tcgen05.st is warp-collective
                 if (!ok) break;
-                const unsigned char *src = smem + SRC_OFF + ss * C::CHUNK_BYTES;
-                unsigned char *a_hi = smem + sa * 2 * C::A_BYTES;
-                unsigned char *a_lo = a_hi + C::A_BYTES;
+                tc_fence_after();
+                const unsigned char *src = smem + ss * C::CHUNK_BYTES;
+                const uint32_t ta_hi = lane_base + (uint32_t)(C::ACC + sa * 2 * A_COLS), ta_lo = ta_hi + A_COLS;
                 if (t0 < src0 + KS && src0 < t0 + M)
-                    gen_chunk<GPR, true>(src, a_hi, a_lo, tx, ty, tz, tgt, src0, row, slice);
+                    gen_chunk<true>(src, ta_hi, ta_lo, tx, ty, tz, tgt, src0, slice);
                 else
-                    gen_chunk<GPR, false>(src, a_hi, a_lo, tx, ty, tz, tgt, src0, row, slice);
-                fence_async_smem();
-                mbar_arrive(smem_addr(&a_full[sa]));
-                if (++sa == A_STAGES) {
+                    gen_chunk<false>(src, ta_hi, ta_lo, tx, ty, tz, tgt, src0, slice);
+                tmem_st_wait();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&a_full[sa]));
+                if (++sa == AS) {
                     sa = 0;
                     pa ^= 1;
                 }
@@ -465,28 +506,32 @@ __global__ void __launch_bounds__(M * GPR + 32) far_tc_kernel(const TcArgs a)
                 }
             }
             if (!ok) break;
-            // epilogue: this item's accumulator
-            ok = wait_or_abort(smem_addr(acc_full), (uint32_t)(item_count & 1), abort);
+            // epilogue: this item's accumulator, [hi*hi + lo*hi | hi*lo]
+            ok = __all_sync(0xffffffffu, wait_or_abort(smem_addr(acc_full), (uint32_t)(it & 1), abort));
             if (!ok) break;
             tc_fence_after();
-            constexpr int GROUPS = NGEN / 32 / 4;      // warps sharing one lane quadrant
-            constexpr int COLS = C::N / GROUPS;        // accumulator columns per warp
-            const int quad = warp & 3, grp = warp >> 2;
+            constexpr int GROUPS = NGEN / 32 / 4;  // warps sharing one lane quadrant
+            constexpr int COLS = C::N / GROUPS;    // accumulator columns per warp
+            const int grp = warp >> 2;
             const int64_t trow = t0 + quad * 32 + lane;
             constexpr int LD = COLS >= 16 ? 16 : 8;  // columns per tcgen05.ld
             static_assert(COLS % LD == 0, "accumulator columns per warp");
 #pragma unroll
             for (int cb = 0; cb < COLS / LD; ++cb) {
-                uint32_t r[16];
                 const int col0 = grp * COLS + cb * LD;
-                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col0;
+                uint32_t r0[16], r1[16];
                 if (LD == 16) {
-                    tmem_ld16(taddr, r);
+                    tmem_ld16(lane_base + (uint32_t)col0, r0);
+                    tmem_ld16(lane_base + (uint32_t)(C::N + col0), r1);
                 } else {
-                    uint32_t r8[8];
-                    tmem_ld8(taddr, r8);
+                    uint32_t q0[8], q1[8];
+                    tmem_ld8(lane_base + (uint32_t)col0, q0);
+                    tmem_ld8(lane_base + (uint32_t)(C::N + col0), q1);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) r[i] = r8[i];
+                    for (int i = 0; i < 8; ++i) {
+                        r0[i] = q0[i];
+                        r1[i] = q1[i];
+                    }
                 }
                 tmem_ld_wait();
                 if (trow < nq) {
@@ -496,16 +541,19 @@ __global__ void __launch_bounds__(M * GPR + 32) far_tc_kernel(const TcArgs a)
                         const int part = col >= R ? 1 : 0;  // Re columns first, then Im
                         const int jj = col - part * R;
                         if (jj < a.ncols) {
+                            const float f = __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
                             double *dst = reinterpret_cast<double *>(a.v + trow + (int64_t)jj * a.ldv) + part;
-                            atomicAdd(dst, (double)__uint_as_float(r[i]) * (double)ks);
+                            atomicAdd(dst, (double)f * (double)ks);
                         }
                     }
                 }
             }
             tc_fence_before();
-            mbar_arrive(smem_addr(acc_empty));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(acc_empty));
         }
-        if (!ok) {
+        tmem_st_wait();
+        if (!ok && lane == 0) {
             atomicExch(a.err, 1);
             *abort = 1;
         }
@@ -514,39 +562,8 @@ __global__ void __launch_bounds__(M * GPR + 32) far_tc_kernel(const TcArgs a)
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, C::TMEM_COLS);
+        tmem_dealloc(tmem, 512);
     }
-}
-
-template <int R, int GPR, int SS, int A_STAGES>
-gyps_status run_pass_cfg(Mesh *m, const TcArgs &a0, int64_t n_chunks, const double2 *X, int64_t ldx, int nrhs,
-                         double2 *v, cudaStream_t s, unsigned char *panel)
-{
-    using C = Cfg<R>;
-    constexpr int SMEM = A_STAGES * 2 * C::A_BYTES + SS * C::CHUNK_BYTES + 128;
-    constexpr int NT = M * GPR + 32;
-    GYPS_CUDA(cudaFuncSetAttribute(far_tc_kernel<R, GPR, SS, A_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-    int occ = 0;
-    GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, far_tc_kernel<R, GPR, SS, A_STAGES>, NT, SMEM));
-    occ = std::max(occ, 1);
-    TcArgs a = a0;
-    const int64_t items = a.n_tiles * a.n_segs;
-    const int64_t grid = std::min<int64_t>((int64_t)m->num_sms * occ, items);
-    for (int c0 = 0; c0 < nrhs; c0 += R) {
-        StageTimer ti(m, s, 0);
-        dim3 gi((unsigned)((n_chunks * KS + 255) / 256), (unsigned)R);
-        tc_interp_kernel<R><<<gi, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, n_chunks * KS, X, ldx, c0, nrhs,
-                                                a.ks, m->pad, panel);
-        GYPS_CUDA(cudaGetLastError());
-        ti.done(1);
-        a.v = v + (int64_t)c0 * a.ldv;
-        a.ncols = std::min(R, nrhs - c0);
-        StageTimer tf(m, s, 1);
-        far_tc_kernel<R, GPR, SS, A_STAGES><<<(unsigned)grid, NT, SMEM, s>>>(a);
-        GYPS_CUDA(cudaGetLastError());
-        tf.done(1);
-    }
-    return GYPS_OK;
 }
 
 template <int R>
@@ -569,9 +586,24 @@ gyps_status run(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, doub
     a.ncols = 0;
     a.ks = (float)k;
     a.err = m->d_err;
-    // four generator threads per target row (16 generator warps per CTA), four tile stages, one CTA
-    // per SM (two CTAs with two stages each measured no faster at 16 right-hand sides)
-    return run_pass_cfg<R, 4, (R == 16 ? 4 : 3), 4>(m, a, n_chunks, X, ldx, nrhs, v, s, panel);
+    GYPS_CUDA(cudaFuncSetAttribute(far_tc_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    // one CTA per SM: each takes the whole tensor memory
+    const int64_t grid = std::min<int64_t>((int64_t)m->num_sms, a.n_tiles * a.n_segs);
+    for (int c0 = 0; c0 < nrhs; c0 += R) {
+        StageTimer ti(m, s, 0);
+        dim3 gi((unsigned)((n_chunks * KS + 255) / 256), (unsigned)R);
+        tc_interp_kernel<R><<<gi, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, n_chunks * KS, X, ldx, c0, nrhs,
+                                                a.ks, m->pad, panel);
+        GYPS_CUDA(cudaGetLastError());
+        ti.done(1);
+        a.v = v + (int64_t)c0 * a.ldv;
+        a.ncols = std::min(R, nrhs - c0);
+        StageTimer tf(m, s, 1);
+        far_tc_kernel<R><<<(unsigned)grid, NT, C::SMEM, s>>>(a);
+        GYPS_CUDA(cudaGetLastError());
+        tf.done(1);
+    }
+    return GYPS_OK;
 }
 
 }  // namespace tc

@@ -17,7 +17,7 @@ def rel(a, b):
     return max(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c]) for c in range(a.shape[1]))
 
 
-@pytest.mark.parametrize("level,q,k,nrhs", [(1, 3, 5.0, 16), (2, 3, 16.0, 16), (2, 7, 9.0, 20), (3, 3, 30.0, 32)])
+@pytest.mark.parametrize("level,q,k,nrhs", [(1, 3, 5.0, 16), (2, 3, 16.0, 16), (2, 7, 9.0, 20), (3, 3, 30.0, 32), (3, 3, 12.0, 64), (2, 7, 7.0, 70)])
 def test_tc_apply_vs_oracle(level, q, k, nrhs):
     import paper_1804_00995_gb300 as g
     v, t = synth.icosphere(level)
