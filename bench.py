@@ -69,6 +69,13 @@ def workload():
 
 
 # ---------------------------------------------------------------- clocks
+def smi_id_of(props, local_rank=0):
+    """nvidia-smi id of the device: its UUID where torch reports one."""
+    if getattr(props, "uuid", None) is not None:
+        return "GPU-" + str(props.uuid)
+    return str(local_rank)
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -252,10 +259,7 @@ def run_gyps(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    smi_id = str(local_rank)
-    if getattr(props, "uuid", None) is not None:
-        smi_id = "GPU-" + str(props.uuid)
-    clocks = ClockSampler(smi_id)
+    clocks = ClockSampler(smi_id_of(props, local_rank))
     mesh.profile(True)
     if world > 1:
         dist.barrier()
@@ -391,19 +395,23 @@ def run_batch(args):
         b.apply()
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(smi_id_of(torch.cuda.get_device_properties(0)))
+    clocks.start()
+    time.sleep(0.3)
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
         b.apply()
         ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
+    clk = clocks.stop()
     ms = sum(a.elapsed_time(c) for a, c in ev) / args.steps
     pairs = b.info["pairs"]
     line = {
         "metric": "GPairs/s batched single-layer apply", "value": pairs / (ms * 1e-3) / 1e9, "unit": UNIT,
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "dtype": "f32", "data": "synthetic",
-        "pair_rhs_per_s": pairs * 64 / (ms * 1e-3),
+        "dtype": "bf16x3+f32" if b.info["tensor_cores"] else "f32", "data": "synthetic",
+        "pair_rhs_per_s": pairs * 64 / (ms * 1e-3), "clocks": clk,
         "config": {"workload": "batch12_r64", "meshes": [(it["kind"], it["level"], int(it["tri"].shape[0]),
                                                              round(float(it["k"]), 3)) for it in items],
                    "nq_total": int(sum(m.nq for m in meshes)), "nrhs": 64, "quad_points": 3,
@@ -483,17 +491,21 @@ def run_large(args):
         g.sl_apply(mesh, cfg["k"], x, prec=prec, out=y)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(0)
+    clocks = ClockSampler(smi_id_of(props))
     mesh.profile(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks.start()
+    time.sleep(0.3)
     for i in range(args.steps):
         ev[i][0].record(stream)
         g.sl_apply(mesh, cfg["k"], x, prec=prec, out=y)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    clk = clocks.stop()
     prof = mesh.profile_read()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     pairs = float(mesh.nq) ** 2
-    props = torch.cuda.get_device_properties(0)
     peak = sm_peak_pairs(props.multi_processor_count, 2070.0) / 1e9
     far_ms = prof["far_ms"] / max(prof["far_launches"], 1) * prof["far_launches"] / max(prof["applies"], 1)
     line = {
@@ -505,7 +517,7 @@ def run_large(args):
                    "far": prec, "near": "fp64", "l2": "inputs larger than L2"},
         "roofline": {"bound": "alu", "achieved": pairs / (far_ms * 1e-3) / 1e9, "peak": peak, "unit": UNIT,
                      "frac": pairs / (far_ms * 1e-3) / 1e9 / peak, "traffic": None, "kernel": "far_tc_kernel"},
-        "gpu_launches": int(prof["launches"]),
+        "gpu_launches": int(prof["launches"]), "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 

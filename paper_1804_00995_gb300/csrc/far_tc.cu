@@ -29,7 +29,7 @@ constexpr int KC = 2 * KS;                      // K extent per chunk: Gr for th
 constexpr int GPR = 4;                          // generator threads per target row
 constexpr int NGEN = M * GPR;                   // 16 generator warps
 constexpr int NT = NGEN + 64;                   // + product warp + copy warp
-constexpr int SEG_CHUNKS = 64;                  // chunks per work item (4096 sources)
+constexpr int SEG_CHUNKS = 256;                 // chunks per work item (16384 sources)
 constexpr int POS_XY = KS / 2 * 16;             // float4 (-x0, -x1, -y0, -y1) per source pair
 constexpr int POS_BYTES = POS_XY + KS / 2 * 8;  // + float2 (-z0, -z1) per pair (scaled by k)
 constexpr uint32_t CORE_LBO = 128;              // bytes between core matrices along K
@@ -109,17 +109,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-}
-
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -169,6 +158,34 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
     for (int n = 0; n < (1 << 22); ++n) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((n & 255) == 255 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+// Poll that suspends the thread until the phase completes or about `ns`
+// nanoseconds pass (for the product and copy warps: a spinning poll would take
+// issue slots from the generator warps sharing their scheduler).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded (about a second at most) suspending wait; gives up when another
+// thread reported a failure.
+__device__ __forceinline__ bool wait_sleep_or_abort(uint32_t bar, uint32_t parity, volatile int *abort)
+{
+    for (int n = 0; n < (1 << 21); ++n) {
+        if (mbar_try_wait_hint(bar, parity, 500u)) return true;
+        if ((n & 15) == 15 && *abort) return false;
     }
     *abort = 1;
     return false;
@@ -253,14 +270,20 @@ struct TcArgs {
     int *err;
 };
 
-// Kernel tile of one generator thread (its row = its tensor-memory lane) for
-// its slice of the chunk (KS / GPR sources): bf16 hi/lo of Gr at K = s and of
-// Gi at K = KS + s; bf16 pairs (2c, 2c + 1) of K share column c.
+// Kernel values of one generator thread (its row = its tensor-memory lane) for
+// group q (8 sources) of its slice of the chunk (KS / GPR sources): bf16 hi/lo
+// pairs of Gr and Gi, sources (2p, 2p + 1) in the (lower, upper) halves.
+constexpr int SRC_PER = KS / GPR;
+constexpr int GROUPS_PER_CHUNK = SRC_PER / 8;
+
+struct Group {
+    uint32_t hr[4], lr[4], hi[4], li[4];
+};
+
 template <bool CHECK>
-__device__ __forceinline__ void gen_chunk(const unsigned char *src, uint32_t ta_hi, uint32_t ta_lo, float2 tx,
-                                          float2 ty, float2 tz, int64_t tgt, int64_t src0, int slice)
+__device__ __forceinline__ void gen_group(const unsigned char *src, int q, float2 tx, float2 ty, float2 tz,
+                                          int64_t tgt, int64_t src0, int slice, Group &g)
 {
-    constexpr int SRC_PER = KS / GPR;
     const float4 *XY = reinterpret_cast<const float4 *>(src);
     const float2 *Z = reinterpret_cast<const float2 *>(src + POS_XY);
     const float2 magic = make_float2(12582912.0f, 12582912.0f);
@@ -268,44 +291,59 @@ __device__ __forceinline__ void gen_chunk(const unsigned char *src, uint32_t ta_
     const float2 inv2pi = make_float2(0.159154943091895335769f, 0.159154943091895335769f);
     const float2 m2pi = make_float2(-6.28318530717958647692f, -6.28318530717958647692f);
 #pragma unroll
-    for (int q = 0; q < SRC_PER / 8; ++q) {  // groups of 8 sources = 4 tensor-memory columns
-        uint32_t hr[4], lr[4], hi_[4], li[4];
-#pragma unroll
-        for (int p4 = 0; p4 < 4; ++p4) {
-            const int pp = (slice * SRC_PER + q * 8) / 2 + p4;  // source pair within the chunk
-            const float4 xy = XY[pp];
-            const float2 sz = Z[pp];
-            float2 dx = __fadd2_rn(tx, make_float2(xy.x, xy.y));
-            float2 dy = __fadd2_rn(ty, make_float2(xy.z, xy.w));
-            float2 dz = __fadd2_rn(tz, sz);
-            float2 r2 = __fmul2_rn(dx, dx);
-            r2 = __ffma2_rn(dy, dy, r2);
-            r2 = __ffma2_rn(dz, dz, r2);
-            const float2 rs = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-            const float2 ph = __fmul2_rn(r2, rs);
-            const float2 nr = __fadd2_rn(__ffma2_rn(ph, inv2pi, magic), nmagic);
-            const float2 ang = __ffma2_rn(nr, m2pi, ph);
-            float2 gre = __fmul2_rn(make_float2(cos_mufu(ang.x), cos_mufu(ang.y)), rs);
-            float2 gim = __fmul2_rn(make_float2(sin_mufu(ang.x), sin_mufu(ang.y)), rs);
-            if (CHECK) {
-                if (src0 + 2 * pp == tgt) {
-                    gre.x = 0.0f;
-                    gim.x = 1.0f;
-                }
-                if (src0 + 2 * pp + 1 == tgt) {
-                    gre.y = 0.0f;
-                    gim.y = 1.0f;
-                }
+    for (int p4 = 0; p4 < 4; ++p4) {
+        const int pp = (slice * SRC_PER + q * 8) / 2 + p4;  // source pair within the chunk
+        const float4 xy = XY[pp];
+        const float2 sz = Z[pp];
+        float2 dx = __fadd2_rn(tx, make_float2(xy.x, xy.y));
+        float2 dy = __fadd2_rn(ty, make_float2(xy.z, xy.w));
+        float2 dz = __fadd2_rn(tz, sz);
+        float2 r2 = __fmul2_rn(dx, dx);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        const float2 rs = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        const float2 ph = __fmul2_rn(r2, rs);
+        const float2 nr = __fadd2_rn(__ffma2_rn(ph, inv2pi, magic), nmagic);
+        const float2 ang = __ffma2_rn(nr, m2pi, ph);
+        float2 gre = __fmul2_rn(make_float2(cos_mufu(ang.x), cos_mufu(ang.y)), rs);
+        float2 gim = __fmul2_rn(make_float2(sin_mufu(ang.x), sin_mufu(ang.y)), rs);
+        if (CHECK) {
+            if (src0 + 2 * pp == tgt) {
+                gre.x = 0.0f;
+                gim.x = 1.0f;
             }
-            split2(gre, hr[p4], lr[p4]);
-            split2(gim, hi_[p4], li[p4]);
+            if (src0 + 2 * pp + 1 == tgt) {
+                gre.y = 0.0f;
+                gim.y = 1.0f;
+            }
         }
-        const uint32_t cre = (uint32_t)(slice * SRC_PER + q * 8) / 2, cim = cre + KS / 2;
-        tmem_st4(ta_hi + cre, hr);
-        tmem_st4(ta_hi + cim, hi_);
-        tmem_st4(ta_lo + cre, lr);
-        tmem_st4(ta_lo + cim, li);
+        split2(gre, g.hr[p4], g.lr[p4]);
+        split2(gim, g.hi[p4], g.li[p4]);
     }
+}
+
+// Stores group q: Gr at K = s, Gi at K = KS + s; bf16 pairs (2c, 2c + 1) of K
+// share tensor-memory column c.
+__device__ __forceinline__ void st_group(uint32_t ta_hi, uint32_t ta_lo, int q, int slice, const Group &g)
+{
+    const uint32_t cre = (uint32_t)(slice * SRC_PER + q * 8) / 2, cim = cre + KS / 2;
+    tmem_st4(ta_hi + cre, g.hr);
+    tmem_st4(ta_hi + cim, g.hi);
+    tmem_st4(ta_lo + cre, g.lr);
+    tmem_st4(ta_lo + cim, g.li);
+}
+
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
 
 // Warp-specialised persistent kernel, one CTA per SM (it takes all 512 columns
@@ -382,10 +420,10 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
         for (int64_t it = 0; it < icount && ok; ++it) {
             const int nc = chunks_of(seg_of(ifirst + it * istep));
             if (it > 0)
-                ok = __all_sync(0xffffffffu, wait_or_abort(smem_addr(acc_empty), (uint32_t)((it - 1) & 1), abort));
+                ok = __all_sync(0xffffffffu, wait_sleep_or_abort(smem_addr(acc_empty), (uint32_t)((it - 1) & 1), abort));
             for (int c = 0; c < nc && ok; ++c) {
-                ok = wait_or_abort(smem_addr(&a_full[sa]), pa, abort) &&
-                     wait_or_abort(smem_addr(&src_full[ss]), ps, abort);
+                ok = wait_sleep_or_abort(smem_addr(&a_full[sa]), pa, abort) &&
+                     wait_sleep_or_abort(smem_addr(&src_full[ss]), ps, abort);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc_fence_after();
@@ -439,7 +477,7 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
                 const int s = j % SS;
                 if (j >= SS) {  // the products of chunk j - SS, the stage's last user, finished
                     ok = __all_sync(0xffffffffu,
-                                    wait_or_abort(smem_addr(&src_empty[s]), (uint32_t)((j / SS - 1) & 1), abort));
+                                    wait_sleep_or_abort(smem_addr(&src_empty[s]), (uint32_t)((j / SS - 1) & 1), abort));
                     if (!ok) break;
                 }
                 if (leader) {
@@ -469,6 +507,7 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
         const float ks = a.ks;
         int n = 0, sa = 0, ss = 0;
         uint32_t pa = 0, ps = 0;
+        bool src_ready = false;  // the panel chunk of the next chunk was seen complete
         for (int64_t it = 0; it < icount && ok; ++it) {
             const int64_t item = ifirst + it * istep;
             const int64_t seg = seg_of(item), tile = item - seg * n_tiles;
@@ -481,17 +520,35 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
             const int nc = chunks_of(seg);
             int64_t src0 = seg * SEG_CHUNKS * KS;
             for (int c = 0; c < nc; ++c, ++n, src0 += KS) {
-                if (n >= AS) ok = wait_or_abort(smem_addr(&mma_done[sa]), pa ^ 1u, abort);
-                ok = ok && wait_or_abort(smem_addr(&src_full[ss]), ps, abort);
+                // The waits sit where their latency overlaps the special-function
+                // work: the panel chunk before the first group, the tile stage (free
+                // once the products of chunk n - A_STAGES finished) after it, and a
+                // non-blocking test of the next chunk's panel after the last group.
+                if (!src_ready) ok = wait_or_abort(smem_addr(&src_full[ss]), ps, abort);
                 ok = __all_sync(0xffffffffu, ok);  // tcgen05.st is warp-collective
                 if (!ok) break;
-                tc_fence_after();
                 const unsigned char *src = smem + ss * C::CHUNK_BYTES;
                 const uint32_t ta_hi = lane_base + (uint32_t)(C::ACC + sa * 2 * A_COLS), ta_lo = ta_hi + A_COLS;
-                if (t0 < src0 + KS && src0 < t0 + M)
-                    gen_chunk<true>(src, ta_hi, ta_lo, tx, ty, tz, tgt, src0, slice);
-                else
-                    gen_chunk<false>(src, ta_hi, ta_lo, tx, ty, tz, tgt, src0, slice);
+                const bool diag = t0 < src0 + KS && src0 < t0 + M;  // the chunk holds targets of this tile
+#pragma unroll
+                for (int q = 0; q < GROUPS_PER_CHUNK; ++q) {
+                    Group g;
+                    if (diag)
+                        gen_group<true>(src, q, tx, ty, tz, tgt, src0, slice, g);
+                    else
+                        gen_group<false>(src, q, tx, ty, tz, tgt, src0, slice, g);
+                    if (q == 0) {
+                        if (n >= AS) ok = wait_or_abort(smem_addr(&mma_done[sa]), pa ^ 1u, abort);
+                        ok = __all_sync(0xffffffffu, ok);
+                        if (!ok) break;
+                        tc_fence_after();
+                    }
+                    st_group(ta_hi, ta_lo, q, slice, g);
+                }
+                if (!ok) break;
+                const int ss_next = ss + 1 == SS ? 0 : ss + 1;
+                const uint32_t ps_next = ss + 1 == SS ? ps ^ 1u : ps;
+                src_ready = __all_sync(0xffffffffu, mbar_test_wait(smem_addr(&src_full[ss_next]), ps_next));
                 tmem_st_wait();
                 tc_fence_before();
                 __syncwarp();
@@ -500,10 +557,8 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
                     sa = 0;
                     pa ^= 1;
                 }
-                if (++ss == SS) {
-                    ss = 0;
-                    ps ^= 1;
-                }
+                ss = ss_next;
+                ps = ps_next;
             }
             if (!ok) break;
             // epilogue: this item's accumulator, [hi*hi + lo*hi | hi*lo]
@@ -514,25 +569,14 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
             constexpr int COLS = C::N / GROUPS;    // accumulator columns per warp
             const int grp = warp >> 2;
             const int64_t trow = t0 + quad * 32 + lane;
-            constexpr int LD = COLS >= 16 ? 16 : 8;  // columns per tcgen05.ld
+            constexpr int LD = 8;  // columns per tcgen05.ld
             static_assert(COLS % LD == 0, "accumulator columns per warp");
 #pragma unroll
             for (int cb = 0; cb < COLS / LD; ++cb) {
                 const int col0 = grp * COLS + cb * LD;
-                uint32_t r0[16], r1[16];
-                if (LD == 16) {
-                    tmem_ld16(lane_base + (uint32_t)col0, r0);
-                    tmem_ld16(lane_base + (uint32_t)(C::N + col0), r1);
-                } else {
-                    uint32_t q0[8], q1[8];
-                    tmem_ld8(lane_base + (uint32_t)col0, q0);
-                    tmem_ld8(lane_base + (uint32_t)(C::N + col0), q1);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        r0[i] = q0[i];
-                        r1[i] = q1[i];
-                    }
-                }
+                uint32_t r0[8], r1[8];
+                tmem_ld8(lane_base + (uint32_t)col0, r0);
+                tmem_ld8(lane_base + (uint32_t)(C::N + col0), r1);
                 tmem_ld_wait();
                 if (trow < nq) {
 #pragma unroll
