@@ -47,7 +47,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gyps", choices=["gyps", "reference"])
     p.add_argument("--workload", default=WORKLOAD,
-                   choices=[WORKLOAD, "batch12_r64", "precond_ellipsoids", "sphere163842_k64_q3_r16"])
+                   choices=[WORKLOAD, "batch12_r64", "precond_ellipsoids", "sphere163842_k64_q3_r16",
+                            "assemble_sphere10242"])
     p.add_argument("--precond-meshes", type=int, default=125, help="training meshes (16 solves each)")
     p.add_argument("--precond-steps", type=int, default=3000)
     p.add_argument("--precond-test", type=int, default=8)
@@ -59,6 +60,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--solve", action="store_true", help="also time GMRES to 1e-6 (FP32 + FP64 check)")
     p.add_argument("--solve-fp64", action="store_true", help="also time the plain FP64 GMRES (minutes)")
+    p.add_argument("--precond-file", default="",
+                   help="sphere163842_k64_q3_r16 --solve: learned preconditioner saved by --save-precond")
+    p.add_argument("--solve-maxit", type=int, default=1500)
     return p.parse_args()
 
 
@@ -470,6 +474,65 @@ def run_precond(args):
     print(json.dumps(line), flush=True)
 
 
+def mie_density_sphere(k, d, pts):
+    """Density of the sound-soft unit sphere for p_inc = exp(ik d.x) (Mie series,
+    the exact solution the discrete one converges to): sum_n (2n+1) i^n
+    P_n(d.x) / (i k h_n(k)); measurement only."""
+    from scipy.special import eval_legendre, spherical_jn, spherical_yn
+    d = np.asarray(d, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    c = (pts / np.linalg.norm(pts, axis=1, keepdims=True)) @ d
+    lam = np.zeros(pts.shape[0], dtype=np.complex128)
+    for n in range(int(np.ceil(k + 4.0 * k ** (1.0 / 3.0) + 10)) + 1):
+        lam += (2 * n + 1) * (1j ** n) * eval_legendre(n, c) / (1j * k * (spherical_jn(n, k) + 1j * spherical_yn(n, k)))
+    return lam
+
+
+def solve_large(g, mesh, v, t, k, F, dirs, args):
+    """Workload sphere163842_k64_q3_r16, --solve: (flexible) GMRES to 1e-6 on all
+    16 plane waves, tensor-core working operator, FP32 CUDA-core operator for the
+    true residual (an FP64 residual over the whole mesh would cost minutes per
+    check); then the FP64 residual on the exact rows of the vertices inside a
+    patch of 4096 triangles and the error against the Mie series at 4096 sampled
+    vertices."""
+    import torch
+    P = None
+    if args.precond_file:
+        P = g.Precond(64, 4)
+        P.load(args.precond_file)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, rep = g.gmres_solve(mesh, k, F, tol=1e-6, restart=300, maxit=args.solve_maxit, prec="tc_bf16x3",
+                           check_prec="fp32", max_refine=2, precond=P)
+    torch.cuda.synchronize()
+    seconds = time.perf_counter() - t0
+    patch = 4096
+    tot = np.bincount(t.ravel(), minlength=mesh.nv)
+    inside = np.bincount(t[:patch].ravel(), minlength=mesh.nv)
+    rows = np.flatnonzero((inside == tot) & (tot > 0))
+    t1 = time.perf_counter()
+    Y = g.sl_apply(mesh, k, X, prec="fp64", tri_range=(0, patch))
+    torch.cuda.synchronize()
+    t_fp64 = time.perf_counter() - t1
+    Fr, Yr = F.cpu().numpy()[rows], Y.cpu().numpy()[rows]
+    res64 = np.linalg.norm(Fr - Yr, axis=0) / np.linalg.norm(Fr, axis=0)
+    samp = np.sort(np.random.default_rng(7).choice(mesh.nv, 4096, replace=False))
+    Xs = X.cpu().numpy()[samp]
+    mie = []
+    for j in range(len(dirs)):
+        lam = mie_density_sphere(k, dirs[j], v[samp])
+        mie.append(float(np.linalg.norm(Xs[:, j] - lam) / np.linalg.norm(lam)))
+    return {"tol": 1e-6, "seconds": seconds, "iterations": rep.iterations, "applies": rep.applies,
+            "check_applies": rep.check_applies, "refinements": rep.refinements, "status": rep.status,
+            "precond": "learned (flexible GMRES)" if P is not None else "none",
+            "precond_dropped": bool(rep.precond_fallback), "restart": 300,
+            "working": "tc_bf16x3", "check": "fp32",
+            "residual_check_max": float(np.max(rep.true_residual)),
+            "fp64_rows": int(rows.size), "fp64_patch_triangles": patch, "fp64_check_s": t_fp64,
+            "fp64_residual_rows_max": float(res64.max()), "fp64_residual_rows_median": float(np.median(res64)),
+            "mie_vertices": int(samp.size), "mie_rel_err_max": max(mie), "mie_rel_err_median": float(np.median(mie))}
+
+
 def run_large(args):
     """Workload sphere163842_k64_q3_r16: icosphere with 327680 triangles,
     q = 3 (983040 points), k = 64, 16 plane waves (directions seed 7); one step
@@ -519,11 +582,61 @@ def run_large(args):
                      "frac": pairs / (far_ms * 1e-3) / 1e9 / peak, "traffic": None, "kernel": "far_tc_kernel"},
         "gpu_launches": int(prof["launches"]), "clocks": clk,
     }
+    if args.solve:
+        line["solve"] = solve_large(g, mesh, v, t, cfg["k"], x, dirs, args)
+    print(json.dumps(line), flush=True)
+
+
+def run_assemble(args):
+    """Workload assemble_sphere10242: dense Galerkin matrix (a6) of the icosphere
+    with 20480 triangles (10242 vertices), q = 3, k = 16: Nv^2 complex entries
+    (1.68 GB), triangle-pair blocks with FP64 accumulation, plus the correction;
+    kernel values in FP32 (MUFU) or FP64.  Reported: assembly time, the bytes of
+    V written per second (16 Nv^2 / t) and Gauss pairs per second."""
+    import torch
+
+    import paper_1804_00995_gb300 as g
+    from paper_1804_00995_gb300 import build as gb
+    gb.build()
+    v, t = synth.icosphere(5)
+    mesh = g.Mesh(v, t, 3)
+    k = 16.0
+    props = torch.cuda.get_device_properties(0)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        V = g.sl_assemble(mesh, k, prec=prec)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        stream = torch.cuda.current_stream()
+        clocks = ClockSampler(smi_id_of(props))
+        clocks.start()
+        time.sleep(0.3)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            g.sl_assemble(mesh, k, prec=prec)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        out[prec] = {"ms": ms, "v_write_gbs": 16.0 * mesh.nv ** 2 / (ms * 1e-3) / 1e9,
+                     "gauss_pairs_per_s": float(mesh.nq) ** 2 / (ms * 1e-3), "clocks": clk}
+        del V
+    line = {
+        "metric": "dense single-layer assembly (a6): ms, V bytes written per second", "value": out["fp32"]["ms"],
+        "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "data": "synthetic",
+        "dtype": "f32 kernel values, f64 sums",
+        "config": {"workload": "assemble_sphere10242", "nv": mesh.nv, "nt": mesh.nt, "q": 3, "k": k,
+                   "v_bytes": 16 * mesh.nv ** 2},
+        "fp32": out["fp32"], "fp64": out["fp64"],
+    }
     print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
+    if args.workload == "assemble_sphere10242":
+        run_assemble(args)
+        return
     if args.workload == "sphere163842_k64_q3_r16":
         run_large(args)
         return
