@@ -154,8 +154,9 @@ gyps_status gyps_near_correct(gyps_mesh_t mesh, int nrhs, const void *X, int64_t
  * LHS = integral(...)/(4 pi) + regularize(...)/(4 pi)):
  *     V = (1/4pi) Phi^T W G W Phi + C,   nv x nv complex double2,
  * column-major with ldv >= nv; V_ij pairs test function i with trial
- * function j.  prec: GYPS_PREC_FP64 or GYPS_PREC_FP32 (kernel values in FP32,
- * sums in FP64).  Errors: INVALID, UNSUPPORTED, CUDA.
+ * function j.  prec: GYPS_PREC_FP64 or GYPS_PREC_FP32 (kernel values and the
+ * partial sums of one thread, at most 6 q^2 terms, in FP32; added up in FP64).
+ * Errors: INVALID, UNSUPPORTED (prec, or more than 65535 triangles), CUDA.
  */
 gyps_status gyps_sl_assemble(gyps_mesh_t mesh, double k, int prec, void *V, int64_t ldv, void *stream);
 

@@ -143,6 +143,20 @@ def test_dense_assembly_sphere642(g):
         assert np.linalg.norm(got32 - ref) / np.linalg.norm(ref) < 1e-5
 
 
+@pytest.mark.parametrize("q", [1, 7])
+def test_dense_assembly_other_rules(g, q):
+    """Dense assembly with the 1- and 7-point rules (both kernels: FP64 triangle
+    pairs, FP32 vertex x triangle) on a 320-triangle ellipsoid."""
+    v, t = synth.ellipsoid(2, (0.8, 1.2, 1.5), (0.3, 1.0, -0.4), 0.7)
+    om = oracle.Mesh(v, t, q)
+    gm = g.Mesh(v, t, q)
+    ref = om.assemble(7.0)
+    got = to_np(g.sl_assemble(gm, 7.0, prec="fp64"))
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+    got32 = to_np(g.sl_assemble(gm, 7.0, prec="fp32"))
+    assert np.linalg.norm(got32 - ref) / np.linalg.norm(ref) < 1e-5
+
+
 def test_gmres_sphere642_matches_lu(g):
     """Workload sphere642_k5_q3: FP64 GMRES against the oracle's LU solve.  A
     residual tol bounds the solution error by cond(V) tol, so the LU comparison
