@@ -192,6 +192,10 @@ def test_tiny_meshes_and_ragged_tails(g):
             for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5)):
                 y = to_np(g.sl_apply(gm, 2.0, torch.as_tensor(x).cuda(), prec=prec))
                 assert rel(y, om.apply(2.0, x)) < tol
+            # tensor-core form: one target tile and one source chunk, mostly padding
+            x16 = synth.random_complex(np.random.default_rng(10 + q), nv, 16)
+            y16 = to_np(g.sl_apply(gm, 2.0, torch.as_tensor(x16).cuda(), prec="tc_bf16x3"))
+            assert rel(y16, om.apply(2.0, x16)) < 1e-4
 
 
 def test_invalid_inputs(g):
