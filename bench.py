@@ -159,6 +159,35 @@ def sm_peak_pairs(num_sms, mhz):
     return num_sms * MUFU_PER_CLK_PER_SM / MUFU_PER_PAIR * mhz * 1e6
 
 
+def far_roofline(achieved_gpairs, prec, nrhs, num_sms, mhz):
+    """Roofline of the dense kernel product.  CUDA cores: the MUFU bound (3
+    special-function results per pair).  Tensor cores: the lower of that bound
+    and the tensor-pipe bound of the three split products, 3 x 8 R flop per pair
+    for a pass of R right-hand sides (measured bf16 burst rate); when the tensor
+    pipe binds, achieved and peak are stated in TFLOP/s."""
+    sfu = sm_peak_pairs(num_sms, mhz) / 1e9
+    out = {"bound": "alu", "achieved": achieved_gpairs, "peak": sfu, "unit": UNIT, "frac": achieved_gpairs / sfu,
+           "peak_basis": f"{num_sms} SMs x {MUFU_PER_CLK_PER_SM}/{MUFU_PER_PAIR} pairs/clk x {mhz:.0f} MHz "
+                         f"(measured sm_max_mhz)"}
+    if prec == "fp32" or nrhs < 16:
+        return out
+    r_pass = 64 if nrhs >= 64 else (32 if nrhs > 16 else 16)
+    flop_per_pair = 24.0 * r_pass
+    try:
+        tflops = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+        basis = "measured bf16 burst"
+    except Exception:
+        tflops, basis = 1900.0, "fallback bf16 burst"
+    tensor = tflops * 1e12 / flop_per_pair / 1e9
+    out["tensor_peak_gpairs"] = tensor
+    if tensor < sfu:
+        out.update({"bound": "tensor", "achieved": achieved_gpairs * flop_per_pair / 1e3, "peak": tflops,
+                    "unit": "TFLOP/s", "frac": achieved_gpairs / tensor,
+                    "peak_basis": f"{basis} {tflops:.0f} TFLOP/s; 3 split products x 8 x {r_pass} flop per pair "
+                                  f"(the MUFU bound, {sfu:.0f} GPairs/s, is higher)"})
+    return out
+
+
 # ---------------------------------------------------------------- CPU baseline
 def oracle_sample(v, t, cfg, seconds, seed=1804):
     """Times the oracle's apply restricted to a sample of output rows: all
@@ -302,7 +331,6 @@ def run_gyps(args, rank, world, local_rank):
         peak_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
     except Exception:
         peak_mhz = clk.get("sm_max_mhz") or 2070.0
-    peak = sm_peak_pairs(props.multi_processor_count, peak_mhz) / 1e9
     traffic = far_traffic_per_launch() if (prec == "fp32" and nrhs == 1) else None
 
     # end to end through the public API with host buffers (pinned), copies inside
@@ -356,12 +384,10 @@ def run_gyps(args, rank, world, local_rank):
                        "k": k, "quad_points": cfg["q"], "nrhs": nrhs, "far": prec, "near": "fp64",
                        "l2": "flushed (512 MB write) before every step", "pairs_per_step": pairs,
                        "ranks": "independent replicas, one right-hand side each"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-                         "traffic": traffic,
-                         "kernel": "far32_kernel<1,4,false>" if prec == "fp32" else "far_tc_kernel",
-                         "peak_basis": f"{props.multi_processor_count} SMs x {MUFU_PER_CLK_PER_SM}/{MUFU_PER_PAIR} "
-                                       f"pairs/clk x {peak_mhz:.0f} MHz (measured sm_max_mhz)",
-                         "far_ms_per_launch": far_ms},
+            "roofline": dict(far_roofline(achieved, prec, nrhs, props.multi_processor_count, peak_mhz),
+                             traffic=traffic,
+                             kernel="far32_kernel<1,4,false>" if prec == "fp32" else "far_tc_kernel",
+                             far_ms_per_launch=far_ms),
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nv * 16 * nrhs,
                     "d2h_bytes_per_step": nv * 16 * nrhs},
@@ -569,7 +595,6 @@ def run_large(args):
     prof = mesh.profile_read()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     pairs = float(mesh.nq) ** 2
-    peak = sm_peak_pairs(props.multi_processor_count, 2070.0) / 1e9
     far_ms = prof["far_ms"] / max(prof["far_launches"], 1) * prof["far_launches"] / max(prof["applies"], 1)
     line = {
         "metric": "GPairs/s single-layer apply, 16 right-hand sides", "value": pairs / (ms * 1e-3) / 1e9,
@@ -578,8 +603,8 @@ def run_large(args):
         "pair_rhs_per_s": pairs * 16 / (ms * 1e-3),
         "config": {"workload": "sphere163842_k64_q3_r16", "nv": mesh.nv, "nq": mesh.nq, "k": cfg["k"], "nrhs": 16,
                    "far": prec, "near": "fp64", "l2": "inputs larger than L2"},
-        "roofline": {"bound": "alu", "achieved": pairs / (far_ms * 1e-3) / 1e9, "peak": peak, "unit": UNIT,
-                     "frac": pairs / (far_ms * 1e-3) / 1e9 / peak, "traffic": None, "kernel": "far_tc_kernel"},
+        "roofline": dict(far_roofline(pairs / (far_ms * 1e-3) / 1e9, prec, 16, props.multi_processor_count, 2070.0),
+                         traffic=None, kernel="far_tc_kernel" if prec != "fp32" else "far32_kernel"),
         "gpu_launches": int(prof["launches"]), "clocks": clk,
     }
     if args.solve:
