@@ -54,6 +54,9 @@ typedef enum {
     GYPS_PREC_FP64 = 0,         /* G and G u in FP64 (the plain reference form) */
     GYPS_PREC_FP32 = 1,         /* G in FP32 on the CUDA cores, compensated FP32 sums */
     GYPS_PREC_TC_BF16X3 = 2,    /* G tile x RHS panel on tensor cores, bf16 hi+lo split */
+    GYPS_PREC_DF64 = 3,         /* G and G u in double-float (hi + lo FP32 pairs, about 44 bits) on the
+                                   FP32 pipe: FP64-class accuracy (about 1e-12 from FP64) at several
+                                   times the FP64 pipe's speed; for true-residual checks */
     GYPS_PREC_AUTO = 4          /* FP32 below 16 right-hand sides, tensor cores above */
 } gyps_prec;
 

@@ -27,7 +27,7 @@ __all__ = [
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgyps.so")
 
-PREC = {"fp64": 0, "fp32": 1, "tc_bf16x3": 2, "auto": 4}
+PREC = {"fp64": 0, "fp32": 1, "tc_bf16x3": 2, "df64": 3, "auto": 4}
 NO_NEAR = 0x1
 
 _STATUS = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "NAN", 6: "TIMEOUT", 7: "UNSUPPORTED"}

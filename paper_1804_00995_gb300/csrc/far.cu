@@ -424,7 +424,7 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
     if (prec == GYPS_PREC_AUTO) prec = (nrhs >= 16 && k > 0.0 && full) ? GYPS_PREC_TC_BF16X3 : GYPS_PREC_FP32;
     if (prec == GYPS_PREC_TC_BF16X3 && (k <= 0.0 || !full))
         return set_error(GYPS_ERR_UNSUPPORTED, "tensor-core precision needs k > 0 and all triangles");
-    if (prec != GYPS_PREC_FP32 && prec != GYPS_PREC_FP64 && prec != GYPS_PREC_TC_BF16X3)
+    if (prec != GYPS_PREC_FP32 && prec != GYPS_PREC_FP64 && prec != GYPS_PREC_TC_BF16X3 && prec != GYPS_PREC_DF64)
         return set_error(GYPS_ERR_INVALID, "unknown precision");
     const int64_t t_begin = tri_begin * m->q, t_end = tri_end * m->q;
 
@@ -462,7 +462,12 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
             interp64_kernel<<<g, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, ldu, X, ldx, nrhs, u64);
             GYPS_CUDA(cudaGetLastError());
             ti.done(1);
-            for (int c0 = 0; c0 < nrhs;) {
+            for (int c0 = 0; c0 < nrhs && prec == GYPS_PREC_DF64;) {
+                const int w = nrhs - c0 >= 4 ? 4 : nrhs - c0 >= 2 ? 2 : 1;
+                GYPS_TRY(run_far_df(m, k, u64, ldu, c0, w, v, ldv, t_begin, t_end, s));
+                c0 += w;
+            }
+            for (int c0 = 0; c0 < nrhs && prec == GYPS_PREC_FP64;) {
                 int w = chunk_width(nrhs - c0);
                 gyps_status st;
                 switch (w) {
@@ -551,7 +556,8 @@ extern "C" gyps_status gyps_sl_apply(gyps_mesh_t h, double k, int nrhs, const vo
     }
     if (tri_begin < 0 || tri_end > m->nt || tri_begin > tri_end)
         return set_error(GYPS_ERR_INVALID, "triangle range outside [0, nt]");
-    if (prec != GYPS_PREC_FP64 && prec != GYPS_PREC_FP32 && prec != GYPS_PREC_TC_BF16X3 && prec != GYPS_PREC_AUTO)
+    if (prec != GYPS_PREC_FP64 && prec != GYPS_PREC_FP32 && prec != GYPS_PREC_TC_BF16X3 && prec != GYPS_PREC_AUTO &&
+        prec != GYPS_PREC_DF64)
         return set_error(GYPS_ERR_INVALID, "unknown precision");
     if (prec == GYPS_PREC_TC_BF16X3 && nrhs < 16)
         return set_error(GYPS_ERR_UNSUPPORTED, "tensor-core precision needs at least 16 right-hand sides");

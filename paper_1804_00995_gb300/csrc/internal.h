@@ -146,6 +146,8 @@ cudaError_t launch_near_build(const Mesh &m, cudaStream_t s);
 // a2-a5: one matrix-free apply with device pointers
 gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
                          int prec, uint32_t flags, int64_t tri_begin, int64_t tri_end, cudaStream_t s);
+gyps_status run_far_df(Mesh *m, double k, const double2 *u64, int64_t ldu, int c0, int w, double2 *v, int64_t ldv,
+                       int64_t t_begin, int64_t t_end, cudaStream_t s);
 gyps_status far_tc(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, double2 *v, int64_t ldv,
                    cudaStream_t s);
 cudaError_t launch_near_spmv(const Mesh &m, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
