@@ -177,6 +177,44 @@ def test_coincident_block_vs_brute_force_helmholtz():
     assert errs[0] / errs[1] > 3.5
 
 
+@pytest.mark.parametrize("shared", ["edge", "vertex"])
+def test_adjacent_pair_vs_brute_force_helmholtz(shared):
+    """Two triangles that share an edge (or a vertex), slightly out of plane:
+    the whole 4x4 (5x5) V, far part with the correction, against the same outer
+    Gauss rule with the inner integrals of exp(ikr)/r by Duffy quadrature over
+    each triangle.  The difference is the Gauss error of the smooth remainder
+    (exp(ikr) - 1)/r, O(h^2); a wrong sign, a transposed block or a dropped
+    correction between neighbours leaves an O(1) or O(h) error."""
+    k = 4.0
+    errs = []
+    for h in (0.1, 0.05):
+        P = np.array([[0.0, 0.0, 0.0], [h, 0.0, 0.0], [0.4 * h, 0.9 * h, 0.0], [0.6 * h, -0.8 * h, 0.15 * h],
+                      [-0.7 * h, -0.2 * h, 0.1 * h], [-0.3 * h, -0.9 * h, -0.05 * h]])
+        if shared == "edge":
+            tri = np.array([[0, 1, 2], [1, 0, 3]], dtype=np.int32)
+        else:
+            tri = np.array([[0, 1, 2], [0, 4, 5]], dtype=np.int32)
+        used = np.unique(tri)
+        remap = {int(v): i for i, v in enumerate(used)}
+        tri = np.vectorize(remap.get)(tri).astype(np.int32)
+        P = P[used]
+        m = oracle.Mesh(P, tri, 7)
+        V = m.assemble(k)
+        bary, _ = oracle.quad_rule(7)
+        ref = np.zeros_like(V)
+        for a in range(2):
+            for b in range(2):
+                Pb = [P[v] for v in tri[b]]
+                for kk in range(7):
+                    xk = m.x[7 * a + kk]
+                    inner = inner_integral(xk, Pb, lambda r: np.exp(1j * k * r) / r, ng=60)
+                    blk = m.w[7 * a + kk] * np.outer(bary[kk], inner) / (4 * np.pi)
+                    ref[np.ix_(tri[a], tri[b])] += blk
+        errs.append(np.abs(V - ref).max() / np.abs(ref).max())
+    assert errs[1] < 5e-5
+    assert errs[0] / errs[1] > 3.5
+
+
 # ------------------------------------------------------------- far part
 def test_far_part_is_complex_symmetric():
     """Eq. (BEM) with the same points and space on both sides: Phi^T W G W Phi
