@@ -58,8 +58,9 @@ def parse():
                    help="kernel-product arithmetic (tc_bf16x3: tensor cores, needs nrhs >= 16)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--solve", action="store_true",
-                   help="also time GMRES to 1e-6 (FP32 operator, double-float true-residual checks)")
+    p.add_argument("--solve", action=argparse.BooleanOptionalAction, default=None,
+                   help="also time GMRES to 1e-6 (FP32 / tensor-core operator, double-float true-residual "
+                        "checks); on by default for the default workload, off for the others")
     p.add_argument("--solve-fp64", action="store_true", help="also time the plain FP64 GMRES (minutes)")
     p.add_argument("--precond-file", default="",
                    help="sphere163842_k64_q3_r16 --solve: learned preconditioner saved by --save-precond")
@@ -354,7 +355,7 @@ def run_gyps(args, rank, world, local_rank):
     e2e_value = world * pairs / e2e_mean / 1e9
 
     solve = None
-    if args.solve or args.solve_fp64:
+    if args.solve is not False or args.solve_fp64:
         f = g.rhs_planewave(mesh, k, [cfg["dirs"][0]])
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
