@@ -463,7 +463,7 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
             GYPS_CUDA(cudaGetLastError());
             ti.done(1);
             for (int c0 = 0; c0 < nrhs && prec == GYPS_PREC_DF64;) {
-                const int w = nrhs - c0 >= 4 ? 4 : nrhs - c0 >= 2 ? 2 : 1;
+                const int w = chunk_width(nrhs - c0);
                 GYPS_TRY(run_far_df(m, k, u64, ldu, c0, w, v, ldv, t_begin, t_end, s));
                 c0 += w;
             }

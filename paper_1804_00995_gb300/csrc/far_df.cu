@@ -200,6 +200,7 @@ gyps_status run_far_df(Mesh *m, double k, const double2 *u64, int64_t ldu, int c
     const unsigned grid = (unsigned)((t_end - t_begin + 127) / 128);
     StageTimer tf(m, s, 1);
     switch (w) {
+    case 8: dfl::far_df_kernel<8><<<grid, 128, 0, s>>>(m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, v, ldv); break;
     case 4: dfl::far_df_kernel<4><<<grid, 128, 0, s>>>(m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, v, ldv); break;
     case 2: dfl::far_df_kernel<2><<<grid, 128, 0, s>>>(m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, v, ldv); break;
     default: dfl::far_df_kernel<1><<<grid, 128, 0, s>>>(m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, v, ldv); break;

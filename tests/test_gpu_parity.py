@@ -76,7 +76,7 @@ def test_apply_fp64(pair, g, k, nrhs):
 
 
 @pytest.mark.parametrize("k", [0.0, 5.0, 16.0, 64.0])
-@pytest.mark.parametrize("nrhs", [1, 3, 6])
+@pytest.mark.parametrize("nrhs", [1, 3, 6, 11])
 def test_apply_df64(pair, g, k, nrhs):
     """Double-float products: FP64-class accuracy against the oracle and within
     1e-11 of the FP64 GPU form (k = 64 puts phases k r up to about 130 rad)."""
