@@ -164,6 +164,30 @@ gyps_status gyps_near_correct(gyps_mesh_t mesh, int nrhs, const void *X, int64_t
 gyps_status gyps_sl_assemble(gyps_mesh_t mesh, double k, int prec, void *V, int64_t ldv, void *stream);
 
 /*
+ * Single-layer potential at points (the radiation operator of the listing in
+ * Sec. 6.4: Sdom = integral(points, S2, Gxy, Vh)/(4 pi)
+ * + regularize(points, S2, '[1/r]', Vh)/(4 pi)):
+ *     P[i, c] = (1/4pi) sum_l G(x_i, y_l) eta_l sum_j phi_j(y_l) X[j, c] + R[i, c],
+ * G = exp(ik r)/r at the mesh's Gauss points y_l (weights eta_l); R: for every
+ * triangle b whose centroid lies within twice its largest centroid-vertex
+ * distance of x_i, (1/4pi) sum_j (int_b lambda_j(y)/|x_i - y| dy, closed form,
+ * minus the Gauss sum of lambda_j/|x_i - y_l| over b) X[v_j(b), c] (Sec. 5.2).
+ *   pts   npts x 3 doubles (x, y, z per point), host or device.  A point must
+ *         not coincide with a Gauss point of the mesh (the far sum would be
+ *         infinite there).
+ *   X     nv x nrhs complex double2 (the density, e.g. a solution of
+ *         gyps_gmres_solve), leading dimension ldx.
+ *   P     npts x nrhs complex double2, leading dimension ldp >= npts.
+ *   prec  GYPS_PREC_FP32 (AUTO), GYPS_PREC_FP64 or GYPS_PREC_DF64 for the far
+ *         sum; the regularisation is FP64.
+ * npts = 0 returns at once (pts and P may then be NULL).
+ * Synchronous. Errors: INVALID (sizes, NULL, non-finite host points),
+ * UNSUPPORTED (tensor-core precision), CUDA, TIMEOUT.
+ */
+gyps_status gyps_sl_potential(gyps_mesh_t mesh, double k, int64_t npts, const double *pts, int nrhs,
+                              const void *X, int64_t ldx, void *P, int64_t ldp, int prec, void *stream);
+
+/*
  * Right-hand sides of the sound-soft example (Sec. 6.4, RHS = integral(S2, Vh,
  * PW)): F_ij = sum_k w_k phi_i(x_k) exp(i k d_j . x_k) by the mesh's rule.
  *   dirs  HOST, nrhs x 3 doubles (propagation directions d_j, used as given).

@@ -300,6 +300,37 @@ class Mesh:
         """Dense V = (1/4pi) Phi^T W G W Phi + C (Nv, Nv) complex."""
         return self.assemble_far(k) + self.near.toarray()
 
+    def potential(self, k, pts, x):
+        """Single-layer potential of the density x (nv, nrhs) at points pts (npts, 3):
+        the radiation operator of the listing in Sec. 6.4,
+        integral(points, S2, Gxy, Vh)/(4 pi) + regularize(points, S2, '[1/r]', Vh)/(4 pi).
+        The Gauss-point sum of exp(ikr)/r; then, for each triangle whose centroid
+        lies within twice its largest centroid-vertex distance of the point (the
+        reading of "close enough" for points), the closed-form integral of
+        lambda_j / |x - y| over it minus the Gauss sum of the same (Sec. 5.2).
+        Points must not coincide with Gauss points."""
+        x = np.asarray(x, dtype=np.complex128)
+        one = x.ndim == 1
+        if one:
+            x = x[:, None]
+        pts = np.ascontiguousarray(np.asarray(pts, dtype=np.float64).reshape(-1, 3))
+        u = self.w[:, None] * (self.phi @ x)
+        v = kernel_matvec(pts, None, self.x, u, k)
+        bary, _ = quad_rule(self.q)
+        P = self.vtx[self.tri]                                  # (nt, 3, 3)
+        cen = P.mean(axis=1)
+        rad2 = 4.0 * np.max(np.sum((P - cen[:, None, :]) ** 2, axis=2), axis=1)
+        for i, p in enumerate(pts):
+            for b in np.flatnonzero(np.sum((cen - p) ** 2, axis=1) < rad2):
+                exact = p1_inv_r(p, *P[b])
+                ys = self.x[b * self.q:(b + 1) * self.q]
+                r = np.linalg.norm(ys - p, axis=1)
+                keep = r > 0.0
+                gauss = (self.w[b * self.q:(b + 1) * self.q][keep] / r[keep]) @ bary[keep]
+                v[i] += (exact - gauss) @ x[self.tri[b]]
+        v /= 4.0 * np.pi
+        return v[:, 0] if one else v
+
     def rhs_planewave(self, k, dirs):
         """F_i = int phi_i exp(ik d.x) by the domain's rule, one column per direction (Sec. 6.4)."""
         dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))

@@ -96,6 +96,9 @@ _SIGS = {
                            ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "gyps_sl_assemble": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                           ctypes.c_void_p], ctypes.c_int),
+    "gyps_sl_potential": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
+                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p],
+                          ctypes.c_int),
     "gyps_rhs_planewave": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                             ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "gyps_gmres_solve": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
@@ -302,6 +305,27 @@ def sl_assemble(mesh: Mesh, k: float, prec: str = "fp64", device=None, stream=No
     v = _empty_colmajor(mesh.nv, mesh.nv, dev)
     _check(load().gyps_sl_assemble(mesh.handle, float(k), PREC[prec], v.data_ptr(), mesh.nv, _stream(stream)))
     return v
+
+
+def sl_potential(mesh: Mesh, k: float, pts, X, prec: str = "fp32", stream=None):
+    """P (npts, nrhs): the single-layer potential of the density X at the points
+    pts (npts, 3), with the [1/r] regularisation near the surface (gyps_sl_potential).
+    pts and X on the device give P on the device; host inputs give host output."""
+    torch = _torch()
+    one = (hasattr(X, "dim") and X.dim() == 1) or (not hasattr(X, "dim") and np.asarray(X).ndim == 1)
+    x, nrhs, ldx = _colmajor(X, mesh.nv, "X")
+    if hasattr(pts, "dim"):
+        p = pts.to(torch.float64).contiguous()
+    else:
+        p = torch.as_tensor(np.ascontiguousarray(np.asarray(pts, dtype=np.float64)))
+    if p.dim() != 2 or p.shape[1] != 3:
+        raise ValueError("pts must be (npts, 3)")
+    npts = p.shape[0]
+    out = _empty_colmajor(max(npts, 1), nrhs, x.device)[:npts]
+    ldp = max(npts, 1)
+    _check(load().gyps_sl_potential(mesh.handle, float(k), npts, p.data_ptr(), nrhs, x.data_ptr(), ldx,
+                                    out.data_ptr(), ldp, PREC[prec], _stream(stream)))
+    return out[:, 0] if one else out
 
 
 def rhs_planewave(mesh: Mesh, k: float, dirs, device=None, stream=None):

@@ -205,15 +205,18 @@ __global__ void __launch_bounds__(FarCfg<R, T>::NT) far32_kernel(const FarArgs a
 
 // ---------------------------------------------------------------- a3: far, FP64
 // The plain FP64 form: one thread per target, all sources streamed through
-// shared memory, exp(ikr)/r from FP64 sincos and rsqrt.
+// shared memory, exp(ikr)/r from FP64 sincos and rsqrt.  Targets tgt[t] for t
+// in [t_begin, t_end); self: the targets are the sources (quadrature points),
+// so the point paired with itself takes G = ik.
 template <int R>
-__global__ void __launch_bounds__(128) far64_kernel(const double4_32a *pts, const double2 *u64, int64_t ldu, int c0, int64_t nq,
-                                                    double k, int64_t t_begin, int64_t t_end, double2 *v, int64_t ldv)
+__global__ void __launch_bounds__(128) far64_kernel(const double4_32a *tgt, const double4_32a *pts, const double2 *u64,
+                                                    int64_t ldu, int c0, int64_t nq, double k, int64_t t_begin,
+                                                    int64_t t_end, bool self, double2 *v, int64_t ldv)
 {
     __shared__ double4_32a sp[128];
     __shared__ double2 su[128][R];
     const int64_t tg = t_begin + (int64_t)blockIdx.x * 128 + threadIdx.x;
-    const double4_32a x = pts[min(tg, t_end - 1)];
+    const double4_32a x = tgt[min(tg, t_end - 1)];
     double ar[R], ai[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) ar[j] = ai[j] = 0.0;
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(128) far64_kernel(const double4_32a *pts, cons
         for (int ll = 0; ll < n; ++ll) {
             double4_32a y = sp[ll];
             double gr, gi;
-            if (s0 + ll == tg) {
+            if (self && s0 + ll == tg) {
                 gr = 0.0;
                 gi = k;
             } else {
@@ -403,12 +406,12 @@ static gyps_status run_far32(Mesh *m, double k, const double2 *X, int64_t ldx, i
 }
 
 template <int R>
-static gyps_status run_far64(Mesh *m, double k, const double2 *u64, int64_t ldu, int c0, double2 *v, int64_t ldv,
-                             int64_t t_begin, int64_t t_end, cudaStream_t s)
+static gyps_status run_far64(Mesh *m, double k, const double4_32a *tgt, bool self, const double2 *u64, int64_t ldu,
+                             int c0, double2 *v, int64_t ldv, int64_t t_begin, int64_t t_end, cudaStream_t s)
 {
     unsigned grid = (unsigned)((t_end - t_begin + 127) / 128);
     StageTimer tf(m, s, 1);
-    far64_kernel<R><<<grid, 128, 0, s>>>(m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, v, ldv);
+    far64_kernel<R><<<grid, 128, 0, s>>>(tgt, m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, self, v, ldv);
     GYPS_CUDA(cudaGetLastError());
     tf.done(1);
     return GYPS_OK;
@@ -464,17 +467,17 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
             ti.done(1);
             for (int c0 = 0; c0 < nrhs && prec == GYPS_PREC_DF64;) {
                 const int w = chunk_width(nrhs - c0);
-                GYPS_TRY(run_far_df(m, k, u64, ldu, c0, w, v, ldv, t_begin, t_end, s));
+                GYPS_TRY(run_far_df(m, k, m->d_pts64, true, u64, ldu, c0, w, v, ldv, t_begin, t_end, s));
                 c0 += w;
             }
             for (int c0 = 0; c0 < nrhs && prec == GYPS_PREC_FP64;) {
                 int w = chunk_width(nrhs - c0);
                 gyps_status st;
                 switch (w) {
-                case 8: st = run_far64<8>(m, k, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
-                case 4: st = run_far64<4>(m, k, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
-                case 2: st = run_far64<2>(m, k, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
-                default: st = run_far64<1>(m, k, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
+                case 8: st = run_far64<8>(m, k, m->d_pts64, true, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
+                case 4: st = run_far64<4>(m, k, m->d_pts64, true, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
+                case 2: st = run_far64<2>(m, k, m->d_pts64, true, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
+                default: st = run_far64<1>(m, k, m->d_pts64, true, u64, ldu, c0, v, ldv, t_begin, t_end, s); break;
                 }
                 GYPS_TRY(st);
                 c0 += w;
@@ -503,6 +506,80 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
 }
 
 // Host staging of an nv x nrhs complex block with leading dimension ld.
+// Far part of the potential at arbitrary points (the radiation operator of the
+// listing in Sec. 6.4: integral(points, S2, Gxy, Vh)).  The FP32 kernel takes
+// the points as targets numbered from nq_pad on, past every source index, so
+// its self-pair test never fires: the target and accumulator pointers are
+// shifted back by that offset (every access stays inside the point arrays).
+template <int R, int T>
+static gyps_status run_far32_points(Mesh *m, double k, const double2 *X, int64_t ldx, int c0, const float4 *tgt32,
+                                    int64_t npts, double2 *v, int64_t ldv, cudaStream_t s)
+{
+    using C = FarCfg<R, T>;
+    float *panel = reinterpret_cast<float *>(m->ws_den);
+    StageTimer ti(m, s, 0);
+    interp32_kernel<R><<<(unsigned)((m->nq_pad + 255) / 256), 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq,
+                                                                           m->nq_pad, X, ldx, c0, panel);
+    GYPS_CUDA(cudaGetLastError());
+    ti.done(1);
+    const int64_t off = m->nq_pad;
+    FarArgs a = far_args(m, panel, v + (int64_t)c0 * ldv - off, ldv, off, off + npts, C::TT, k);
+    a.tgt = tgt32 - off;
+    StageTimer tf(m, s, 1);
+    if (k > 0.0)
+        GYPS_TRY((launch_far32<R, T, false>(m, a, s)));
+    else
+        GYPS_TRY((launch_far32<R, T, true>(m, a, s)));
+    tf.done(1);
+    return GYPS_OK;
+}
+
+gyps_status far_points(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, const float4 *tgt32,
+                       const double4_32a *tgt64, int64_t npts, double2 *v, int64_t ldv, int prec, cudaStream_t s)
+{
+    GYPS_CUDA(cudaMemset2DAsync(v, ldv * sizeof(double2), 0, npts * sizeof(double2), nrhs, s));
+    if (npts == 0) return GYPS_OK;
+    if (prec == GYPS_PREC_FP32) {
+        GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(m->n_src_tiles * den_tile_floats(8)) * sizeof(float)));
+        for (int c0 = 0; c0 < nrhs;) {
+            const int w = chunk_width(nrhs - c0);
+            gyps_status st;
+            switch (w) {
+            case 8: st = run_far32_points<8, 2>(m, k, X, ldx, c0, tgt32, npts, v, ldv, s); break;
+            case 4: st = run_far32_points<4, 2>(m, k, X, ldx, c0, tgt32, npts, v, ldv, s); break;
+            case 2: st = run_far32_points<2, 4>(m, k, X, ldx, c0, tgt32, npts, v, ldv, s); break;
+            default: st = run_far32_points<1, 4>(m, k, X, ldx, c0, tgt32, npts, v, ldv, s); break;
+            }
+            GYPS_TRY(st);
+            c0 += w;
+        }
+        return GYPS_OK;
+    }
+    const int64_t ldu = m->nq;
+    GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(ldu * nrhs) * sizeof(double2)));
+    double2 *u64 = reinterpret_cast<double2 *>(m->ws_den);
+    dim3 g((unsigned)((m->nq + 255) / 256), (unsigned)nrhs);
+    interp64_kernel<<<g, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, ldu, X, ldx, nrhs, u64);
+    GYPS_CUDA(cudaGetLastError());
+    for (int c0 = 0; c0 < nrhs;) {
+        const int w = chunk_width(nrhs - c0);
+        gyps_status st;
+        if (prec == GYPS_PREC_DF64) {
+            st = run_far_df(m, k, tgt64, false, u64, ldu, c0, w, v, ldv, 0, npts, s);
+        } else {
+            switch (w) {
+            case 8: st = run_far64<8>(m, k, tgt64, false, u64, ldu, c0, v, ldv, 0, npts, s); break;
+            case 4: st = run_far64<4>(m, k, tgt64, false, u64, ldu, c0, v, ldv, 0, npts, s); break;
+            case 2: st = run_far64<2>(m, k, tgt64, false, u64, ldu, c0, v, ldv, 0, npts, s); break;
+            default: st = run_far64<1>(m, k, tgt64, false, u64, ldu, c0, v, ldv, 0, npts, s); break;
+            }
+        }
+        GYPS_TRY(st);
+        c0 += w;
+    }
+    return GYPS_OK;
+}
+
 static gyps_status stage_in(Mesh *m, const void *src, int64_t ld, int nrhs, double2 *dst, cudaStream_t s)
 {
     GYPS_CUDA(cudaMemcpy2DAsync(dst, m->nv * sizeof(double2), src, ld * sizeof(double2), m->nv * sizeof(double2), nrhs,

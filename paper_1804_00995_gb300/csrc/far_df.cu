@@ -91,11 +91,12 @@ __device__ __forceinline__ float rsqrt_mufu(float x)
     return y;
 }
 
-// exp(i phi) / r and the G u products; s: (sources) shared tiles.
+// exp(i phi) / r and the G u products for targets tgt[t], t in [t_begin, t_end);
+// self: the targets are the sources, the point paired with itself takes G = ik.
 template <int R>
-__global__ void __launch_bounds__(128) far_df_kernel(const double4_32a *pts, const double2 *u64, int64_t ldu, int c0,
-                                                     int64_t nq, double k, int64_t t_begin, int64_t t_end, double2 *v,
-                                                     int64_t ldv)
+__global__ void __launch_bounds__(128) far_df_kernel(const double4_32a *tgt, const double4_32a *pts, const double2 *u64,
+                                                     int64_t ldu, int c0, int64_t nq, double k, int64_t t_begin,
+                                                     int64_t t_end, bool self, double2 *v, int64_t ldv)
 {
     __shared__ float4 tab[kTab];
     __shared__ float4 sxy[128];     // (x hi, x lo, y hi, y lo)
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(128) far_df_kernel(const double4_32a *pts, con
     __shared__ float4 su[128][R];   // (Re hi, Re lo, Im hi, Im lo)
     for (int i = threadIdx.x; i < kTab; i += 128) tab[i] = g_sincos[i];
     const int64_t tg = t_begin + (int64_t)blockIdx.x * 128 + threadIdx.x;
-    const double4_32a x = pts[min(tg, t_end - 1)];
+    const double4_32a x = tgt[min(tg, t_end - 1)];
     const df tx = from_double(x.x), ty = from_double(x.y), tz = from_double(x.z);
     const df kd = from_double(k);
     const df step = from_double(6.283185307179586476925286766559 / kTab);  // 2 pi / kTab
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(128) far_df_kernel(const double4_32a *pts, con
         const int n = (int)min((int64_t)128, nq - s0);
         for (int ll = 0; ll < n; ++ll) {
             df gr, gi;
-            if (s0 + ll == tg) {  // the point paired with itself: G = ik
+            if (self && s0 + ll == tg) {  // the point paired with itself: G = ik
                 gr = df{0.0f, 0.0f};
                 gi = kd;
             } else {
@@ -193,17 +194,17 @@ static gyps_status ensure_table(int device, cudaStream_t s)
 }  // namespace dfl
 
 // v[t, c0 .. c0 + w) for targets [t_begin, t_end): the double-float far part.
-gyps_status run_far_df(Mesh *m, double k, const double2 *u64, int64_t ldu, int c0, int w, double2 *v, int64_t ldv,
-                       int64_t t_begin, int64_t t_end, cudaStream_t s)
+gyps_status run_far_df(Mesh *m, double k, const double4_32a *tgt, bool self, const double2 *u64, int64_t ldu, int c0,
+                       int w, double2 *v, int64_t ldv, int64_t t_begin, int64_t t_end, cudaStream_t s)
 {
     GYPS_TRY(dfl::ensure_table(m->device, s));
     const unsigned grid = (unsigned)((t_end - t_begin + 127) / 128);
     StageTimer tf(m, s, 1);
     switch (w) {
-    case 8: dfl::far_df_kernel<8><<<grid, 128, 0, s>>>(m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, v, ldv); break;
-    case 4: dfl::far_df_kernel<4><<<grid, 128, 0, s>>>(m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, v, ldv); break;
-    case 2: dfl::far_df_kernel<2><<<grid, 128, 0, s>>>(m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, v, ldv); break;
-    default: dfl::far_df_kernel<1><<<grid, 128, 0, s>>>(m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, v, ldv); break;
+    case 8: dfl::far_df_kernel<8><<<grid, 128, 0, s>>>(tgt, m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, self, v, ldv); break;
+    case 4: dfl::far_df_kernel<4><<<grid, 128, 0, s>>>(tgt, m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, self, v, ldv); break;
+    case 2: dfl::far_df_kernel<2><<<grid, 128, 0, s>>>(tgt, m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, self, v, ldv); break;
+    default: dfl::far_df_kernel<1><<<grid, 128, 0, s>>>(tgt, m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, self, v, ldv); break;
     }
     GYPS_CUDA(cudaGetLastError());
     tf.done(1);

@@ -90,6 +90,8 @@ struct Mesh {
     void *ws_v = nullptr; size_t ws_v_bytes = 0;       // target accumulators
     void *ws_stage = nullptr; size_t ws_stage_bytes = 0;  // host<->device staging
     void *ws_tc = nullptr; size_t ws_tc_bytes = 0;        // tensor-core source panel
+    void *ws_pts = nullptr; size_t ws_pts_bytes = 0;      // potential at points: point copies, far sums, staging
+    double4_32a *d_tri_cen = nullptr;                     // per triangle: centroid, (2 x largest centroid-vertex distance)^2
     float pad = 0.0f;                                     // distance of padding points
     // mesh graph for the learned preconditioner (built on first use)
     int32_t *d_adj_ptr = nullptr, *d_adj = nullptr;       // vertex neighbours over mesh edges
@@ -136,6 +138,8 @@ gyps_status grow(Mesh *m, void **buf, size_t *cap, size_t need);
 gyps_status check_mesh(gyps_mesh_t h, Mesh **out);
 gyps_status enter_device(const Mesh *m);
 bool is_device_pointer(const void *p);
+// Reads (and clears) the error word of bounded device waits; TIMEOUT if set.
+gyps_status check_err_word(Mesh *m, cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers
 // a1: quadrature points and the FP32 position panel
@@ -146,8 +150,12 @@ cudaError_t launch_near_build(const Mesh &m, cudaStream_t s);
 // a2-a5: one matrix-free apply with device pointers
 gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
                          int prec, uint32_t flags, int64_t tri_begin, int64_t tri_end, cudaStream_t s);
-gyps_status run_far_df(Mesh *m, double k, const double2 *u64, int64_t ldu, int c0, int w, double2 *v, int64_t ldv,
-                       int64_t t_begin, int64_t t_end, cudaStream_t s);
+gyps_status run_far_df(Mesh *m, double k, const double4_32a *tgt, bool self, const double2 *u64, int64_t ldu, int c0,
+                       int w, double2 *v, int64_t ldv, int64_t t_begin, int64_t t_end, cudaStream_t s);
+// Far part of the potential at npts points (tgt32 / tgt64: the points): v[i, c] = sum_l G(x_i, y_l) u_l,c
+// with u = W Phi X, no self pairs; prec FP32 | FP64 | DF64; v: npts x nrhs, ld ldv, overwritten.
+gyps_status far_points(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, const float4 *tgt32,
+                       const double4_32a *tgt64, int64_t npts, double2 *v, int64_t ldv, int prec, cudaStream_t s);
 gyps_status far_tc(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, double2 *v, int64_t ldv,
                    cudaStream_t s);
 cudaError_t launch_near_spmv(const Mesh &m, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
