@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--impl", default="gyps", choices=["gyps", "reference"])
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "batch12_r64", "precond_ellipsoids", "sphere163842_k64_q3_r16",
-                            "assemble_sphere10242"])
+                            "assemble_sphere10242", "field_sphere10242_k16"])
     p.add_argument("--precond-meshes", type=int, default=125, help="training meshes (16 solves each)")
     p.add_argument("--precond-steps", type=int, default=3000)
     p.add_argument("--precond-test", type=int, default=8)
@@ -521,6 +521,87 @@ def mie_density_sphere(k, d, pts):
     return lam
 
 
+def mie_scattered_sphere(k, d, pts):
+    """Field scattered by the sound-soft unit sphere for p_inc = exp(ik d.x), outside it:
+    -sum_n (2n+1) i^n j_n(k)/h_n(k) h_n(k r) P_n(d.x/r); measurement only."""
+    from scipy.special import eval_legendre, spherical_jn, spherical_yn
+    d = np.asarray(d, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    r = np.linalg.norm(pts, axis=1)
+    c = (pts / r[:, None]) @ d
+    s = np.zeros(pts.shape[0], dtype=np.complex128)
+    for n in range(int(np.ceil(k + 4.0 * k ** (1.0 / 3.0) + 12)) + 1):
+        hk = spherical_jn(n, k) + 1j * spherical_yn(n, k)
+        hr = spherical_jn(n, k * r) + 1j * spherical_yn(n, k * r)
+        s -= (2 * n + 1) * (1j ** n) * spherical_jn(n, k) / hk * hr * eval_legendre(n, c)
+    return s
+
+
+def run_field(args):
+    """Workload field_sphere10242_k16: the total field of the sound-soft sphere
+    (the listing of Sec. 6.4: Pdom = PW - Sdom lambda) on a 300 x 300 grid of the
+    plane y = 0, x, z in [-2.5, 2.5], from the GMRES density of
+    sphere10242_k16_q7 (icosphere 20480 triangles, q = 7, k = 16, d = (1, 0, 0)).
+    One step = one potential evaluation (FP32 far sum, FP64 [1/r]
+    regularisation) at the 90000 points; error against the Mie total field at
+    the points more than 0.1 from the surface."""
+    import torch
+
+    import paper_1804_00995_gb300 as g
+    from paper_1804_00995_gb300 import build as gb
+    gb.build()
+    cfg = synth.WORKLOADS[WORKLOAD]
+    v, t = synth.icosphere(cfg["level"])
+    mesh = g.Mesh(v, t, cfg["q"])
+    k, d = cfg["k"], np.asarray(cfg["dirs"][0], dtype=np.float64)
+    f = g.rhs_planewave(mesh, k, [d])
+    t0 = time.perf_counter()
+    lam, rep = g.gmres_solve(mesh, k, f, tol=cfg["tol"], restart=200, maxit=2000, prec="fp32", check_prec="df64")
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    n = 300
+    a = np.linspace(-2.5, 2.5, n)
+    X, Z = np.meshgrid(a, a, indexing="ij")
+    pts = np.stack([X.ravel(), np.zeros(n * n), Z.ravel()], axis=1)
+    pd = torch.as_tensor(pts).cuda()
+    for _ in range(args.warmup):
+        g.sl_potential(mesh, k, pd, lam, prec="fp32")
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(smi_id_of(torch.cuda.get_device_properties(0)))
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        p = g.sl_potential(mesh, k, pd, lam, prec="fp32")
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(x.elapsed_time(y) for x, y in ev) / args.steps
+    p = p.cpu().numpy()[:, 0]
+    total = np.exp(1j * k * pts @ d) - p
+    r = np.linalg.norm(pts, axis=1)
+    inside, outside = r < 0.9, r > 1.1
+    mie_total = np.exp(1j * k * pts[outside] @ d) + mie_scattered_sphere(k, d, pts[outside])
+    pairs = float(len(pts)) * mesh.nq
+    line = {
+        "metric": "GPairs/s single-layer potential at points (total field of the solved sphere)",
+        "value": pairs / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "field_sphere10242_k16", "points": len(pts), "grid": "300 x 300, y = 0, [-2.5, 2.5]^2",
+                   "nq": mesh.nq, "k": k, "near": "fp64 [1/r] regularisation"},
+        "solve": {"seconds": t_solve, "iterations": rep.iterations, "status": rep.status,
+                  "true_residual_df64": float(rep.true_residual[0])},
+        "field_error": {"inside_max_abs_total": float(np.abs(total[inside]).max()),
+                        "outside_max_abs": float(np.abs(total[outside] - mie_total).max()),
+                        "outside_median_abs": float(np.median(np.abs(total[outside] - mie_total))),
+                        "points_inside": int(inside.sum()), "points_outside": int(outside.sum())},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def solve_large(g, mesh, v, t, k, F, dirs, args):
     """Workload sphere163842_k64_q3_r16, --solve: (flexible) GMRES to 1e-6 on all
     16 plane waves, tensor-core working operator, double-float operator for the
@@ -668,6 +749,9 @@ def main():
     args = parse()
     if args.workload == "assemble_sphere10242":
         run_assemble(args)
+        return
+    if args.workload == "field_sphere10242_k16":
+        run_field(args)
         return
     if args.workload == "sphere163842_k64_q3_r16":
         run_large(args)

@@ -26,7 +26,7 @@ __global__ void point_prep_kernel(const double *p, int64_t n, float4 *p32, doubl
 }
 
 // Per triangle: centroid and the squared near radius (2 x largest centroid-vertex distance)^2.
-__global__ void tri_center_kernel(const double *vtx, const int32_t *tri, int64_t nt, double4_32a *cen)
+__global__ void tri_center_kernel(const double *vtx, const int32_t *tri, int64_t nt, double4_32a *cen, float4 *cen32)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
@@ -36,12 +36,15 @@ __global__ void tri_center_kernel(const double *vtx, const int32_t *tri, int64_t
 #pragma unroll
     for (int m = 0; m < 3; ++m) r2 = fmax(r2, dot(P[m] - c, P[m] - c));
     cen[t] = make_double4_32a(c.x, c.y, c.z, 4.0 * r2);
+    // FP32 candidate test: a widened radius keeps every triangle the FP64 test accepts
+    cen32[t] = make_float4((float)c.x, (float)c.y, (float)c.z, (float)(4.0 * r2 * 1.001));
 }
 
 // P[i, c0 + cc] = (1/4pi) (v[i, c0 + cc] + correction), CH columns per launch row.
 template <int CH>
 __global__ void point_finish_kernel(const double *vtx, const int32_t *tri, int64_t nt, const double4_32a *pts64,
-                                    const Rule rule, const double4_32a *cen, const double4_32a *tgt, int64_t npts,
+                                    const Rule rule, const double4_32a *cen, const float4 *cen32,
+                                    const double4_32a *tgt, int64_t npts,
                                     const double2 *v, int64_t ldv, const double2 *X, int64_t ldx, int nrhs,
                                     double2 *P, int64_t ldp)
 {
@@ -54,7 +57,13 @@ __global__ void point_finish_kernel(const double *vtx, const int32_t *tri, int64
     double2 acc[CH];
 #pragma unroll
     for (int cc = 0; cc < CH; ++cc) acc[cc] = make_double2(0.0, 0.0);
+    // FP32 scan with a margin above its rounding error (coordinates of size |x|), then the FP64 test
+    const float xf = (float)x.x, yf = (float)x.y, zf = (float)x.z;
+    const float margin = 1e-5f * (1.0f + xf * xf + yf * yf + zf * zf);
     for (int64_t b = 0; b < nt; ++b) {
+        const float4 cf = cen32[b];
+        const float ex = xf - cf.x, ey = yf - cf.y, ez = zf - cf.z;
+        if (ex * ex + ey * ey + ez * ez >= cf.w + margin) continue;
         const double4_32a c = cen[b];
         const double3 d = make_double3(x.x - c.x, x.y - c.y, x.z - c.z);
         if (dot(d, d) >= c.w) continue;
@@ -93,9 +102,11 @@ __global__ void point_finish_kernel(const double *vtx, const int32_t *tri, int64
 static gyps_status potential_device(Mesh *m, double k, int64_t npts, const double *pts_dev, int nrhs, const double2 *X,
                                     int64_t ldx, double2 *P, int64_t ldp, int prec, cudaStream_t s)
 {
-    if (!m->d_tri_cen) {
-        GYPS_CUDA(cudaMalloc((void **)&m->d_tri_cen, (size_t)m->nt * sizeof(double4_32a)));
-        tri_center_kernel<<<(unsigned)((m->nt + 255) / 256), 256, 0, s>>>(m->d_vtx, m->d_tri, m->nt, m->d_tri_cen);
+    if (!m->d_tri_cen32) {
+        if (!m->d_tri_cen) GYPS_CUDA(cudaMalloc((void **)&m->d_tri_cen, (size_t)m->nt * sizeof(double4_32a)));
+        GYPS_CUDA(cudaMalloc((void **)&m->d_tri_cen32, (size_t)m->nt * sizeof(float4)));
+        tri_center_kernel<<<(unsigned)((m->nt + 255) / 256), 256, 0, s>>>(m->d_vtx, m->d_tri, m->nt, m->d_tri_cen,
+                                                                         m->d_tri_cen32);
         GYPS_CUDA(cudaGetLastError());
     }
     // workspace: float4 points, double4 points, v (npts x nrhs)
@@ -112,8 +123,8 @@ static gyps_status potential_device(Mesh *m, double k, int64_t npts, const doubl
     GYPS_TRY(far_points(m, k, X, ldx, nrhs, p32, p64, npts, v, npts, prec, s));
     constexpr int CH = 4;
     dim3 g((unsigned)((npts + 127) / 128), (unsigned)((nrhs + CH - 1) / CH));
-    point_finish_kernel<CH><<<g, 128, 0, s>>>(m->d_vtx, m->d_tri, m->nt, m->d_pts64, m->rule, m->d_tri_cen, p64, npts,
-                                              v, npts, X, ldx, nrhs, P, ldp);
+    point_finish_kernel<CH><<<g, 128, 0, s>>>(m->d_vtx, m->d_tri, m->nt, m->d_pts64, m->rule, m->d_tri_cen,
+                                              m->d_tri_cen32, p64, npts, v, npts, X, ldx, nrhs, P, ldp);
     GYPS_CUDA(cudaGetLastError());
     return GYPS_OK;
 }

@@ -19,3 +19,13 @@ def test_bench_mie_series_matches_oracle():
 
 def test_far_profile_matches_source():
     assert bench.far_traffic_per_launch() is not None
+
+
+def test_bench_mie_scattered_field_cancels_the_incident_wave_on_the_sphere():
+    """Sound-soft boundary: p_inc + p_sca = 0 on the unit sphere."""
+    rng = np.random.default_rng(5)
+    pts = rng.normal(size=(40, 3))
+    pts /= np.linalg.norm(pts, axis=1, keepdims=True)
+    for k, d in ((5.0, np.array([0.0, 0.0, 1.0])), (16.0, np.array([1.0, 0.0, 0.0]))):
+        s = bench.mie_scattered_sphere(k, d, pts)
+        assert np.max(np.abs(s + np.exp(1j * k * pts @ d))) < 1e-9
