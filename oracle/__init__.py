@@ -71,6 +71,11 @@ def _load():
             lib.or_p1_inv_r.argtypes = [dp, dp, dp, dp, dp]
             lib.or_p1_inv_r.restype = None
             lib.or_near_blocks.argtypes = [dp, i32p, ctypes.c_int, ctypes.c_int64, i64p, i64p, dp]
+            lib.or_dl_kernel_matvec.argtypes = [ctypes.c_int64, dp, i64p, ctypes.c_int64, dp, dp,
+                                                ctypes.c_double, ctypes.c_int64, dp, dp]
+            lib.or_p1_dn_inv_r.argtypes = [dp, dp, dp, dp, dp]
+            lib.or_p1_dn_inv_r.restype = None
+            lib.or_dl_near_blocks.argtypes = [dp, i32p, ctypes.c_int, ctypes.c_int64, i64p, i64p, dp]
             lib.or_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -229,6 +234,60 @@ def near_matrix(vtx, tri, q):
 
 
 # --------------------------------------------------------------------------
+# Double layer: kernel n_y . grad_y exp(ikr)/r, correction 'grady[1/r]'
+# --------------------------------------------------------------------------
+
+def dl_kernel_matvec(xt, tid, ys, nrm, u, k):
+    """v = H u with H_tl = (1 - ikr) exp(ikr) n_l . (x_t - y_l) / r^3, H = 0 where tid[t] == l."""
+    lib = _load()
+    xt = np.ascontiguousarray(xt, dtype=np.float64)
+    ys = np.ascontiguousarray(ys, dtype=np.float64)
+    nrm = np.ascontiguousarray(nrm, dtype=np.float64)
+    u = np.asarray(u, dtype=np.complex128)
+    if u.ndim == 1:
+        u = u[:, None]
+    nt, ns, nrhs = xt.shape[0], ys.shape[0], u.shape[1]
+    uflat = np.ascontiguousarray(u.ravel(order="F"))
+    vflat = np.zeros(nt * nrhs, dtype=np.complex128)
+    tidp = None
+    if tid is not None:
+        tid = np.ascontiguousarray(tid, dtype=np.int64)
+        tidp = _i64p(tid)
+    lib.or_dl_kernel_matvec(nt, _dp(xt), tidp, ns, _dp(ys), _dp(nrm), float(k), nrhs,
+                            _dp(uflat.view(np.float64)), _dp(vflat.view(np.float64)))
+    return vflat.reshape((nt, nrhs), order="F")
+
+
+def p1_dn_inv_r(x, p0, p1, p2):
+    """int_T lambda_j(y) n . (x - y)/|x - y|^3 dy for j = 0, 1, 2 (closed form; 0 in the plane of T)."""
+    lib = _load()
+    out = np.zeros(3)
+    args = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, p0, p1, p2)]
+    lib.or_p1_dn_inv_r(*[_dp(a) for a in args], _dp(out))
+    return out
+
+
+def dl_near_matrix(vtx, tri, q):
+    """Sparse real double-layer correction (Nv, Nv) on the pairs sharing a vertex."""
+    lib = _load()
+    nv = vtx.shape[0]
+    vtx = np.ascontiguousarray(vtx, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    pa, pb = near_pairs(tri, nv)
+    pa = np.ascontiguousarray(pa, dtype=np.int64)
+    pb = np.ascontiguousarray(pb, dtype=np.int64)
+    blk = np.zeros((pa.shape[0], 3, 3))
+    if lib.or_dl_near_blocks(_dp(vtx), _i32p(tri), int(q), pa.shape[0], _i64p(pa), _i64p(pb), _dp(blk)) != 0:
+        raise ValueError("bad quadrature order")
+    ti, tj = tri[pa].astype(np.int64), tri[pb].astype(np.int64)
+    rows = np.repeat(ti, 3, axis=1).reshape(-1)
+    cols = np.tile(tj, (1, 3)).reshape(-1)
+    c = sp.coo_matrix((blk.reshape(-1), (rows, cols)), shape=(nv, nv)).tocsr()
+    c.sum_duplicates()
+    return c
+
+
+# --------------------------------------------------------------------------
 # The operator on a mesh
 # --------------------------------------------------------------------------
 
@@ -279,6 +338,32 @@ class Mesh:
             mask = np.zeros(self.nv, dtype=bool)
             mask[np.asarray(rows)] = True
             y[~mask] = 0.0
+        return y[:, 0] if one else y
+
+    def point_normals(self):
+        """Unit normal of the triangle of each quadrature point (Nq, 3)."""
+        P = self.vtx[self.tri]
+        n = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        return np.repeat(n, self.q, axis=0)
+
+    @property
+    def dl_near(self):
+        if getattr(self, "_cdl", None) is None:
+            self._cdl = dl_near_matrix(self.vtx, self.tri, self.q)
+        return self._cdl
+
+    def dl_apply(self, k, x):
+        """Galerkin double layer K x, K_ij = (1/4pi) int int phi_i(x) n_y . grad_y exp(ik|x-y|)/|x-y| phi_j(y):
+        the same factorisation as the single layer (Phi^T W H W Phi / 4pi) with the
+        kernel H and the 'grady[1/r]' correction on pairs sharing a vertex."""
+        x = np.asarray(x, dtype=np.complex128)
+        one = x.ndim == 1
+        if one:
+            x = x[:, None]
+        u = self.w[:, None] * (self.phi @ x)
+        v = dl_kernel_matvec(self.x, np.arange(self.nq), self.x, self.point_normals(), u, k)
+        y = (self.phi.T @ (self.w[:, None] * v)) / (4.0 * np.pi) + self.dl_near @ x
         return y[:, 0] if one else y
 
     def apply(self, k, x, rows=None):

@@ -292,6 +292,172 @@ int or_near_blocks(const double *vtx, const int32_t *tri, int q,
 }
 
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
+/* ------------------------------------------------------------------------ */
+/* Double layer (the next operator after the single layer; the paper's       */
+/* grady[exp(ikr)/r] kernels with the 'grady[1/r]' regularisation):          */
+/*   H(x, y) = n_y . grad_y exp(ik|x-y|)/|x-y|                                */
+/*           = (1 - i k r) exp(i k r) n_y . (x - y) / r^3,                   */
+/* n_y the unit normal of the source triangle.  Within one flat triangle     */
+/* n_y . (x - y) = 0, so the point paired with itself takes H := 0.          */
+/* ------------------------------------------------------------------------ */
+
+/* v[t, j] = sum_l H(x_t, y_l) u[l, j]; ns_nrm: ns x 3 unit normals at the sources. */
+int or_dl_kernel_matvec(int64_t nt, const double *xt, const int64_t *tid,
+                        int64_t ns, const double *ys, const double *ns_nrm, double k, int64_t nrhs,
+                        const double *u, double *v)
+{
+    #pragma omp parallel
+    {
+        double *acc = (double *)calloc((size_t)(2 * nrhs), sizeof(double));
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t t = 0; t < nt; ++t) {
+            for (int64_t j = 0; j < 2 * nrhs; ++j) acc[j] = 0.0;
+            for (int64_t l = 0; l < ns; ++l) {
+                if (tid != NULL && tid[t] == l) continue;
+                const double *x = xt + 3 * t, *y = ys + 3 * l, *n = ns_nrm + 3 * l;
+                double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+                double r = sqrt(dot3(d, d));
+                double f = dot3(n, d) / (r * r * r);
+                /* (1 - i k r)(cos kr + i sin kr) */
+                double c = cos(k * r), sn = sin(k * r);
+                double hr = (c + k * r * sn) * f, hi = (sn - k * r * c) * f;
+                for (int64_t j = 0; j < nrhs; ++j) {
+                    double ur = u[2 * (j * ns + l)], ui = u[2 * (j * ns + l) + 1];
+                    acc[2 * j] += hr * ur - hi * ui;
+                    acc[2 * j + 1] += hr * ui + hi * ur;
+                }
+            }
+            for (int64_t j = 0; j < nrhs; ++j) {
+                v[2 * (j * nt + t)] = acc[2 * j];
+                v[2 * (j * nt + t) + 1] = acc[2 * j + 1];
+            }
+        }
+        free(acc);
+    }
+    return 0;
+}
+
+/*
+ * int_T lambda_j(y) n . (x - y) / |x - y|^3 dy over the flat triangle T =
+ * (P0, P1, P2) with unit normal n = (P1 - P0) x (P2 - P0) / |.|, in closed
+ * form.  With h = n . (x - P0) (so n . (x - y) = h on T) and rho the
+ * projection of x onto the plane of T:
+ *   h int_T 1/R^3 = sign(h) Omega, Omega the solid angle of T seen from x,
+ *     Omega = sum_e [atan(p_e s+ / (q_e + |h| R+)) - atan(p_e s- / (q_e + |h| R-))]
+ *     (the edge sum that also gives the |h| term of int_T 1/R);
+ *   int_T (y - rho)/R^3 = - sum_e m_e ln((R+ + s+)/(R- + s-))
+ *     (in-plane divergence theorem applied to 1/R);
+ *   result_j = lambda_j(rho) sign(h) Omega + h grad lambda_j . int_T (y - rho)/R^3.
+ * For x in the plane of T the value is 0 (principal value).
+ */
+void or_p1_dn_inv_r(const double *x, const double *P0, const double *P1, const double *P2, double *out)
+{
+    const double *P[3] = {P0, P1, P2};
+    double e1[3], e2[3], nn[3];
+    for (int c = 0; c < 3; ++c) {
+        e1[c] = P1[c] - P0[c];
+        e2[c] = P2[c] - P0[c];
+    }
+    cross3(e1, e2, nn);
+    double twoA = sqrt(dot3(nn, nn));
+    double n[3] = {nn[0] / twoA, nn[1] / twoA, nn[2] / twoA};
+    double xp0[3] = {x[0] - P0[0], x[1] - P0[1], x[2] - P0[2]};
+    double h = dot3(xp0, n);
+    double ah = fabs(h);
+    if (ah == 0.0) {
+        out[0] = out[1] = out[2] = 0.0;
+        return;
+    }
+    double rho0[3] = {x[0] - h * n[0], x[1] - h * n[1], x[2] - h * n[2]};
+    double omega = 0.0, Wv[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < 3; ++i) {
+        const double *Pm = P[i], *Pp = P[(i + 1) % 3];
+        double t[3] = {Pp[0] - Pm[0], Pp[1] - Pm[1], Pp[2] - Pm[2]};
+        double len = sqrt(dot3(t, t));
+        t[0] /= len; t[1] /= len; t[2] /= len;
+        double m[3];
+        cross3(t, n, m);
+        double am[3] = {Pm[0] - rho0[0], Pm[1] - rho0[1], Pm[2] - rho0[2]};
+        double ap[3] = {Pp[0] - rho0[0], Pp[1] - rho0[1], Pp[2] - rho0[2]};
+        double lm = dot3(am, t), lp = dot3(ap, t);
+        double p = dot3(am, m);
+        double R02 = p * p + h * h;
+        double xm[3] = {x[0] - Pm[0], x[1] - Pm[1], x[2] - Pm[2]};
+        double xpp[3] = {x[0] - Pp[0], x[1] - Pp[1], x[2] - Pp[2]};
+        double Rm = sqrt(dot3(xm, xm)), Rp = sqrt(dot3(xpp, xpp));
+        double L = log(r_plus_l(Rp, lp, R02) / r_plus_l(Rm, lm, R02));
+        omega += atan(p * lp / (R02 + ah * Rp)) - atan(p * lm / (R02 + ah * Rm));
+        Wv[0] -= m[0] * L;
+        Wv[1] -= m[1] * L;
+        Wv[2] -= m[2] * L;
+    }
+    double sg = h > 0.0 ? 1.0 : -1.0;
+    for (int j = 0; j < 3; ++j) {
+        const double *A = P[(j + 1) % 3], *B = P[(j + 2) % 3];
+        double ab[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+        double g[3];
+        cross3(n, ab, g);
+        g[0] /= twoA; g[1] /= twoA; g[2] /= twoA;
+        double rj[3] = {rho0[0] - P[j][0], rho0[1] - P[j][1], rho0[2] - P[j][2]};
+        double lam0 = 1.0 + dot3(g, rj);
+        out[j] = lam0 * sg * omega + h * dot3(g, Wv);
+    }
+}
+
+/* Correction blocks of the double layer on near pairs (a, b), as or_near_blocks
+   with the 'grady[1/r]' part: (1/4pi) sum_k w_k lambda_i(x_k) (I_j(x_k, b) -
+   sum_l eta_l lambda_j(y_l) n_b . (x_k - y_l)/r^3).  a == b gives 0 (coplanar). */
+int or_dl_near_blocks(const double *vtx, const int32_t *tri, int q,
+                      int64_t npairs, const int64_t *pa, const int64_t *pb, double *blocks)
+{
+    double bary[21], wr[7];
+    if (or_quad_rule(q, bary, wr) != 0) return -1;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < npairs; ++p) {
+        int64_t a = pa[p], b = pb[p];
+        double blk[9] = {0};
+        if (a != b) {
+            const double *A[3], *B[3];
+            for (int m = 0; m < 3; ++m) {
+                A[m] = vtx + 3 * (int64_t)tri[3 * a + m];
+                B[m] = vtx + 3 * (int64_t)tri[3 * b + m];
+            }
+            double ea[3], fa[3], na[3], eb[3], fb[3], nb[3];
+            for (int c = 0; c < 3; ++c) {
+                ea[c] = A[1][c] - A[0][c]; fa[c] = A[2][c] - A[0][c];
+                eb[c] = B[1][c] - B[0][c]; fb[c] = B[2][c] - B[0][c];
+            }
+            cross3(ea, fa, na);
+            cross3(eb, fb, nb);
+            double area_a = 0.5 * sqrt(dot3(na, na)), area_b = 0.5 * sqrt(dot3(nb, nb));
+            double un[3] = {nb[0] / (2 * area_b), nb[1] / (2 * area_b), nb[2] / (2 * area_b)};
+            for (int kq = 0; kq < q; ++kq) {
+                double xk[3];
+                for (int c = 0; c < 3; ++c)
+                    xk[c] = bary[3 * kq] * A[0][c] + bary[3 * kq + 1] * A[1][c] + bary[3 * kq + 2] * A[2][c];
+                double wk = wr[kq] * area_a;
+                double ex[3];
+                or_p1_dn_inv_r(xk, B[0], B[1], B[2], ex);
+                double gs[3] = {0.0, 0.0, 0.0};
+                for (int lq = 0; lq < q; ++lq) {
+                    double yl[3];
+                    for (int c = 0; c < 3; ++c)
+                        yl[c] = bary[3 * lq] * B[0][c] + bary[3 * lq + 1] * B[1][c] + bary[3 * lq + 2] * B[2][c];
+                    double dd[3] = {xk[0] - yl[0], xk[1] - yl[1], xk[2] - yl[2]};
+                    double r = sqrt(dot3(dd, dd));
+                    double f = wr[lq] * area_b * dot3(un, dd) / (r * r * r);
+                    for (int j = 0; j < 3; ++j) gs[j] += f * bary[3 * lq + j];
+                }
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        blk[3 * i + j] += wk * bary[3 * kq + i] * (ex[j] - gs[j]) / (4.0 * M_PI);
+            }
+        }
+        for (int e = 0; e < 9; ++e) blocks[9 * p + e] = blk[e];
+    }
+    return 0;
+}
+
 int or_num_threads(void)
 {
 #ifdef _OPENMP
