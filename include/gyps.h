@@ -164,6 +164,25 @@ gyps_status gyps_near_correct(gyps_mesh_t mesh, int nrhs, const void *X, int64_t
 gyps_status gyps_sl_assemble(gyps_mesh_t mesh, double k, int prec, void *V, int64_t ldv, void *stream);
 
 /*
+ * Galerkin double layer (the paper's grady[exp(ikr)/r] kernel with the
+ * 'grady[1/r]' regularisation, Sec. 5.2, in the factorisation of Eq. (BEM)):
+ *     Y = K X,  K_ij = (1/4pi) int int phi_i(x) n_y . grad_y exp(ik|x-y|)/|x-y| phi_j(y),
+ *     K = (1/4pi) Phi^T W H W Phi + C_dl,  H = (1 - ikr) exp(ikr) n_y . (x - y) / r^3,
+ * n_y the outward unit normal of the source triangle ((P1 - P0) x (P2 - P0)
+ * for the mesh's orientation); pairs inside one flat triangle give 0 (the
+ * principal value); C_dl on triangles sharing a vertex: closed-form integral
+ * of lambda_j n . (x - y)/|x - y|^3 minus its Gauss sum.  On the unit sphere
+ * K Y_n = (1/2 + i k^2 j_n(k) h_n'(k)) Y_n (-1/(2(2n+1)) at k = 0).
+ *   X, Y  nv x nrhs complex double2 (host or device), leading dims >= nv.
+ *   prec  GYPS_PREC_FP64 or GYPS_PREC_FP32 (AUTO); the correction is FP64.
+ * Built with its correction on the first call (then cached in the mesh).
+ * Synchronous. Errors: INVALID, UNSUPPORTED (tensor-core or double-float
+ * precision), CUDA, OOM.
+ */
+gyps_status gyps_dl_apply(gyps_mesh_t mesh, double k, int nrhs, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                          int prec, void *stream);
+
+/*
  * Single-layer potential at points (the radiation operator of the listing in
  * Sec. 6.4: Sdom = integral(points, S2, Gxy, Vh)/(4 pi)
  * + regularize(points, S2, '[1/r]', Vh)/(4 pi)):

@@ -96,6 +96,8 @@ _SIGS = {
                            ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "gyps_sl_assemble": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                           ctypes.c_void_p], ctypes.c_int),
+    "gyps_dl_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "gyps_sl_potential": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p],
                           ctypes.c_int),
@@ -305,6 +307,16 @@ def sl_assemble(mesh: Mesh, k: float, prec: str = "fp64", device=None, stream=No
     v = _empty_colmajor(mesh.nv, mesh.nv, dev)
     _check(load().gyps_sl_assemble(mesh.handle, float(k), PREC[prec], v.data_ptr(), mesh.nv, _stream(stream)))
     return v
+
+
+def dl_apply(mesh: Mesh, k: float, X, prec: str = "fp32", stream=None):
+    """Y = K X, the Galerkin double layer with its 'grady[1/r]' correction (gyps_dl_apply)."""
+    one = (hasattr(X, "dim") and X.dim() == 1) or (not hasattr(X, "dim") and np.asarray(X).ndim == 1)
+    x, nrhs, ldx = _colmajor(X, mesh.nv, "X")
+    y = _empty_colmajor(mesh.nv, nrhs, x.device)
+    _check(load().gyps_dl_apply(mesh.handle, float(k), nrhs, x.data_ptr(), ldx, y.data_ptr(),
+                                max(y.stride(1), mesh.nv) if nrhs > 1 else mesh.nv, PREC[prec], _stream(stream)))
+    return y[:, 0] if one else y
 
 
 def sl_potential(mesh: Mesh, k: float, pts, X, prec: str = "fp32", stream=None):

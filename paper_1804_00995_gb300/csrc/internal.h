@@ -93,6 +93,8 @@ struct Mesh {
     void *ws_pts = nullptr; size_t ws_pts_bytes = 0;      // potential at points: point copies, far sums, staging
     double4_32a *d_tri_cen = nullptr;                     // per triangle: centroid, (2 x largest centroid-vertex distance)^2
     float4 *d_tri_cen32 = nullptr;                        // the same in FP32, radius widened (candidate test)
+    double4_32a *d_tri_nrm = nullptr;                     // double layer: unit normal per triangle
+    double *d_cdl_val = nullptr;                          // double layer: correction values on C's pattern
     float pad = 0.0f;                                     // distance of padding points
     // mesh graph for the learned preconditioner (built on first use)
     int32_t *d_adj_ptr = nullptr, *d_adj = nullptr;       // vertex neighbours over mesh edges

@@ -67,4 +67,49 @@ static __device__ void p1_over_r(double3 x, const double3 P[3], double out[3])
     }
 }
 
+// Closed-form y-integral over the flat triangle P of lambda_j(y) n . (x - y)/|x - y|^3
+// (the double layer's 'grady[1/r]' part), n = (P1 - P0) x (P2 - P0) / |.|.  With
+// h = n . (x - P0), n . (x - y) = h on P, and
+//   h int 1/R^3 = sign(h) Omega,  Omega = sum_e [atan(p_e s+ / (q_e + |h| R+)) - atan(p_e s- / (q_e + |h| R-))]
+//   (the solid angle of P seen from x, the edge sum of the single layer's |h| term),
+//   int (y - rho)/R^3 = - sum_e m_e ln((R+ + s+)/(R- + s-))  (in-plane divergence theorem on 1/R):
+//   out_j = lambda_j(rho) sign(h) Omega + h grad lambda_j . int (y - rho)/R^3;  0 for x in the plane.
+static __device__ void p1_dn_over_r(double3 x, const double3 P[3], double out[3])
+{
+    double3 nn = cross(P[1] - P[0], P[2] - P[0]);
+    double two_area = sqrt(dot(nn, nn));
+    double3 n = (1.0 / two_area) * nn;
+    double h = dot(x - P[0], n);
+    double ah = fabs(h);
+    if (ah == 0.0) {
+        out[0] = out[1] = out[2] = 0.0;
+        return;
+    }
+    double3 rho = x - h * n;
+    double omega = 0.0;
+    double3 Wv = make_double3(0.0, 0.0, 0.0);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        double3 a = P[e], b = P[(e + 1) % 3];
+        double3 tv = b - a;
+        double3 t = (1.0 / sqrt(dot(tv, tv))) * tv;
+        double3 me = cross(t, n);
+        double sm = dot(a - rho, t), sp = dot(b - rho, t);
+        double pe = dot(a - rho, me);
+        double qe = pe * pe + h * h;
+        double3 xa = x - a, xb = x - b;
+        double Rm = sqrt(dot(xa, xa)), Rp = sqrt(dot(xb, xb));
+        double L = log(log_arg(Rp, sp, qe) / log_arg(Rm, sm, qe));
+        omega += atan(pe * sp / (qe + ah * Rp)) - atan(pe * sm / (qe + ah * Rm));
+        Wv = Wv + (-L) * me;
+    }
+    const double sg = h > 0.0 ? 1.0 : -1.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        double3 g = (1.0 / two_area) * cross(n, P[(j + 2) % 3] - P[(j + 1) % 3]);  // grad lambda_j
+        double lam_rho = 1.0 + dot(g, rho - P[j]);
+        out[j] = lam_rho * sg * omega + h * dot(g, Wv);
+    }
+}
+
 }  // namespace gyps
