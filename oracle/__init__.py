@@ -15,6 +15,12 @@ It follows the paper's formulation step by step:
   sharing a vertex, analytic integral in y minus the Gauss sum, outer Gauss in x.
 * Sec. 6.4, Eqs. (Singlelayer), (Singlelayerwf): right-hand side
   ``F_i = int phi_i exp(ik d.x)`` and the solve ``V lambda = F``.
+* Sec. 6.4 (radiation operator): the single-layer potential at points, with the
+  same '[1/r]' regularisation for triangles near a point.
+* Sec. 5.2 with the grady[exp(ikr)/r] kernel: the double layer ``K``, its
+  'grady[1/r]' correction in closed form (solid angle and edge logarithms).
+* The Brakhage-Werner combined operator ``1/2 M + K - i eta V`` (Brakhage and
+  Werner 1965), assembled from the operators above, and its sphere closed form.
 
 Readings where the paper is silent (all listed with the design notes): the
 3-point rule is the interior (2/3, 1/6, 1/6) rule; "close enough" means sharing
@@ -366,6 +372,13 @@ class Mesh:
         y = (self.phi.T @ (self.w[:, None] * v)) / (4.0 * np.pi) + self.dl_near @ x
         return y[:, 0] if one else y
 
+    def bw_apply(self, k, eta, x):
+        """Brakhage-Werner combined operator (1/2 M + K - i eta V) x: the Galerkin
+        exterior trace of u = (D - i eta S) phi (jump relation of the double-layer
+        potential; Brakhage and Werner 1965), M = Phi^T W Phi (Eq. A=BWB)."""
+        x = np.asarray(x, dtype=np.complex128)
+        return 0.5 * (self.mass() @ x) + self.dl_apply(k, x) - 1j * eta * self.apply(k, x)
+
     def apply(self, k, x, rows=None):
         """V x = far part + C x (Sec. 5.2, listing of Sec. 6.4: LHS = integral + regularize)."""
         y = self.far_apply(k, x, rows)
@@ -525,3 +538,30 @@ def mie_density(k: float, d, pts):
         h = spherical_jn(n, k) + 1j * spherical_yn(n, k)
         lam += (2 * n + 1) * (1j ** n) * eval_legendre(n, c) / (1j * k * h)
     return lam
+
+
+def dl_sphere_eigenvalue(n: int, k: float) -> complex:
+    """Double-layer eigenvalue on the unit sphere for degree-n harmonics (outward
+    normal): -1/(2(2n+1)) at k = 0, else 1/2 + i k^2 j_n(k) h_n^(1)'(k)."""
+    from scipy.special import spherical_jn, spherical_yn
+    if k == 0.0:
+        return -1.0 / (2 * (2 * n + 1))
+    hp = spherical_jn(n, k, derivative=True) + 1j * spherical_yn(n, k, derivative=True)
+    return 0.5 + 1j * k * k * spherical_jn(n, k) * hp
+
+
+def bw_density(k: float, eta: float, d, pts):
+    """Density phi of (1/2 + K - i eta V) phi = -p_inc on the unit sphere for
+    p_inc = exp(ik d.x) = sum_n (2n+1) i^n j_n(k) P_n(d.x):
+    phi(x) = -sum_n (2n+1) i^n j_n(k) P_n(d.x) / (1/2 + mu_n(K) - i eta mu_n(V))."""
+    from scipy.special import eval_legendre, spherical_jn
+    d = np.asarray(d, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    pts = np.asarray(pts, dtype=np.float64)
+    c = (pts / np.linalg.norm(pts, axis=1, keepdims=True)) @ d
+    nmax = int(np.ceil(k + 4.0 * k ** (1.0 / 3.0) + 10))
+    phi = np.zeros(pts.shape[0], dtype=np.complex128)
+    for n in range(nmax + 1):
+        lam = 0.5 + dl_sphere_eigenvalue(n, k) - 1j * eta * sphere_eigenvalue(n, k)
+        phi -= (2 * n + 1) * (1j ** n) * spherical_jn(n, k) * eval_legendre(n, c) / lam
+    return phi
