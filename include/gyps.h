@@ -60,6 +60,14 @@ typedef enum {
     GYPS_PREC_AUTO = 4          /* FP32 below 16 right-hand sides, tensor cores above */
 } gyps_prec;
 
+/* Boundary integral equation that gyps_gmres_solve solves for sound-soft scattering. */
+typedef enum {
+    GYPS_FORM_SINGLE_LAYER = 0,   /* V X = F (first kind, Sec. 6.4); resonant where k^2 is an
+                                     interior Dirichlet eigenvalue */
+    GYPS_FORM_BRAKHAGE_WERNER = 1 /* (1/2 M + K - i eta V) X = F: the density of u = (D - i eta S) phi,
+                                     uniquely solvable for every k when eta > 0 */
+} gyps_formulation;
+
 /* gyps_sl_apply flags */
 #define GYPS_APPLY_NO_NEAR 0x1u /* far part (1/4pi) Phi^T W G W Phi only, no correction C */
 
@@ -183,6 +191,26 @@ gyps_status gyps_dl_apply(gyps_mesh_t mesh, double k, int nrhs, const void *X, i
                           int prec, void *stream);
 
 /*
+ * Combined-field operator of the indirect Brakhage-Werner formulation: the
+ * scattered field is sought as u = (D - i eta S) phi, with D the double-layer
+ * and S the single-layer potential (1/4pi normalisation); its exterior trace
+ * (jump relation of D) gives, in Galerkin form,
+ *     Y = (1/2 M + K - i eta V) X,   M = Phi^T W Phi (Eq. A=BWB),
+ * V the single layer of gyps_sl_apply and K the double layer of gyps_dl_apply.
+ * Sound-soft scattering of u_inc solves (1/2 M + K - i eta V) phi = -F with F
+ * from gyps_rhs_planewave; for eta > 0 the operator is invertible at every
+ * k > 0 (no interior resonances).  On the unit sphere its eigenvalue for
+ * degree-n harmonics is 1/2 + mu_n(K) - i eta mu_n(V).
+ *   X, Y  nv x nrhs complex double2 (host or device), leading dims >= nv, not overlapping.
+ *   prec  precision of V (as gyps_sl_apply); K is FP64 for GYPS_PREC_FP64 and
+ *         GYPS_PREC_DF64, FP32 otherwise; M is FP64.
+ * Synchronous. Errors: INVALID, UNSUPPORTED (tensor cores with k = 0 or fewer
+ * than 16 columns), CUDA, OOM, TIMEOUT.
+ */
+gyps_status gyps_bw_apply(gyps_mesh_t mesh, double k, double eta, int nrhs, const void *X, int64_t ldx,
+                          void *Y, int64_t ldy, int prec, void *stream);
+
+/*
  * Single-layer potential at points (the radiation operator of the listing in
  * Sec. 6.4: Sdom = integral(points, S2, Gxy, Vh)/(4 pi)
  * + regularize(points, S2, '[1/r]', Vh)/(4 pi)):
@@ -217,7 +245,7 @@ gyps_status gyps_rhs_planewave(gyps_mesh_t mesh, double k, int nrhs, const doubl
 
 /* GMRES options (gyps_gmres_solve). */
 typedef struct {
-    double tol;          /* relative residual ||F - V X|| / ||F|| per column (e.g. 1e-6) */
+    double tol;          /* relative residual ||F - A X|| / ||F|| per column (e.g. 1e-6) */
     int32_t restart;     /* Krylov dimension m before a restart (>= 1) */
     int32_t maxit;       /* total inner iterations per call (>= 1) */
     int32_t prec;        /* gyps_prec of the operator inside the Krylov loop */
@@ -225,6 +253,8 @@ typedef struct {
     int32_t use_x0;      /* 1: X holds the initial guess on entry; 0: start from zero */
     int32_t max_refine;  /* refinement sweeps when the check exceeds tol (0 = none) */
     gyps_precond_t precond; /* NULL, or a learned preconditioner: flexible GMRES with z = M(q) */
+    int32_t formulation; /* gyps_formulation (0: single layer) */
+    double eta;          /* coupling of the Brakhage-Werner operator (e.g. k); unused otherwise */
 } gyps_gmres_opts;
 
 /* GMRES report, HOST.  Arrays are caller-owned, length nrhs, may be NULL. */
@@ -241,10 +271,13 @@ typedef struct {
 } gyps_gmres_report;
 
 /*
- * Solves V X = F (Sec. 6.4, Eq. Singlelayerwf) for nrhs columns by restarted
- * GMRES: Arnoldi with classical Gram-Schmidt applied twice, in FP64 on the
- * device, Givens rotations on the host, one Krylov space per column, the
- * operator applied to all columns at once with `opts->prec`.  After the
+ * Solves A X = F for nrhs columns by restarted
+ * GMRES, A = V (Sec. 6.4, Eq. Singlelayerwf) or, with opts->formulation =
+ * GYPS_FORM_BRAKHAGE_WERNER, A = 1/2 M + K - i opts->eta V (gyps_bw_apply;
+ * pass -F for the sound-soft problem).  Arnoldi with classical Gram-Schmidt
+ * applied twice, in FP64 on the device, Givens rotations on the host, one
+ * Krylov space per column, the operator applied to all columns at once with
+ * `opts->prec`.  After the
  * Krylov loop the residual is recomputed with `opts->check_prec`; while it is
  * above tol and refinements remain, GMRES is run on the residual equation
  * and the correction added (mixed-precision iterative refinement).
@@ -255,6 +288,8 @@ typedef struct {
  * cycle that does not halve the residual of any column, drops the
  * preconditioner for the rest of the solve (unpreconditioned GMRES from the
  * current iterate) and the report says so.  The check-precision residual judges the result either way.
+ * The learned preconditioner models V: with the Brakhage-Werner operator it is
+ * UNSUPPORTED.
  * Returns NOT_CONVERGED (X = last iterate) when a column misses tol, NAN
  * when a non-finite value appears.
  */

@@ -67,7 +67,8 @@ class _BatchInfo(ctypes.Structure):
 class _GmresOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("check_prec", ctypes.c_int32), ("use_x0", ctypes.c_int32),
-                ("max_refine", ctypes.c_int32), ("precond", ctypes.c_void_p)]
+                ("max_refine", ctypes.c_int32), ("precond", ctypes.c_void_p), ("formulation", ctypes.c_int32),
+                ("eta", ctypes.c_double)]
 
 
 class _GmresReport(ctypes.Structure):
@@ -98,6 +99,8 @@ _SIGS = {
                           ctypes.c_void_p], ctypes.c_int),
     "gyps_dl_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "gyps_bw_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                       ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "gyps_sl_potential": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p],
                           ctypes.c_int),
@@ -319,6 +322,16 @@ def dl_apply(mesh: Mesh, k: float, X, prec: str = "fp32", stream=None):
     return y[:, 0] if one else y
 
 
+def bw_apply(mesh: Mesh, k: float, eta: float, X, prec: str = "fp32", stream=None):
+    """Y = (1/2 M + K - i eta V) X, the Brakhage-Werner combined operator (gyps_bw_apply)."""
+    one = (hasattr(X, "dim") and X.dim() == 1) or (not hasattr(X, "dim") and np.asarray(X).ndim == 1)
+    x, nrhs, ldx = _colmajor(X, mesh.nv, "X")
+    y = _empty_colmajor(mesh.nv, nrhs, x.device)
+    _check(load().gyps_bw_apply(mesh.handle, float(k), float(eta), nrhs, x.data_ptr(), ldx, y.data_ptr(),
+                                max(y.stride(1), mesh.nv) if nrhs > 1 else mesh.nv, PREC[prec], _stream(stream)))
+    return y[:, 0] if one else y
+
+
 def sl_potential(mesh: Mesh, k: float, pts, X, prec: str = "fp32", stream=None):
     """P (npts, nrhs): the single-layer potential of the density X at the points
     pts (npts, 3), with the [1/r] regularisation near the surface (gyps_sl_potential).
@@ -477,10 +490,16 @@ class GmresReport:
     status: str
 
 
+FORMULATION = {"sl": 0, "bw": 1}
+
+
 def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, maxit: int = 1000,
                 prec: str = "fp32", check_prec: str = "fp64", x0=None, max_refine: int = 3, raise_on_fail=False,
-                precond: "Precond" = None, stream=None):
-    """Solves V X = F (gyps_gmres_solve).  Returns (X, GmresReport)."""
+                precond: "Precond" = None, stream=None, formulation: str = "sl", eta: float = None):
+    """Solves A X = F (gyps_gmres_solve), A = V ("sl") or 1/2 M + K - i eta V
+    ("bw", eta defaults to k, or 1 at k = 0).  Returns (X, GmresReport)."""
+    if eta is None:
+        eta = float(k) if k > 0 else 1.0
     f, nrhs, ldf = _colmajor(F, mesh.nv, "F")
     if x0 is not None:
         x, _, _ = _colmajor(x0.clone() if hasattr(x0, "clone") else x0, mesh.nv, "x0")
@@ -490,7 +509,8 @@ def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, 
     else:
         x = _empty_colmajor(mesh.nv, nrhs, f.device)
     opts = _GmresOpts(float(tol), int(restart), int(maxit), PREC[prec], PREC[check_prec], 1 if x0 is not None else 0,
-                      int(max_refine), precond.handle.value if precond is not None else None)
+                      int(max_refine), precond.handle.value if precond is not None else None,
+                      FORMULATION[formulation], float(eta))
     est = np.zeros(nrhs)
     tru = np.zeros(nrhs)
     conv = np.zeros(nrhs, dtype=np.int32)

@@ -248,7 +248,7 @@ static gyps_status dl_prepare(Mesh *m, cudaStream_t s)
     return GYPS_OK;
 }
 
-static gyps_status dl_apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
+gyps_status dl_apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
                                    int prec, cudaStream_t s)
 {
     GYPS_TRY(dl_prepare(m, s));
@@ -280,6 +280,55 @@ static gyps_status dl_apply_device(Mesh *m, double k, int nrhs, const double2 *X
     dim3 gp((unsigned)((m->nv + 127) / 128), (unsigned)nrhs);
     project_kernel<<<gp, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_pts64, m->rule, m->nv, v, ld, m->d_c_rowptr,
                                       m->d_c_col, m->d_cdl_val, X, ldx, Y, ldy, 1);
+    GYPS_CUDA(cudaGetLastError());
+    return GYPS_OK;
+}
+
+// Combined operator of the indirect Brakhage-Werner formulation: u = (D - i eta S) phi
+// outside the surface; the exterior trace (1/2 + K - i eta V) phi = -u_inc holds on it
+// (jump of the double-layer potential), in Galerkin form with the mass matrix
+// M = Phi^T W Phi of Eq. (A=BWB).  Y holds V X on entry and T holds K X:
+//   Y = 1/2 Phi^T W Phi X + T - i eta Y.
+__global__ void bw_combine_kernel(const int32_t *v2t_ptr, const int32_t *v2t, const int32_t *tri,
+                                  const double4_32a *pts64, const Rule rule, int64_t nv, const double2 *X,
+                                  int64_t ldx, const double2 *T, int64_t ldt, double eta, double2 *Y, int64_t ldy)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t c = blockIdx.y;
+    if (i >= nv) return;
+    const double2 *xc = X + c * ldx;
+    const int q = rule.q;
+    double mr = 0.0, mi = 0.0;
+    for (int32_t e = v2t_ptr[i]; e < v2t_ptr[i + 1]; ++e) {
+        const int32_t te = v2t[e];
+        const int64_t t = te / 3;
+        const int corner = te - 3 * (int)t;
+        const double2 x0 = xc[tri[3 * t]], x1 = xc[tri[3 * t + 1]], x2 = xc[tri[3 * t + 2]];
+        for (int l = 0; l < q; ++l) {
+            const double *b = rule.bary + 3 * l;
+            const double wb = pts64[t * q + l].w * b[corner];
+            mr += wb * (b[0] * x0.x + b[1] * x1.x + b[2] * x2.x);
+            mi += wb * (b[0] * x0.y + b[1] * x1.y + b[2] * x2.y);
+        }
+    }
+    const double2 kx = T[i + c * ldt];
+    const double2 vx = Y[i + c * ldy];
+    Y[i + c * ldy] = make_double2(0.5 * mr + kx.x + eta * vx.y, 0.5 * mi + kx.y - eta * vx.x);
+}
+
+// Y = (1/2 M + K - i eta V) X.  V in prec; K in FP64 for the FP64 and
+// double-float precisions, in FP32 otherwise.
+gyps_status bw_apply_device(Mesh *m, double k, double eta, int nrhs, const double2 *X, int64_t ldx, double2 *Y,
+                            int64_t ldy, int prec, cudaStream_t s)
+{
+    GYPS_TRY(grow(m, &m->ws_bw, &m->ws_bw_bytes, (size_t)m->nv * nrhs * sizeof(double2)));
+    double2 *T = reinterpret_cast<double2 *>(m->ws_bw);
+    const int kprec = (prec == GYPS_PREC_FP64 || prec == GYPS_PREC_DF64) ? GYPS_PREC_FP64 : GYPS_PREC_FP32;
+    GYPS_TRY(dl_apply_device(m, k, nrhs, X, ldx, T, m->nv, kprec, s));
+    GYPS_TRY(apply_device(m, k, nrhs, X, ldx, Y, ldy, prec, 0, 0, m->nt, s));
+    dim3 g((unsigned)((m->nv + 127) / 128), (unsigned)nrhs);
+    bw_combine_kernel<<<g, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_tri, m->d_pts64, m->rule, m->nv, X, ldx, T, m->nv,
+                                        eta, Y, ldy);
     GYPS_CUDA(cudaGetLastError());
     return GYPS_OK;
 }
@@ -326,4 +375,49 @@ extern "C" gyps_status gyps_dl_apply(gyps_mesh_t h, double k, int nrhs, const vo
                                     cudaMemcpyDeviceToHost, s));
     GYPS_CUDA(cudaStreamSynchronize(s));
     return GYPS_OK;
+}
+
+extern "C" gyps_status gyps_bw_apply(gyps_mesh_t h, double k, double eta, int nrhs, const void *X, int64_t ldx,
+                                     void *Y, int64_t ldy, int prec, void *stream)
+{
+    Mesh *m;
+    GYPS_TRY(check_mesh(h, &m));
+    if (nrhs < 1 || nrhs > 4096) return set_error(GYPS_ERR_INVALID, "nrhs must be in 1..4096");
+    if (!X || !Y) return set_error(GYPS_ERR_INVALID, "NULL argument");
+    if (ldx < m->nv || ldy < m->nv) return set_error(GYPS_ERR_INVALID, "leading dimension < nv");
+    if (!std::isfinite(k) || k < 0.0) return set_error(GYPS_ERR_INVALID, "k must be finite and >= 0");
+    if (!std::isfinite(eta)) return set_error(GYPS_ERR_INVALID, "eta must be finite");
+    if (prec == GYPS_PREC_AUTO) prec = GYPS_PREC_FP32;
+    if (prec != GYPS_PREC_FP64 && prec != GYPS_PREC_FP32 && prec != GYPS_PREC_TC_BF16X3 && prec != GYPS_PREC_DF64)
+        return set_error(GYPS_ERR_INVALID, "unknown precision");
+    if (prec == GYPS_PREC_TC_BF16X3 && nrhs < 16)
+        return set_error(GYPS_ERR_UNSUPPORTED, "tensor-core precision needs 16 or more right-hand sides");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dx = is_device_pointer(X), dy = is_device_pointer(Y);
+    if (dx && dy && (const char *)X < (const char *)Y + ldy * nrhs * 16 &&
+        (const char *)Y < (const char *)X + ldx * nrhs * 16)
+        return set_error(GYPS_ERR_INVALID, "X and Y overlap");
+    const size_t blk = (size_t)m->nv * nrhs * sizeof(double2);
+    double2 *xs = nullptr, *ys = nullptr;
+    if (!dx || !dy) {
+        GYPS_TRY(grow(m, &m->ws_stage, &m->ws_stage_bytes, 2 * blk));
+        xs = reinterpret_cast<double2 *>(m->ws_stage);
+        ys = xs + (size_t)m->nv * nrhs;
+    }
+    const double2 *xin = (const double2 *)X;
+    int64_t lxin = ldx;
+    if (!dx) {
+        GYPS_CUDA(cudaMemcpy2DAsync(xs, m->nv * sizeof(double2), X, ldx * sizeof(double2), m->nv * sizeof(double2), nrhs,
+                                    cudaMemcpyHostToDevice, s));
+        xin = xs;
+        lxin = m->nv;
+    }
+    double2 *yout = dy ? (double2 *)Y : ys;
+    const int64_t lyout = dy ? ldy : m->nv;
+    GYPS_TRY(bw_apply_device(m, k, eta, nrhs, xin, lxin, yout, lyout, prec, s));
+    if (!dy)
+        GYPS_CUDA(cudaMemcpy2DAsync(Y, ldy * sizeof(double2), ys, m->nv * sizeof(double2), m->nv * sizeof(double2), nrhs,
+                                    cudaMemcpyDeviceToHost, s));
+    GYPS_CUDA(cudaStreamSynchronize(s));
+    return check_err_word(m, s);
 }

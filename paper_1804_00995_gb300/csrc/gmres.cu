@@ -182,6 +182,16 @@ struct Solver {
     gyps_precond_t P = nullptr;  // learned preconditioner (flexible GMRES) while pre_on
     bool pre_on = false;
     int fallback = 0;
+    int form = GYPS_FORM_SINGLE_LAYER;
+    double eta = 0.0;
+
+    // Y = A X for the system's operator A: V (first kind), or 1/2 M + K - i eta V
+    // (Brakhage-Werner); X and Y are nv x nrhs.
+    gyps_status op(const double2 *X, int64_t ldx, double2 *Y, int prec)
+    {
+        if (form == GYPS_FORM_BRAKHAGE_WERNER) return bw_apply_device(m, k, eta, nrhs, X, ldx, Y, nv, prec, s);
+        return apply_device(m, k, nrhs, X, ldx, Y, nv, prec, 0, 0, m->nt, s);
+    }
 
     // Column norms without the non-finite check (the preconditioned cycle
     // handles a non-finite value by dropping the preconditioner).
@@ -230,7 +240,7 @@ struct Solver {
     // R = B - V X with precision prec (B: ld ldb; X: ld ldx).
     gyps_status residual(const double2 *B, int64_t ldb, const double2 *X, int64_t ldx, int prec)
     {
-        GYPS_TRY(apply_device(m, k, nrhs, X, ldx, w.W, nv, prec, 0, 0, m->nt, s));
+        GYPS_TRY(op(X, ldx, w.W, prec));
         zresid_kernel<<<grid_v, 256, 0, s>>>(B, ldb, w.W, nv, w.R);
         GYPS_CUDA(cudaGetLastError());
         return GYPS_OK;
@@ -295,7 +305,7 @@ struct Solver {
                     }
                     vin = zj;
                 }
-                GYPS_TRY(apply_device(this->m, k, nrhs, vin, nv, w.W, nv, prec, 0, 0, this->m->nt, s));
+                GYPS_TRY(op(vin, nv, w.W, prec));
                 ++applies;
                 ++iters;
                 --budget;
@@ -407,6 +417,8 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
     S.restart = o.restart;
     S.s = s;
     S.nv = m->nv;
+    S.form = o.formulation;
+    S.eta = o.eta;
     S.grid_v = dim3((unsigned)((m->nv + 255) / 256), (unsigned)nrhs);
     S.grid_r = dim3((unsigned)std::min<int64_t>((m->nv + 255) / 256, 64), (unsigned)nrhs);
     const size_t blk = (size_t)m->nv * nrhs * sizeof(double2);
@@ -515,6 +527,14 @@ extern "C" gyps_status gyps_gmres_solve(gyps_mesh_t h, double k, int nrhs, const
     const gyps_gmres_opts &o = *opts;
     if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 4096 || o.maxit < 1 || o.max_refine < 0)
         return set_error(GYPS_ERR_INVALID, "bad GMRES options");
+    if (o.formulation != GYPS_FORM_SINGLE_LAYER && o.formulation != GYPS_FORM_BRAKHAGE_WERNER)
+        return set_error(GYPS_ERR_INVALID, "unknown formulation");
+    if (o.formulation == GYPS_FORM_BRAKHAGE_WERNER) {
+        if (!std::isfinite(o.eta)) return set_error(GYPS_ERR_INVALID, "eta must be finite");
+        if (o.precond) return set_error(GYPS_ERR_UNSUPPORTED, "the learned preconditioner models the single layer");
+        if (o.prec == GYPS_PREC_TC_BF16X3 && nrhs < 16)
+            return set_error(GYPS_ERR_UNSUPPORTED, "tensor-core precision needs 16 or more right-hand sides");
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const bool df = is_device_pointer(F), dx = is_device_pointer(X);
     if (df && dx) return gmres_device(m, k, nrhs, (const double2 *)F, ldf, (double2 *)X, ldx, o, report, s);

@@ -89,6 +89,7 @@ struct Mesh {
     void *ws_den = nullptr; size_t ws_den_bytes = 0;   // density panel / FP64 densities
     void *ws_v = nullptr; size_t ws_v_bytes = 0;       // target accumulators
     void *ws_stage = nullptr; size_t ws_stage_bytes = 0;  // host<->device staging
+    void *ws_bw = nullptr; size_t ws_bw_bytes = 0;        // K X of the combined operator
     void *ws_tc = nullptr; size_t ws_tc_bytes = 0;        // tensor-core source panel
     void *ws_pts = nullptr; size_t ws_pts_bytes = 0;      // potential at points: point copies, far sums, staging
     double4_32a *d_tri_cen = nullptr;                     // per triangle: centroid, (2 x largest centroid-vertex distance)^2
@@ -163,6 +164,12 @@ gyps_status far_tc(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, d
                    cudaStream_t s);
 cudaError_t launch_near_spmv(const Mesh &m, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
                              cudaStream_t s);
+
+// Double layer Y = K X and the combined operator Y = (1/2 M + K - i eta V) X (device pointers)
+gyps_status dl_apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
+                            int prec, cudaStream_t s);
+gyps_status bw_apply_device(Mesh *m, double k, double eta, int nrhs, const double2 *X, int64_t ldx, double2 *Y,
+                            int64_t ldy, int prec, cudaStream_t s);
 
 // a6, a7
 gyps_status assemble_device(Mesh *m, double k, int prec, double2 *V, int64_t ldv, cudaStream_t s);

@@ -55,3 +55,32 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib_path):
     assert lib.gyps_last_error(buf, 256) == 1
     assert b"quad_points" in buf.value
     assert lib.gyps_sl_apply(None, 1.0, 1, None, 1, None, 1, 1, 0, -1, -1, None) == 1
+
+
+STRUCTS = {"_MeshInfo": "gyps_mesh_info_t", "_Profile": "gyps_profile_t", "_BatchItem": "gyps_batch_item",
+           "_BatchInfo": "gyps_batch_info_t", "_GmresOpts": "gyps_gmres_opts", "_GmresReport": "gyps_gmres_report"}
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes mirror has the header struct's size and field offsets (gcc on the header)."""
+    import shutil
+    import subprocess
+    import paper_1804_00995_gb300 as g
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "gyps.h"', "int main(void) {"]
+    expect = []
+    for py, c in STRUCTS.items():
+        cls = getattr(g, py)
+        lines.append(f'printf("%zu\\n", sizeof({c}));')
+        expect.append(ctypes.sizeof(cls))
+        for name, _ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({c}, {name}));')
+            expect.append(getattr(cls, name).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
