@@ -182,10 +182,11 @@ gyps_status gyps_sl_assemble(gyps_mesh_t mesh, double k, int prec, void *V, int6
  * of lambda_j n . (x - y)/|x - y|^3 minus its Gauss sum.  On the unit sphere
  * K Y_n = (1/2 + i k^2 j_n(k) h_n'(k)) Y_n (-1/(2(2n+1)) at k = 0).
  *   X, Y  nv x nrhs complex double2 (host or device), leading dims >= nv.
- *   prec  GYPS_PREC_FP64 or GYPS_PREC_FP32 (AUTO); the correction is FP64.
+ *   prec  GYPS_PREC_FP64, GYPS_PREC_FP32 (AUTO) or GYPS_PREC_DF64 for the far
+ *         sum; the correction is FP64.
  * Built with its correction on the first call (then cached in the mesh).
- * Synchronous. Errors: INVALID, UNSUPPORTED (tensor-core or double-float
- * precision), CUDA, OOM.
+ * Synchronous. Errors: INVALID, UNSUPPORTED (tensor-core precision), CUDA,
+ * OOM, TIMEOUT.
  */
 gyps_status gyps_dl_apply(gyps_mesh_t mesh, double k, int nrhs, const void *X, int64_t ldx, void *Y, int64_t ldy,
                           int prec, void *stream);
@@ -202,8 +203,8 @@ gyps_status gyps_dl_apply(gyps_mesh_t mesh, double k, int nrhs, const void *X, i
  * k > 0 (no interior resonances).  On the unit sphere its eigenvalue for
  * degree-n harmonics is 1/2 + mu_n(K) - i eta mu_n(V).
  *   X, Y  nv x nrhs complex double2 (host or device), leading dims >= nv, not overlapping.
- *   prec  precision of V (as gyps_sl_apply); K is FP64 for GYPS_PREC_FP64 and
- *         GYPS_PREC_DF64, FP32 otherwise; M is FP64.
+ *   prec  precision of V (as gyps_sl_apply); K takes the same precision for
+ *         GYPS_PREC_FP64 and GYPS_PREC_DF64, FP32 otherwise; M is FP64.
  * Synchronous. Errors: INVALID, UNSUPPORTED (tensor cores with k = 0 or fewer
  * than 16 columns), CUDA, OOM, TIMEOUT.
  */

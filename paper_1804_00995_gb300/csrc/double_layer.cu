@@ -10,6 +10,7 @@
 // its Gauss sum.
 #include <cmath>
 
+#include "far_tile.cuh"
 #include "internal.h"
 #include "p1_geom.cuh"
 
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(128) far_dl64_kernel(const double4_32a *pts, c
     __shared__ double4_32a sn[128];
     __shared__ double2 su[128][R];
     const int64_t tg = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    const int64_t tq0 = (tg / q) * q;
     const double4_32a x = pts[min(tg, nq - 1)];
     double ar[R], ai[R];
 #pragma unroll
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(128) far_dl64_kernel(const double4_32a *pts, c
         __syncthreads();
         const int n = (int)min((int64_t)128, nq - s0);
         for (int ll = 0; ll < n; ++ll) {
-            if ((s0 + ll) / q == tg / q) continue;  // same flat triangle: n . (x - y) = 0
+            if ((uint64_t)(s0 + ll - tq0) < (uint64_t)q) continue;  // same flat triangle: n . (x - y) = 0
             const double4_32a y = sp[ll], nn = sn[ll];
             const double dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
             const double r2 = dx * dx + dy * dy + dz * dz;
@@ -130,93 +132,299 @@ __global__ void __launch_bounds__(128) far_dl64_kernel(const double4_32a *pts, c
     }
 }
 
-__device__ __forceinline__ float mufu_rsqrt_dl(float x)
+// ---------------------------------------------------------------- far part, FP32
+// The FP32 form follows the single layer's tile design: a persistent grid walks
+// (target tile) x (source tile) items, source tiles are staged by 1-D bulk copies
+// into a 3-stage ring (positions, normals, densities), every thread owns T
+// targets and takes source points in pairs with packed f32x2 arithmetic, and
+// per-tile FP32 sums are folded into TwoSum pairs.  Coordinates are scaled by k,
+// so rs = 1/(k r), k r = r2 rs and n . (x - y) rs^3 = H-factor / k^2, restored
+// at the flush; Laplace (k = 0) runs unscaled without the phase.  Pairs inside
+// one triangle (its q points are consecutive) give 0.
+//
+// Normal panel tile, in the position panel's pair layout:
+//   float4 NXY[P] = (nx0, nx1, ny0, ny1), float2 NZ[P] = (nz0, nz1); padding 0.
+__global__ void nrm_panel_kernel(const double4_32a *nrm, int q, int64_t nq, int64_t nq_pad, float *panel)
 {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float mufu_sin_dl(float x)
-{
-    float y;
-    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float mufu_cos_dl(float x)
-{
-    float y;
-    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nq_pad) return;
+    float x = 0.0f, y = 0.0f, z = 0.0f;
+    if (l < nq) {
+        const double4_32a n = nrm[l / q];
+        x = (float)n.x;
+        y = (float)n.y;
+        z = (float)n.z;
+    }
+    const int64_t tile = l / kSrcTile;
+    const int p = (int)(l % kSrcTile) >> 1, lane = (int)(l & 1);
+    float *base = panel + tile * kPosTileFloats;
+    base[4 * p + lane] = x;
+    base[4 * p + 2 + lane] = y;
+    base[4 * kSrcPairs + 2 * p + lane] = z;
 }
 
-// The same in FP32: coordinates scaled by k (k r = r2 rs; unscaled with phase 0
-// for the Laplace kernel), phase reduced to
-// [-pi, pi] by the nearest multiple of 2 pi, MUFU rsqrt / sin / cos; the
-// factor k^2 of n . (x - y) / r^3 under the scaling is applied at the end.
-// Per tile of 128 sources the FP32 sums are added into FP64 accumulators.
-template <int R>
-__global__ void __launch_bounds__(128) far_dl32_kernel(const double4_32a *pts, const double4_32a *nrm, int q,
-                                                       const double2 *u64, int64_t ldu, int c0, int64_t nq, float ks,
-                                                       float kfac, double2 *v, int64_t ldv)
+struct DlArgs {
+    const float *pos_panel, *nrm_panel, *den_panel;
+    const float4 *tgt;
+    double2 *v;
+    int64_t ldv, nq, n_src_tiles, n_tgt_tiles;
+    int q;
+    float ks;
+    int *err;
+};
+
+template <int R, int T>
+struct DlCfg {
+    static constexpr int NT = 128;
+    static constexpr int TT = NT * T;
+    static constexpr int STAGES = 3;
+    static constexpr int POS_BYTES = kPosTileFloats * 4;
+    static constexpr int NRM_BYTES = kPosTileFloats * 4;
+    static constexpr int DEN_BYTES = kSrcPairs * 6 * R * 4;
+    static constexpr int STAGE_BYTES = POS_BYTES + NRM_BYTES + DEN_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 64;
+};
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <int R, int T, bool LAP, bool CHECK>
+__device__ __forceinline__ void dl_tile(const float *sp, const float2 (&tx)[T], const float2 (&ty)[T],
+                                        const float2 (&tz)[T], const int64_t (&tq0)[T], int64_t src0, int q,
+                                        float ks, float2 (&are)[T][R], float2 (&aim)[T][R])
 {
-    __shared__ float4 sp[128];      // (x, y, z) k
-    __shared__ float4 sn[128];      // normal
-    __shared__ float2 su[128][R];
-    const int64_t tg = (int64_t)blockIdx.x * 128 + threadIdx.x;
-    const double4_32a x64 = pts[min(tg, nq - 1)];
-    const float tx = (float)x64.x * ks, ty = (float)x64.y * ks, tz = (float)x64.z * ks;
-    double ar[R], ai[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) ar[j] = ai[j] = 0.0;
-    for (int64_t s0 = 0; s0 < nq; s0 += 128) {
-        const int64_t l = s0 + threadIdx.x;
-        if (l < nq) {
-            const double4_32a p = pts[l];
-            const double4_32a nn = nrm[l / q];
-            sp[threadIdx.x] = make_float4((float)p.x * ks, (float)p.y * ks, (float)p.z * ks, 0.0f);
-            sn[threadIdx.x] = make_float4((float)nn.x, (float)nn.y, (float)nn.z, 0.0f);
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const double2 uu = u64[l + (int64_t)(c0 + j) * ldu];
-                su[threadIdx.x][j] = make_float2((float)uu.x, (float)uu.y);
-            }
+    const float4 *XY = reinterpret_cast<const float4 *>(sp);
+    const float2 *Z = reinterpret_cast<const float2 *>(sp + 4 * kSrcPairs);
+    const float4 *NXY = reinterpret_cast<const float4 *>(sp + kPosTileFloats);
+    const float2 *NZ = reinterpret_cast<const float2 *>(sp + kPosTileFloats + 4 * kSrcPairs);
+    const float4 *U = reinterpret_cast<const float4 *>(sp + 2 * kPosTileFloats);
+    const float2 *N = reinterpret_cast<const float2 *>(sp + 2 * kPosTileFloats + 4 * kSrcPairs * R);
+    const float2 ks2 = make_float2(ks, ks);
+    const float2 magic = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23: round to integer
+    const float2 nmagic = make_float2(-12582912.0f, -12582912.0f);
+    const float2 inv2pi = make_float2(0.159154943091895335769f, 0.159154943091895335769f);
+    const float2 m2pi = make_float2(-6.28318530717958647692f, -6.28318530717958647692f);
+#pragma unroll 2
+    for (int p = 0; p < kSrcPairs; ++p) {
+        const float4 xy = XY[p], nxy = NXY[p];
+        float2 sx = make_float2(xy.x, xy.y), sy = make_float2(xy.z, xy.w), sz = Z[p];
+        const float2 nx = make_float2(nxy.x, nxy.y), ny = make_float2(nxy.z, nxy.w), nz = NZ[p];
+        if (!LAP) {
+            sx = __fmul2_rn(sx, ks2);
+            sy = __fmul2_rn(sy, ks2);
+            sz = __fmul2_rn(sz, ks2);
         }
-        __syncthreads();
-        const int n = (int)min((int64_t)128, nq - s0);
-        float br[R], bi[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) br[j] = bi[j] = 0.0f;
-        for (int ll = 0; ll < n; ++ll) {
-            if ((s0 + ll) / q == tg / q) continue;  // same flat triangle: n . (x - y) = 0
-            const float4 y = sp[ll], nn = sn[ll];
-            const float dx = tx - y.x, dy = ty - y.y, dz = tz - y.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const float rs = mufu_rsqrt_dl(r2);
-            const float kr = kfac * (r2 * rs);  // k r (0 for the Laplace kernel)
-            const float nr = rintf(kr * 0.159154943091895335769f);
-            const float ang = fmaf(nr, -6.28318530717958647692f, kr);
-            const float s = mufu_sin_dl(ang), c = mufu_cos_dl(ang);
-            const float f = (nn.x * dx + nn.y * dy + nn.z * dz) * rs * rs * rs;
-            const float hr = (c + kr * s) * f, hi = (s - kr * c) * f;
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const float2 uu = su[ll][j];
-                br[j] = fmaf(hr, uu.x, fmaf(-hi, uu.y, br[j]));
-                bi[j] = fmaf(hr, uu.y, fmaf(hi, uu.x, bi[j]));
-            }
-        }
+        float2 ure[R], uim[R], unim[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            ar[j] += (double)br[j];
-            ai[j] += (double)bi[j];
+            const float4 u = U[p * R + j];
+            ure[j] = make_float2(u.x, u.y);
+            uim[j] = make_float2(u.z, u.w);
+            if (!LAP) unim[j] = N[p * R + j];
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const float2 dx = __fadd2_rn(tx[t], sx);
+            const float2 dy = __fadd2_rn(ty[t], sy);
+            const float2 dz = __fadd2_rn(tz[t], sz);
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 rs = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+            float2 dn = __fmul2_rn(nx, dx);
+            dn = __ffma2_rn(ny, dy, dn);
+            dn = __ffma2_rn(nz, dz, dn);
+            float2 f = __fmul2_rn(__fmul2_rn(dn, rs), __fmul2_rn(rs, rs));  // n . (x - y) / r^3
+            if (LAP) {
+                if (CHECK) {
+                    if ((uint64_t)(src0 + 2 * p - tq0[t]) < (uint64_t)q) f.x = 0.0f;
+                    if ((uint64_t)(src0 + 2 * p + 1 - tq0[t]) < (uint64_t)q) f.y = 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    are[t][j] = __ffma2_rn(f, ure[j], are[t][j]);
+                    aim[t][j] = __ffma2_rn(f, uim[j], aim[t][j]);
+                }
+                continue;
+            }
+            const float2 ph = __fmul2_rn(r2, rs);                               // k r
+            const float2 nr = __fadd2_rn(__ffma2_rn(ph, inv2pi, magic), nmagic);  // nearest integer to k r / (2 pi)
+            const float2 ang = __ffma2_rn(nr, m2pi, ph);                        // in [-pi, pi]
+            const float2 sn = make_float2(sin_mufu(ang.x), sin_mufu(ang.y));
+            const float2 cs = make_float2(cos_mufu(ang.x), cos_mufu(ang.y));
+            // (1 - i k r) exp(i k r) f = (cos + kr sin) f + i (sin - kr cos) f
+            const float2 cf = __fmul2_rn(cs, f), sf = __fmul2_rn(sn, f);
+            float2 hre = __ffma2_rn(ph, sf, cf);
+            float2 him = __ffma2_rn(neg2(ph), cf, sf);
+            if (CHECK) {  // same triangle (and the point itself): 0
+                if ((uint64_t)(src0 + 2 * p - tq0[t]) < (uint64_t)q) hre.x = him.x = 0.0f;
+                if ((uint64_t)(src0 + 2 * p + 1 - tq0[t]) < (uint64_t)q) hre.y = him.y = 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                are[t][j] = __ffma2_rn(hre, ure[j], are[t][j]);
+                are[t][j] = __ffma2_rn(him, unim[j], are[t][j]);
+                aim[t][j] = __ffma2_rn(hre, uim[j], aim[t][j]);
+                aim[t][j] = __ffma2_rn(him, ure[j], aim[t][j]);
+            }
+        }
+    }
+}
+
+template <int R, int T, bool LAP>
+__global__ void __launch_bounds__(DlCfg<R, T>::NT) far_dl32_kernel(const DlArgs a)
+{
+    using C = DlCfg<R, T>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE_BYTES);
+    const int tid_x = threadIdx.x;
+    const int64_t items = a.n_tgt_tiles * a.n_src_tiles;
+    const int64_t beg = items * blockIdx.x / gridDim.x;
+    const int64_t end = items * (blockIdx.x + 1) / gridDim.x;
+    if (beg >= end) return;
+    if (tid_x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int64_t item) {
+        const int s = (int)((item - beg) % C::STAGES);
+        const int64_t st = item % a.n_src_tiles;
+        const uint32_t bar = smem_addr(&bars[s]);
+        const uint32_t dst = smem_addr(smem + s * C::STAGE_BYTES);
+        mbar_expect_tx(bar, C::STAGE_BYTES);
+        bulk_g2s(dst, a.pos_panel + st * kPosTileFloats, C::POS_BYTES, bar);
+        bulk_g2s(dst + C::POS_BYTES, a.nrm_panel + st * kPosTileFloats, C::NRM_BYTES, bar);
+        bulk_g2s(dst + C::POS_BYTES + C::NRM_BYTES, a.den_panel + st * den_tile_floats(R), C::DEN_BYTES, bar);
+    };
+    int64_t issued = beg;
+    if (tid_x == 0)
+        for (; issued < end && issued < beg + C::STAGES - 1; ++issued) issue(issued);
+
+    float2 tx[T], ty[T], tz[T];
+    int64_t tid[T], tq0[T];
+    float2 are[T][R], aim[T][R];
+    float hre[T][R], lre[T][R], him[T][R], lim[T][R];
+    int64_t cur_tt = -1;
+    const double scale = (double)a.ks * (double)a.ks;
+    auto flush = [&]() {
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            if (tid[t] < a.nq) {
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    double *dst = reinterpret_cast<double *>(a.v + tid[t] + j * a.ldv);
+                    atomicAdd(dst, ((double)hre[t][j] + (double)lre[t][j]) * scale);
+                    atomicAdd(dst + 1, ((double)him[t][j] + (double)lim[t][j]) * scale);
+                }
+            }
+        }
+    };
+    bool failed = false;
+    int64_t i = beg;
+    for (; i < end; ++i) {
+        if (tid_x == 0 && issued < end && issued == i + C::STAGES - 1) {
+            issue(issued);
+            ++issued;
+        }
+        const int64_t tt = i / a.n_src_tiles, st = i % a.n_src_tiles;
+        const int64_t tb = tt * C::TT;
+        const int64_t te = min(tb + (int64_t)C::TT, a.nq);
+        if (tt != cur_tt) {
+            if (cur_tt >= 0) flush();
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const int64_t g = tb + tid_x + t * C::NT;
+                tid[t] = g;
+                tq0[t] = (g / a.q) * a.q;
+                float4 p = a.tgt[min(g, a.nq - 1)];
+                if (!LAP) {
+                    p.x *= a.ks;
+                    p.y *= a.ks;
+                    p.z *= a.ks;
+                }
+                tx[t] = make_float2(p.x, p.x);
+                ty[t] = make_float2(p.y, p.y);
+                tz[t] = make_float2(p.z, p.z);
+#pragma unroll
+                for (int j = 0; j < R; ++j) hre[t][j] = lre[t][j] = him[t][j] = lim[t][j] = 0.0f;
+            }
+            cur_tt = tt;
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int j = 0; j < R; ++j) are[t][j] = aim[t][j] = make_float2(0.0f, 0.0f);
+        const int s = (int)((i - beg) % C::STAGES);
+        const uint32_t parity = (uint32_t)(((i - beg) / C::STAGES) & 1);
+        const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), parity);
+        if (ok) {
+            const float *sp = reinterpret_cast<const float *>(smem + s * C::STAGE_BYTES);
+            const int64_t src0 = st * kSrcTile;
+            // a triangle's q <= 7 points may straddle a tile boundary
+            if (tb - 8 < src0 + kSrcTile && src0 < te + 8)
+                dl_tile<R, T, LAP, true>(sp, tx, ty, tz, tq0, src0, a.q, a.ks, are, aim);
+            else
+                dl_tile<R, T, LAP, false>(sp, tx, ty, tz, tq0, src0, a.q, a.ks, are, aim);
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    two_sum_acc(hre[t][j], lre[t][j], __fadd_rn(are[t][j].x, are[t][j].y));
+                    two_sum_acc(him[t][j], lim[t][j], __fadd_rn(aim[t][j].x, aim[t][j].y));
+                }
+        }
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+    }
+    if (failed) {
+        // report, then wait (bounded) for the copies still in flight
+        if (tid_x == 0) {
+            atomicExch(a.err, 1);
+            for (int64_t j = i; j < issued; ++j) {
+                const int s = (int)((j - beg) % C::STAGES);
+                mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)(((j - beg) / C::STAGES) & 1));
+            }
         }
         __syncthreads();
+        return;
     }
-    if (tg < nq) {
-        const double k2 = (double)ks * (double)ks;
-#pragma unroll
-        for (int j = 0; j < R; ++j) v[tg + (int64_t)(c0 + j) * ldv] = make_double2(ar[j] * k2, ai[j] * k2);
-    }
+    flush();
+}
+
+template <int R, int T>
+static gyps_status run_far_dl32(Mesh *m, double k, const double2 *X, int64_t ldx, int c0, double2 *v, int64_t ldv,
+                                cudaStream_t s)
+{
+    using C = DlCfg<R, T>;
+    float *panel = reinterpret_cast<float *>(m->ws_den);
+    GYPS_CUDA(launch_interp32(m, X, ldx, c0, R, panel, s));
+    DlArgs a;
+    a.pos_panel = m->d_pos_panel;
+    a.nrm_panel = m->d_nrm_panel;
+    a.den_panel = panel;
+    a.tgt = m->d_pts32;
+    a.v = v + (int64_t)c0 * ldv;
+    a.ldv = ldv;
+    a.nq = m->nq;
+    a.n_src_tiles = m->n_src_tiles;
+    a.n_tgt_tiles = (m->nq + C::TT - 1) / C::TT;
+    a.q = m->q;
+    a.ks = k > 0.0 ? (float)k : 1.0f;
+    a.err = m->d_err;
+    auto kern = k > 0.0 ? far_dl32_kernel<R, T, false> : far_dl32_kernel<R, T, true>;
+    GYPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    int occ = 0;
+    GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::NT, C::SMEM));
+    occ = occ > 1 ? occ : 1;
+    const int64_t items = a.n_tgt_tiles * a.n_src_tiles;
+    const int64_t grid = items < (int64_t)m->num_sms * occ ? items : (int64_t)m->num_sms * occ;
+    StageTimer tf(m, s, 1);
+    kern<<<(unsigned)grid, C::NT, C::SMEM, s>>>(a);
+    GYPS_CUDA(cudaGetLastError());
+    tf.done(1);
+    return GYPS_OK;
 }
 
 // Normals and the double-layer correction values (CSR of C), once per mesh.
@@ -243,39 +451,63 @@ static gyps_status dl_prepare(Mesh *m, cudaStream_t s)
         if (val) cudaFree(val);
         return cuda_error(e, "double-layer correction");
     }
-    GYPS_CUDA(cudaStreamSynchronize(s));
+    e = cudaMalloc((void **)&m->d_nrm_panel, (size_t)m->n_src_tiles * kPosTileFloats * sizeof(float));
+    if (e == cudaSuccess) {
+        nrm_panel_kernel<<<(unsigned)((m->nq_pad + 255) / 256), 256, 0, s>>>(m->d_tri_nrm, m->q, m->nq, m->nq_pad,
+                                                                           m->d_nrm_panel);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(val);
+        return cuda_error(e, "double-layer normal panel");
+    }
     m->d_cdl_val = val;
     return GYPS_OK;
 }
 
 gyps_status dl_apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
-                                   int prec, cudaStream_t s)
+                            int prec, cudaStream_t s)
 {
     GYPS_TRY(dl_prepare(m, s));
     const int64_t ld = m->nq;
-    GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(ld * nrhs) * sizeof(double2)));
     GYPS_TRY(grow(m, &m->ws_v, &m->ws_v_bytes, (size_t)(ld * nrhs) * sizeof(double2)));
-    double2 *u64 = reinterpret_cast<double2 *>(m->ws_den);
     double2 *v = reinterpret_cast<double2 *>(m->ws_v);
-    dim3 gi((unsigned)((m->nq + 255) / 256), (unsigned)nrhs);
-    interp64_kernel<<<gi, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, ld, X, ldx, nrhs, u64);
-    GYPS_CUDA(cudaGetLastError());
-    const unsigned grid = (unsigned)((m->nq + 127) / 128);
-    for (int c0 = 0; c0 < nrhs;) {
-        const int w = nrhs - c0 >= 4 ? 4 : nrhs - c0 >= 2 ? 2 : 1;
-        if (prec == GYPS_PREC_FP64) {
+    if (prec == GYPS_PREC_FP64 || prec == GYPS_PREC_DF64) {
+        GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(ld * nrhs) * sizeof(double2)));
+        double2 *u64 = reinterpret_cast<double2 *>(m->ws_den);
+        dim3 gi((unsigned)((m->nq + 255) / 256), (unsigned)nrhs);
+        interp64_kernel<<<gi, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, ld, X, ldx, nrhs, u64);
+        GYPS_CUDA(cudaGetLastError());
+        const unsigned grid = (unsigned)((m->nq + 127) / 128);
+        for (int c0 = 0; c0 < nrhs;) {
+            const int w = nrhs - c0 >= 4 ? 4 : nrhs - c0 >= 2 ? 2 : 1;
+            if (prec == GYPS_PREC_DF64) {
+                GYPS_TRY(run_far_dl_df(m, k, u64, ld, c0, w, v, ld, s));
+                c0 += w;
+                continue;
+            }
             if (w == 4) far_dl64_kernel<4><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, k, v, ld);
             else if (w == 2) far_dl64_kernel<2><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, k, v, ld);
             else far_dl64_kernel<1><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, k, v, ld);
-        } else {
-            // coordinates scaled by k (1 for the Laplace kernel, where the phase is 0)
-            const float ks = k > 0.0 ? (float)k : 1.0f, kfac = k > 0.0 ? 1.0f : 0.0f;
-            if (w == 4) far_dl32_kernel<4><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, ks, kfac, v, ld);
-            else if (w == 2) far_dl32_kernel<2><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, ks, kfac, v, ld);
-            else far_dl32_kernel<1><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, ks, kfac, v, ld);
+            GYPS_CUDA(cudaGetLastError());
+            c0 += w;
         }
-        GYPS_CUDA(cudaGetLastError());
-        c0 += w;
+    } else {
+        // the FP32 kernel adds into v with atomics
+        GYPS_CUDA(cudaMemsetAsync(v, 0, (size_t)(ld * nrhs) * sizeof(double2), s));
+        GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(m->n_src_tiles * den_tile_floats(8)) * sizeof(float)));
+        for (int c0 = 0; c0 < nrhs;) {
+            const int rem = nrhs - c0;
+            const int w = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
+            switch (w) {
+            case 8: GYPS_TRY((run_far_dl32<8, 2>(m, k, X, ldx, c0, v, ld, s))); break;
+            case 4: GYPS_TRY((run_far_dl32<4, 2>(m, k, X, ldx, c0, v, ld, s))); break;
+            case 2: GYPS_TRY((run_far_dl32<2, 4>(m, k, X, ldx, c0, v, ld, s))); break;
+            default: GYPS_TRY((run_far_dl32<1, 4>(m, k, X, ldx, c0, v, ld, s))); break;
+            }
+            c0 += w;
+        }
     }
     dim3 gp((unsigned)((m->nv + 127) / 128), (unsigned)nrhs);
     project_kernel<<<gp, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_pts64, m->rule, m->nv, v, ld, m->d_c_rowptr,
@@ -316,14 +548,14 @@ __global__ void bw_combine_kernel(const int32_t *v2t_ptr, const int32_t *v2t, co
     Y[i + c * ldy] = make_double2(0.5 * mr + kx.x + eta * vx.y, 0.5 * mi + kx.y - eta * vx.x);
 }
 
-// Y = (1/2 M + K - i eta V) X.  V in prec; K in FP64 for the FP64 and
-// double-float precisions, in FP32 otherwise.
+// Y = (1/2 M + K - i eta V) X.  V in prec; K in prec for FP64 and
+// double-float, in FP32 otherwise.
 gyps_status bw_apply_device(Mesh *m, double k, double eta, int nrhs, const double2 *X, int64_t ldx, double2 *Y,
                             int64_t ldy, int prec, cudaStream_t s)
 {
     GYPS_TRY(grow(m, &m->ws_bw, &m->ws_bw_bytes, (size_t)m->nv * nrhs * sizeof(double2)));
     double2 *T = reinterpret_cast<double2 *>(m->ws_bw);
-    const int kprec = (prec == GYPS_PREC_FP64 || prec == GYPS_PREC_DF64) ? GYPS_PREC_FP64 : GYPS_PREC_FP32;
+    const int kprec = (prec == GYPS_PREC_FP64 || prec == GYPS_PREC_DF64) ? prec : GYPS_PREC_FP32;
     GYPS_TRY(dl_apply_device(m, k, nrhs, X, ldx, T, m->nv, kprec, s));
     GYPS_TRY(apply_device(m, k, nrhs, X, ldx, Y, ldy, prec, 0, 0, m->nt, s));
     dim3 g((unsigned)((m->nv + 127) / 128), (unsigned)nrhs);
@@ -347,9 +579,9 @@ extern "C" gyps_status gyps_dl_apply(gyps_mesh_t h, double k, int nrhs, const vo
     if (ldx < m->nv || ldy < m->nv) return set_error(GYPS_ERR_INVALID, "leading dimension < nv");
     if (!std::isfinite(k) || k < 0.0) return set_error(GYPS_ERR_INVALID, "k must be finite and >= 0");
     if (prec == GYPS_PREC_AUTO) prec = GYPS_PREC_FP32;
-    if (prec == GYPS_PREC_TC_BF16X3 || prec == GYPS_PREC_DF64)
-        return set_error(GYPS_ERR_UNSUPPORTED, "double layer: FP64 or FP32");
-    if (prec != GYPS_PREC_FP64 && prec != GYPS_PREC_FP32) return set_error(GYPS_ERR_INVALID, "unknown precision");
+    if (prec == GYPS_PREC_TC_BF16X3) return set_error(GYPS_ERR_UNSUPPORTED, "double layer: FP64, FP32 or DF64");
+    if (prec != GYPS_PREC_FP64 && prec != GYPS_PREC_FP32 && prec != GYPS_PREC_DF64)
+        return set_error(GYPS_ERR_INVALID, "unknown precision");
     cudaStream_t s = (cudaStream_t)stream;
     const bool dx = is_device_pointer(X), dy = is_device_pointer(Y);
     const size_t blk = (size_t)m->nv * nrhs * sizeof(double2);
@@ -374,7 +606,7 @@ extern "C" gyps_status gyps_dl_apply(gyps_mesh_t h, double k, int nrhs, const vo
         GYPS_CUDA(cudaMemcpy2DAsync(Y, ldy * sizeof(double2), ys, m->nv * sizeof(double2), m->nv * sizeof(double2), nrhs,
                                     cudaMemcpyDeviceToHost, s));
     GYPS_CUDA(cudaStreamSynchronize(s));
-    return GYPS_OK;
+    return check_err_word(m, s);
 }
 
 extern "C" gyps_status gyps_bw_apply(gyps_mesh_t h, double k, double eta, int nrhs, const void *X, int64_t ldx,

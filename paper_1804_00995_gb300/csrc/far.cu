@@ -53,6 +53,19 @@ __global__ void interp32_kernel(const int32_t *tri, const double4_32a *pts64, co
     }
 }
 
+// The density panel of columns c0 .. c0+w-1 (w = 1, 2, 4 or 8) for kernels of other TUs.
+cudaError_t launch_interp32(const Mesh *m, const double2 *X, int64_t ldx, int c0, int w, float *panel, cudaStream_t s)
+{
+    const unsigned g = (unsigned)((m->nq_pad + 255) / 256);
+    switch (w) {
+    case 8: interp32_kernel<8><<<g, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, m->nq_pad, X, ldx, c0, panel); break;
+    case 4: interp32_kernel<4><<<g, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, m->nq_pad, X, ldx, c0, panel); break;
+    case 2: interp32_kernel<2><<<g, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, m->nq_pad, X, ldx, c0, panel); break;
+    default: interp32_kernel<1><<<g, 256, 0, s>>>(m->d_tri, m->d_pts64, m->rule, m->nq, m->nq_pad, X, ldx, c0, panel); break;
+    }
+    return cudaGetLastError();
+}
+
 // FP64 densities u64[l + j*ld] for all nrhs columns.
 __global__ void interp64_kernel(const int32_t *tri, const double4_32a *pts64, const Rule rule, int64_t nq, int64_t ld,
                                 const double2 *X, int64_t ldx, int nrhs, double2 *u64)

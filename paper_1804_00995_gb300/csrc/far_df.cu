@@ -91,6 +91,40 @@ __device__ __forceinline__ float rsqrt_mufu(float x)
     return y;
 }
 
+// Phase and distance of one pair in double-float: from r2 = |x - y|^2, the
+// reciprocal rs = 1/r (MUFU estimate, one Newton step), phi = k r and
+// (cos phi, sin phi) by the table and the Taylor remainder.
+struct Phase {
+    df rs, phi, cs, sn;
+};
+
+__device__ __forceinline__ Phase phase_of(df r2, df kd, const float4 *tab)
+{
+    const df one = {1.0f, 0.0f};
+    const df step = from_double(6.283185307179586476925286766559 / kTab);  // 2 pi / kTab
+    const float inv_step = (float)(kTab / 6.283185307179586476925286766559);
+    const df m_sixth = from_double(-1.0 / 6.0);
+    Phase o;
+    // r^-1/2 ... 1/r: y0 from MUFU, one Newton step y = y0 + y0 (1 - r2 y0^2) / 2
+    const float y0 = rsqrt_mufu(r2.hi);
+    const df t = mulf(mulf(r2, y0), y0);
+    const float e = add(one, neg(t)).hi;
+    o.rs = fast_two_sum(y0, 0.5f * y0 * e);
+    o.phi = mul(kd, mul(r2, o.rs));  // k r
+    // phi = j (2 pi / kTab) + d, |d| <= pi / kTab
+    const float jf = rintf(o.phi.hi * inv_step);
+    const df d = add(o.phi, neg(mulf(step, jf)));
+    const float4 sc = tab[((int)jf) & (kTab - 1)];
+    const df sa = {sc.x, sc.y}, ca = {sc.z, sc.w};
+    const df u = mul(d, d);
+    const float u2 = u.hi * u.hi;
+    const df sd = mul(d, add(add(one, mul(u, m_sixth)), df{u2 * (1.0f / 120.0f), 0.0f}));
+    const df cd = add(add(one, df{-0.5f * u.hi, -0.5f * u.lo}), df{u2 * (1.0f / 24.0f), 0.0f});
+    o.sn = add(mul(sa, cd), mul(ca, sd));
+    o.cs = add(mul(ca, cd), neg(mul(sa, sd)));
+    return o;
+}
+
 // exp(i phi) / r and the G u products for targets tgt[t], t in [t_begin, t_end);
 // self: the targets are the sources, the point paired with itself takes G = ik.
 template <int R>
@@ -107,10 +141,6 @@ __global__ void __launch_bounds__(128) far_df_kernel(const double4_32a *tgt, con
     const double4_32a x = tgt[min(tg, t_end - 1)];
     const df tx = from_double(x.x), ty = from_double(x.y), tz = from_double(x.z);
     const df kd = from_double(k);
-    const df step = from_double(6.283185307179586476925286766559 / kTab);  // 2 pi / kTab
-    const float inv_step = (float)(kTab / 6.283185307179586476925286766559);
-    const df one = {1.0f, 0.0f};
-    const df m_sixth = from_double(-1.0 / 6.0);
     df ar[R], ai[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) ar[j] = ai[j] = df{0.0f, 0.0f};
@@ -140,25 +170,9 @@ __global__ void __launch_bounds__(128) far_df_kernel(const double4_32a *tgt, con
                 const float2 qz = sz[ll];
                 const df dx = add(tx, df{-q.x, -q.y}), dy = add(ty, df{-q.z, -q.w}), dz = add(tz, df{-qz.x, -qz.y});
                 const df r2 = add(add(mul(dx, dx), mul(dy, dy)), mul(dz, dz));
-                // r^-1/2 ... 1/r: y0 from MUFU, one Newton step y = y0 + y0 (1 - r2 y0^2) / 2
-                const float y0 = rsqrt_mufu(r2.hi);
-                const df t = mulf(mulf(r2, y0), y0);
-                const float e = add(one, neg(t)).hi;
-                const df rs = fast_two_sum(y0, 0.5f * y0 * e);
-                const df phi = mul(kd, mul(r2, rs));  // k r
-                // phi = j (2 pi / kTab) + d, |d| <= pi / kTab
-                const float jf = rintf(phi.hi * inv_step);
-                const df d = add(phi, neg(mulf(step, jf)));
-                const float4 sc = tab[((int)jf) & (kTab - 1)];
-                const df sa = {sc.x, sc.y}, ca = {sc.z, sc.w};
-                const df u = mul(d, d);
-                const float u2 = u.hi * u.hi;
-                const df sd = mul(d, add(add(one, mul(u, m_sixth)), df{u2 * (1.0f / 120.0f), 0.0f}));
-                const df cd = add(add(one, df{-0.5f * u.hi, -0.5f * u.lo}), df{u2 * (1.0f / 24.0f), 0.0f});
-                const df sn = add(mul(sa, cd), mul(ca, sd));
-                const df cs = add(mul(ca, cd), neg(mul(sa, sd)));
-                gr = mul(cs, rs);
-                gi = mul(sn, rs);
+                const Phase ph = phase_of(r2, kd, tab);
+                gr = mul(ph.cs, ph.rs);
+                gi = mul(ph.sn, ph.rs);
             }
 #pragma unroll
             for (int j = 0; j < R; ++j) {
@@ -171,6 +185,79 @@ __global__ void __launch_bounds__(128) far_df_kernel(const double4_32a *tgt, con
         __syncthreads();
     }
     if (tg < t_end) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) v[tg + (int64_t)(c0 + j) * ldv] = make_double2(to_double(ar[j]), to_double(ai[j]));
+    }
+}
+
+// The double layer's kernel H = (1 - i k r) exp(i k r) n_y . (x - y) / r^3 in
+// double-float, the quadrature points as targets and sources; pairs inside one
+// triangle (its q consecutive points, the point itself included) give 0.
+template <int R>
+__global__ void __launch_bounds__(128) far_dl_df_kernel(const double4_32a *pts, const double4_32a *nrm, int q,
+                                                        const double2 *u64, int64_t ldu, int c0, int64_t nq, double k,
+                                                        double2 *v, int64_t ldv)
+{
+    __shared__ float4 tab[kTab];
+    __shared__ float4 sxy[128];     // (x hi, x lo, y hi, y lo)
+    __shared__ float2 sz[128];      // (z hi, z lo)
+    __shared__ float4 snxy[128];    // normal (x hi, x lo, y hi, y lo)
+    __shared__ float2 snz[128];     // normal (z hi, z lo)
+    __shared__ float4 su[128][R];   // (Re hi, Re lo, Im hi, Im lo)
+    for (int i = threadIdx.x; i < kTab; i += 128) tab[i] = g_sincos[i];
+    const int64_t tg = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    const int64_t tq0 = (tg / q) * q;
+    const double4_32a x = pts[min(tg, nq - 1)];
+    const df tx = from_double(x.x), ty = from_double(x.y), tz = from_double(x.z);
+    const df kd = from_double(k);
+    df ar[R], ai[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) ar[j] = ai[j] = df{0.0f, 0.0f};
+    for (int64_t s0 = 0; s0 < nq; s0 += 128) {
+        const int64_t l = s0 + threadIdx.x;
+        if (l < nq) {
+            const double4_32a p = pts[l];
+            const double4_32a nn = nrm[l / q];
+            const df a = from_double(p.x), b = from_double(p.y), c = from_double(p.z);
+            sxy[threadIdx.x] = make_float4(a.hi, a.lo, b.hi, b.lo);
+            sz[threadIdx.x] = make_float2(c.hi, c.lo);
+            const df na = from_double(nn.x), nb = from_double(nn.y), nc = from_double(nn.z);
+            snxy[threadIdx.x] = make_float4(na.hi, na.lo, nb.hi, nb.lo);
+            snz[threadIdx.x] = make_float2(nc.hi, nc.lo);
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const double2 uu = u64[l + (int64_t)(c0 + j) * ldu];
+                const df re = from_double(uu.x), im = from_double(uu.y);
+                su[threadIdx.x][j] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            }
+        }
+        __syncthreads();
+        const int n = (int)min((int64_t)128, nq - s0);
+        for (int ll = 0; ll < n; ++ll) {
+            if ((uint64_t)(s0 + ll - tq0) < (uint64_t)q) continue;  // same flat triangle
+            const float4 qq = sxy[ll];
+            const float2 qz = sz[ll];
+            const df dx = add(tx, df{-qq.x, -qq.y}), dy = add(ty, df{-qq.z, -qq.w}), dz = add(tz, df{-qz.x, -qz.y});
+            const df r2 = add(add(mul(dx, dx), mul(dy, dy)), mul(dz, dz));
+            const Phase ph = phase_of(r2, kd, tab);
+            const float4 nxy = snxy[ll];
+            const float2 nz = snz[ll];
+            const df dn = add(add(mul(df{nxy.x, nxy.y}, dx), mul(df{nxy.z, nxy.w}, dy)), mul(df{nz.x, nz.y}, dz));
+            const df f = mul(dn, mul(ph.rs, mul(ph.rs, ph.rs)));  // n . (x - y) / r^3
+            // (1 - i k r) exp(i k r) f = (cos + kr sin) f + i (sin - kr cos) f
+            const df gr = mul(add(ph.cs, mul(ph.phi, ph.sn)), f);
+            const df gi = mul(add(ph.sn, neg(mul(ph.phi, ph.cs))), f);
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const float4 uu = su[ll][j];
+                const df ur = {uu.x, uu.y}, ui = {uu.z, uu.w};
+                ar[j] = add(ar[j], add(mul(gr, ur), neg(mul(gi, ui))));
+                ai[j] = add(ai[j], add(mul(gr, ui), mul(gi, ur)));
+            }
+        }
+        __syncthreads();
+    }
+    if (tg < nq) {
 #pragma unroll
         for (int j = 0; j < R; ++j) v[tg + (int64_t)(c0 + j) * ldv] = make_double2(to_double(ar[j]), to_double(ai[j]));
     }
@@ -205,6 +292,23 @@ gyps_status run_far_df(Mesh *m, double k, const double4_32a *tgt, bool self, con
     case 4: dfl::far_df_kernel<4><<<grid, 128, 0, s>>>(tgt, m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, self, v, ldv); break;
     case 2: dfl::far_df_kernel<2><<<grid, 128, 0, s>>>(tgt, m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, self, v, ldv); break;
     default: dfl::far_df_kernel<1><<<grid, 128, 0, s>>>(tgt, m->d_pts64, u64, ldu, c0, m->nq, k, t_begin, t_end, self, v, ldv); break;
+    }
+    GYPS_CUDA(cudaGetLastError());
+    tf.done(1);
+    return GYPS_OK;
+}
+
+// v[t, c0 .. c0 + w) over all quadrature points: the double-float far part of the double layer.
+gyps_status run_far_dl_df(Mesh *m, double k, const double2 *u64, int64_t ldu, int c0, int w, double2 *v, int64_t ldv,
+                          cudaStream_t s)
+{
+    GYPS_TRY(dfl::ensure_table(m->device, s));
+    const unsigned grid = (unsigned)((m->nq + 127) / 128);
+    StageTimer tf(m, s, 1);
+    switch (w) {
+    case 4: dfl::far_dl_df_kernel<4><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ldu, c0, m->nq, k, v, ldv); break;
+    case 2: dfl::far_dl_df_kernel<2><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ldu, c0, m->nq, k, v, ldv); break;
+    default: dfl::far_dl_df_kernel<1><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ldu, c0, m->nq, k, v, ldv); break;
     }
     GYPS_CUDA(cudaGetLastError());
     tf.done(1);
