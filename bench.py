@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--impl", default="gyps", choices=["gyps", "reference"])
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "batch12_r64", "precond_ellipsoids", "sphere163842_k64_q3_r16",
-                            "assemble_sphere10242", "field_sphere10242_k16"])
+                            "assemble_sphere10242", "field_sphere10242_k16", "dl_sphere10242_k16_q7"])
     p.add_argument("--precond-meshes", type=int, default=125, help="training meshes (16 solves each)")
     p.add_argument("--precond-steps", type=int, default=3000)
     p.add_argument("--precond-test", type=int, default=8)
@@ -369,6 +369,15 @@ def run_gyps(args, rank, world, local_rank):
                  "refinements": rep.refinements, "check": "df64", "check_applies": rep.check_applies,
                  "true_residual_df64": float(rep.true_residual[0]),
                  "true_residual_fp64": float(torch.linalg.norm(r64) / torch.linalg.norm(f)), "status": rep.status}
+        # the same scattering problem in the combined-field (Brakhage-Werner) form
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, repb = g.gmres_solve(mesh, k, -f, tol=cfg["tol"], restart=200, maxit=2000, prec="fp32",
+                                check_prec="df64", max_refine=4, formulation="bw", eta=k)
+        torch.cuda.synchronize(dev)
+        solve["brakhage_werner"] = {"s": time.perf_counter() - t0, "eta": k, "iterations": repb.iterations,
+                                    "refinements": repb.refinements,
+                                    "true_residual_df64": float(repb.true_residual[0]), "status": repb.status}
         if args.solve_fp64:
             t0 = time.perf_counter()
             _, rep64 = g.gmres_solve(mesh, k, f, tol=cfg["tol"], restart=200, maxit=2000, prec="fp64",
@@ -602,6 +611,94 @@ def run_field(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dl(args):
+    """Workload dl_sphere10242_k16_q7: the Galerkin double layer K on the mesh of
+    sphere10242_k16_q7 (icosphere 20480 triangles, q = 7, k = 16).  One step =
+    one FP32 apply of K to one random column (persistent tile kernel, FP64
+    correction); once each: the double-float and FP64 applies and the
+    Brakhage-Werner operator 1/2 M + K - i k V; then GMRES to 1e-6 (FP32
+    operator, double-float checks) for the plane wave d = (1, 0, 0) in the
+    first-kind (V) and the combined-field (Brakhage-Werner) form, at k = 16 and
+    at k = 3 pi, where j_0(k) = 0 and V is singular on the unit sphere."""
+    import torch
+
+    import paper_1804_00995_gb300 as g
+    from paper_1804_00995_gb300 import build as gb
+    gb.build()
+    cfg = synth.WORKLOADS[WORKLOAD]
+    v, t = synth.icosphere(cfg["level"])
+    mesh = g.Mesh(v, t, cfg["q"])
+    k = cfg["k"]
+    x = torch.as_tensor(synth.random_complex(np.random.default_rng(1), mesh.nv, 1)).cuda()
+    for _ in range(args.warmup):
+        g.dl_apply(mesh, k, x, prec="fp32")
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(smi_id_of(torch.cuda.get_device_properties(0)))
+    mesh.profile(True)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        y32 = g.dl_apply(mesh, k, x, prec="fp32")
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = mesh.profile_read()
+    mesh.profile(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    far_ms = prof["far_ms"] / max(prof["far_launches"], 1)
+    once = {}
+    for name, fn in (("df64", lambda: g.dl_apply(mesh, k, x, prec="df64")),
+                     ("fp64", lambda: g.dl_apply(mesh, k, x, prec="fp64")),
+                     ("bw_fp32", lambda: g.bw_apply(mesh, k, k, x, prec="fp32"))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        y = fn()
+        torch.cuda.synchronize()
+        once[name] = {"ms": (time.perf_counter() - t0) * 1e3}
+        if name != "bw_fp32":
+            once[name]["y"] = y
+    y64 = once["fp64"].pop("y")
+    once["df64"]["rel_diff_vs_fp64"] = float(torch.linalg.norm(once["df64"].pop("y") - y64) / torch.linalg.norm(y64))
+    rel32 = float(torch.linalg.norm(y32 - y64) / torch.linalg.norm(y64))
+    solves = []
+    d = np.asarray(cfg["dirs"][0], dtype=np.float64)
+    for kk in (k, 3.0 * np.pi):
+        f = g.rhs_planewave(mesh, kk, [d])
+        for form in ("sl", "bw"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, rep = g.gmres_solve(mesh, kk, f if form == "sl" else -f, tol=cfg["tol"], restart=200, maxit=2000,
+                                   prec="fp32", check_prec="df64", max_refine=4, formulation=form, eta=kk)
+            torch.cuda.synchronize()
+            solves.append({"k": kk, "form": {"sl": "V", "bw": "1/2 M + K - i k V"}[form],
+                           "seconds": time.perf_counter() - t0, "iterations": rep.iterations,
+                           "true_residual_df64": float(rep.true_residual[0]), "status": rep.status})
+    pairs = float(mesh.nq) ** 2
+    achieved = pairs / (far_ms * 1e-3) / 1e9
+    props = torch.cuda.get_device_properties(0)
+    try:
+        peak_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
+    except Exception:
+        peak_mhz = clk.get("sm_max_mhz") or 2070.0
+    roof = sm_peak_pairs(props.multi_processor_count, peak_mhz) / 1e9
+    line = {
+        "metric": "GPairs/s double-layer apply (Gauss-point pairs per second)", "value": pairs / (ms * 1e-3) / 1e9,
+        "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "dl_sphere10242_k16_q7", "nv": mesh.nv, "nq": mesh.nq, "k": k, "nrhs": 1,
+                   "near": "fp64 closed-form grady[1/r] correction", "l2": "inputs 5 MB, not flushed (alu bound)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": roof, "unit": "GPairs/s", "frac": achieved / roof,
+                     "traffic": None, "kernel": "far_dl32_kernel<1,4,false>", "far_ms_per_launch": far_ms,
+                     "peak_basis": "3 MUFU results per pair at 16 per clock per SM, measured sm_max_mhz"},
+        "fp32_rel_diff_vs_fp64": rel32, "once": once, "solves": solves, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def solve_large(g, mesh, v, t, k, F, dirs, args):
     """Workload sphere163842_k64_q3_r16, --solve: (flexible) GMRES to 1e-6 on all
     16 plane waves, tensor-core working operator, double-float operator for the
@@ -752,6 +849,9 @@ def main():
         return
     if args.workload == "field_sphere10242_k16":
         run_field(args)
+        return
+    if args.workload == "dl_sphere10242_k16_q7":
+        run_dl(args)
         return
     if args.workload == "sphere163842_k64_q3_r16":
         run_large(args)
