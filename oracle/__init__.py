@@ -21,6 +21,9 @@ It follows the paper's formulation step by step:
   'grady[1/r]' correction in closed form (solid angle and edge logarithms).
 * The Brakhage-Werner combined operator ``1/2 M + K - i eta V`` (Brakhage and
   Werner 1965), assembled from the operators above, and its sphere closed form.
+* The adjoint double layer ``K'`` (normal at the test point) and the direct
+  combined-field operator ``1/2 M + K' - i eta V`` whose solution is the density of
+  the paper's sound-soft problem.
 
 Readings where the paper is silent (all listed with the design notes): the
 3-point rule is the interior (2/3, 1/6, 1/6) rule; "close enough" means sharing
@@ -79,6 +82,8 @@ def _load():
             lib.or_near_blocks.argtypes = [dp, i32p, ctypes.c_int, ctypes.c_int64, i64p, i64p, dp]
             lib.or_dl_kernel_matvec.argtypes = [ctypes.c_int64, dp, i64p, ctypes.c_int64, dp, dp,
                                                 ctypes.c_double, ctypes.c_int64, dp, dp]
+            lib.or_adl_kernel_matvec.argtypes = [ctypes.c_int64, dp, dp, i64p, ctypes.c_int64, dp,
+                                                 ctypes.c_double, ctypes.c_int64, dp, dp]
             lib.or_p1_dn_inv_r.argtypes = [dp, dp, dp, dp, dp]
             lib.or_p1_dn_inv_r.restype = None
             lib.or_dl_near_blocks.argtypes = [dp, i32p, ctypes.c_int, ctypes.c_int64, i64p, i64p, dp]
@@ -264,6 +269,28 @@ def dl_kernel_matvec(xt, tid, ys, nrm, u, k):
     return vflat.reshape((nt, nrhs), order="F")
 
 
+def adl_kernel_matvec(xt, nrm_t, tid, ys, u, k):
+    """v = H' u with H'_tl = -(1 - ikr) exp(ikr) n_t . (x_t - y_l) / r^3 (normal at the
+    target: n_x . grad_x exp(ikr)/r), H' = 0 where tid[t] == l."""
+    lib = _load()
+    xt = np.ascontiguousarray(xt, dtype=np.float64)
+    nrm_t = np.ascontiguousarray(nrm_t, dtype=np.float64)
+    ys = np.ascontiguousarray(ys, dtype=np.float64)
+    u = np.asarray(u, dtype=np.complex128)
+    if u.ndim == 1:
+        u = u[:, None]
+    nt, ns, nrhs = xt.shape[0], ys.shape[0], u.shape[1]
+    uflat = np.ascontiguousarray(u.ravel(order="F"))
+    vflat = np.zeros(nt * nrhs, dtype=np.complex128)
+    tidp = None
+    if tid is not None:
+        tid = np.ascontiguousarray(tid, dtype=np.int64)
+        tidp = _i64p(tid)
+    lib.or_adl_kernel_matvec(nt, _dp(xt), _dp(nrm_t), tidp, ns, _dp(ys), float(k), nrhs,
+                             _dp(uflat.view(np.float64)), _dp(vflat.view(np.float64)))
+    return vflat.reshape((nt, nrhs), order="F")
+
+
 def p1_dn_inv_r(x, p0, p1, p2):
     """int_T lambda_j(y) n . (x - y)/|x - y|^3 dy for j = 0, 1, 2 (closed form; 0 in the plane of T)."""
     lib = _load()
@@ -371,6 +398,34 @@ class Mesh:
         v = dl_kernel_matvec(self.x, np.arange(self.nq), self.x, self.point_normals(), u, k)
         y = (self.phi.T @ (self.w[:, None] * v)) / (4.0 * np.pi) + self.dl_near @ x
         return y[:, 0] if one else y
+
+    def adl_apply(self, k, x):
+        """Galerkin adjoint double layer K' x, K'_ij = (1/4pi) int int phi_i(x) n_x . grad_x
+        exp(ik|x-y|)/|x-y| phi_j(y): the kernel with the normal at the test point, and the
+        transpose of the double layer's correction (K' = K^T for the Galerkin matrices, G
+        being symmetric; the correction is taken as its discrete transpose)."""
+        x = np.asarray(x, dtype=np.complex128)
+        one = x.ndim == 1
+        if one:
+            x = x[:, None]
+        u = self.w[:, None] * (self.phi @ x)
+        v = adl_kernel_matvec(self.x, self.point_normals(), np.arange(self.nq), self.x, u, k)
+        y = (self.phi.T @ (self.w[:, None] * v)) / (4.0 * np.pi) + self.dl_near.T @ x
+        return y[:, 0] if one else y
+
+    def cfie_apply(self, k, eta, x):
+        """Direct combined-field operator (1/2 M + K' - i eta V) x for the sound-soft
+        problem: its solution is the normal derivative of the total field, the density
+        of the paper's first-kind system V lambda = F (Sec. 6.4)."""
+        x = np.asarray(x, dtype=np.complex128)
+        return 0.5 * (self.mass() @ x) + self.adl_apply(k, x) - 1j * eta * self.apply(k, x)
+
+    def rhs_planewave_cfie(self, k, eta, dirs):
+        """F_i = int phi_i (d/dn - i eta) exp(ik d.x) = int phi_i (ik d.n - i eta) exp(ik d.x)
+        by the domain's rule, n the outward unit normal of each triangle."""
+        dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+        p = np.exp(1j * k * (self.x @ dirs.T)) * (1j * k * (self.point_normals() @ dirs.T) - 1j * eta)
+        return np.asarray(self.phi.T @ (self.w[:, None] * p))
 
     def bw_apply(self, k, eta, x):
         """Brakhage-Werner combined operator (1/2 M + K - i eta V) x: the Galerkin

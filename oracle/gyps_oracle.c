@@ -337,6 +337,44 @@ int or_dl_kernel_matvec(int64_t nt, const double *xt, const int64_t *tid,
     return 0;
 }
 
+/* Adjoint double layer: the normal derivative at the target,
+ *   H'(x, y) = n_x . grad_x exp(ik|x-y|)/|x-y| = -(1 - i k r) exp(i k r) n_x . (x - y) / r^3,
+ * v[t, j] = sum_l H'(x_t, y_l) u[l, j]; nt_nrm: nt x 3 unit normals at the targets;
+ * the point paired with itself takes H' := 0. */
+int or_adl_kernel_matvec(int64_t nt, const double *xt, const double *nt_nrm, const int64_t *tid,
+                         int64_t ns, const double *ys, double k, int64_t nrhs, const double *u, double *v)
+{
+    #pragma omp parallel
+    {
+        double *acc = (double *)calloc((size_t)(2 * nrhs), sizeof(double));
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t t = 0; t < nt; ++t) {
+            for (int64_t j = 0; j < 2 * nrhs; ++j) acc[j] = 0.0;
+            const double *x = xt + 3 * t, *n = nt_nrm + 3 * t;
+            for (int64_t l = 0; l < ns; ++l) {
+                if (tid != NULL && tid[t] == l) continue;
+                const double *y = ys + 3 * l;
+                double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+                double r = sqrt(dot3(d, d));
+                double f = -dot3(n, d) / (r * r * r);
+                double c = cos(k * r), sn = sin(k * r);
+                double hr = (c + k * r * sn) * f, hi = (sn - k * r * c) * f;
+                for (int64_t j = 0; j < nrhs; ++j) {
+                    double ur = u[2 * (j * ns + l)], ui = u[2 * (j * ns + l) + 1];
+                    acc[2 * j] += hr * ur - hi * ui;
+                    acc[2 * j + 1] += hr * ui + hi * ur;
+                }
+            }
+            for (int64_t j = 0; j < nrhs; ++j) {
+                v[2 * (j * nt + t)] = acc[2 * j];
+                v[2 * (j * nt + t) + 1] = acc[2 * j + 1];
+            }
+        }
+        free(acc);
+    }
+    return 0;
+}
+
 /*
  * int_T lambda_j(y) n . (x - y) / |x - y|^3 dy over the flat triangle T =
  * (P0, P1, P2) with unit normal n = (P1 - P0) x (P2 - P0) / |.|, in closed
