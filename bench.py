@@ -618,8 +618,11 @@ def run_dl(args):
     correction); once each: the double-float and FP64 applies and the
     Brakhage-Werner operator 1/2 M + K - i k V; then GMRES to 1e-6 (FP32
     operator, double-float checks) for the plane wave d = (1, 0, 0) in the
-    first-kind (V) and the combined-field (Brakhage-Werner) form, at k = 16 and
-    at k = 3 pi, where j_0(k) = 0 and V is singular on the unit sphere."""
+    first-kind (V), the indirect combined-field (Brakhage-Werner) and the direct
+    combined-field (1/2 M + K' - i k V) form, at k = 16 and at k = 3 pi, where
+    j_0(k) = 0 and V is singular on the unit sphere; the first-kind and direct
+    solutions are both du/dn and are compared with the Mie series at 2048
+    vertices."""
     import torch
 
     import paper_1804_00995_gb300 as g
@@ -665,17 +668,25 @@ def run_dl(args):
     rel32 = float(torch.linalg.norm(y32 - y64) / torch.linalg.norm(y64))
     solves = []
     d = np.asarray(cfg["dirs"][0], dtype=np.float64)
+    samp = np.sort(np.random.default_rng(7).choice(mesh.nv, 2048, replace=False))
     for kk in (k, 3.0 * np.pi):
         f = g.rhs_planewave(mesh, kk, [d])
-        for form in ("sl", "bw"):
+        fc = g.rhs_planewave_cfie(mesh, kk, kk, [d])
+        mie = mie_density_sphere(kk, d, v[samp])
+        for form in ("sl", "bw", "cfie"):
+            rhs = {"sl": f, "bw": -f, "cfie": fc}[form]
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, rep = g.gmres_solve(mesh, kk, f if form == "sl" else -f, tol=cfg["tol"], restart=200, maxit=2000,
-                                   prec="fp32", check_prec="df64", max_refine=4, formulation=form, eta=kk)
+            x, rep = g.gmres_solve(mesh, kk, rhs, tol=cfg["tol"], restart=200, maxit=2000, prec="fp32",
+                                   check_prec="df64", max_refine=4, formulation=form, eta=kk)
             torch.cuda.synchronize()
-            solves.append({"k": kk, "form": {"sl": "V", "bw": "1/2 M + K - i k V"}[form],
-                           "seconds": time.perf_counter() - t0, "iterations": rep.iterations,
-                           "true_residual_df64": float(rep.true_residual[0]), "status": rep.status})
+            row = {"k": kk, "form": {"sl": "V", "bw": "1/2 M + K - i k V", "cfie": "1/2 M + K' - i k V"}[form],
+                   "seconds": time.perf_counter() - t0, "iterations": rep.iterations,
+                   "true_residual_df64": float(rep.true_residual[0]), "status": rep.status}
+            if form != "bw":  # both solve for du/dn, the Mie density
+                xs = x.cpu().numpy()[samp, 0]
+                row["mie_rel_error_2048_vertices"] = float(np.linalg.norm(xs - mie) / np.linalg.norm(mie))
+            solves.append(row)
     pairs = float(mesh.nq) ** 2
     achieved = pairs / (far_ms * 1e-3) / 1e9
     props = torch.cuda.get_device_properties(0)

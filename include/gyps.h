@@ -64,8 +64,10 @@ typedef enum {
 typedef enum {
     GYPS_FORM_SINGLE_LAYER = 0,   /* V X = F (first kind, Sec. 6.4); resonant where k^2 is an
                                      interior Dirichlet eigenvalue */
-    GYPS_FORM_BRAKHAGE_WERNER = 1 /* (1/2 M + K - i eta V) X = F: the density of u = (D - i eta S) phi,
+    GYPS_FORM_BRAKHAGE_WERNER = 1, /* (1/2 M + K - i eta V) X = F: the density of u = (D - i eta S) phi,
                                      uniquely solvable for every k when eta > 0 */
+    GYPS_FORM_DIRECT_CFIE = 2      /* (1/2 M + K' - i eta V) X = F: X = du/dn of the total field, the same
+                                     density as the first-kind system; F from gyps_rhs_planewave_cfie */
 } gyps_formulation;
 
 /* gyps_sl_apply flags */
@@ -212,6 +214,30 @@ gyps_status gyps_bw_apply(gyps_mesh_t mesh, double k, double eta, int nrhs, cons
                           void *Y, int64_t ldy, int prec, void *stream);
 
 /*
+ * Galerkin adjoint double layer (the normal derivative at the test point):
+ *     Y = K' X,  K'_ij = (1/4pi) int int phi_i(x) n_x . grad_x exp(ik|x-y|)/|x-y| phi_j(y),
+ * kernel -(1 - ikr) exp(ikr) n_x . (x - y) / r^3 between the Gauss points (n_x of
+ * the test triangle; pairs inside one triangle give 0), plus the transpose of the
+ * double layer's correction (K' = K^T for the Galerkin matrices, G being
+ * symmetric).  Arguments, precisions and errors as gyps_dl_apply.
+ */
+gyps_status gyps_adl_apply(gyps_mesh_t mesh, double k, int nrhs, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                           int prec, void *stream);
+
+/*
+ * Direct combined-field operator for sound-soft scattering: Green's
+ * representation u = u_inc - S (du/dn) of the total field gives on the surface
+ * V du/dn = u_inc and (1/2 + K') du/dn = du_inc/dn; the combination
+ *     Y = (1/2 M + K' - i eta V) X,   M = Phi^T W Phi (Eq. A=BWB),
+ * is invertible at every k > 0 for eta > 0, and its solution for the right-hand
+ * side of gyps_rhs_planewave_cfie is du/dn, the density of the first-kind
+ * system V lambda = F of Sec. 6.4.  Arguments, precisions and errors as
+ * gyps_bw_apply (K' takes the precision K would).
+ */
+gyps_status gyps_cfie_apply(gyps_mesh_t mesh, double k, double eta, int nrhs, const void *X, int64_t ldx,
+                            void *Y, int64_t ldy, int prec, void *stream);
+
+/*
  * Single-layer potential at points (the radiation operator of the listing in
  * Sec. 6.4: Sdom = integral(points, S2, Gxy, Vh)/(4 pi)
  * + regularize(points, S2, '[1/r]', Vh)/(4 pi)):
@@ -244,6 +270,16 @@ gyps_status gyps_sl_potential(gyps_mesh_t mesh, double k, int64_t npts, const do
 gyps_status gyps_rhs_planewave(gyps_mesh_t mesh, double k, int nrhs, const double *dirs,
                                void *F, int64_t ldf, void *stream);
 
+/*
+ * Right-hand sides of the direct combined-field system (gyps_cfie_apply):
+ *     F_ij = sum_k w_k phi_i(x_k) (d/dn - i eta) exp(i k d_j . x_k)
+ *          = sum_k w_k phi_i(x_k) i (k d_j . n - eta) exp(i k d_j . x_k),
+ * n the unit normal (P1 - P0) x (P2 - P0)/|.| of the triangle of x_k.  Arguments as
+ * gyps_rhs_planewave; eta must be finite.
+ */
+gyps_status gyps_rhs_planewave_cfie(gyps_mesh_t mesh, double k, double eta, int nrhs, const double *dirs,
+                                    void *F, int64_t ldf, void *stream);
+
 /* GMRES options (gyps_gmres_solve). */
 typedef struct {
     double tol;          /* relative residual ||F - A X|| / ||F|| per column (e.g. 1e-6) */
@@ -275,7 +311,8 @@ typedef struct {
  * Solves A X = F for nrhs columns by restarted
  * GMRES, A = V (Sec. 6.4, Eq. Singlelayerwf) or, with opts->formulation =
  * GYPS_FORM_BRAKHAGE_WERNER, A = 1/2 M + K - i opts->eta V (gyps_bw_apply;
- * pass -F for the sound-soft problem).  Arnoldi with classical Gram-Schmidt
+ * pass -F for the sound-soft problem), or with GYPS_FORM_DIRECT_CFIE,
+ * A = 1/2 M + K' - i opts->eta V (gyps_cfie_apply; F from gyps_rhs_planewave_cfie).  Arnoldi with classical Gram-Schmidt
  * applied twice, in FP64 on the device, Givens rotations on the host, one
  * Krylov space per column, the operator applied to all columns at once with
  * `opts->prec`.  After the
@@ -289,7 +326,7 @@ typedef struct {
  * cycle that does not halve the residual of any column, drops the
  * preconditioner for the rest of the solve (unpreconditioned GMRES from the
  * current iterate) and the report says so.  The check-precision residual judges the result either way.
- * The learned preconditioner models V: with the Brakhage-Werner operator it is
+ * The learned preconditioner models V: with the combined-field operators it is
  * UNSUPPORTED.
  * Returns NOT_CONVERGED (X = last iterate) when a column misses tol, NAN
  * when a non-finite value appears.

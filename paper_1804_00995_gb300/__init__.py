@@ -99,6 +99,12 @@ _SIGS = {
                           ctypes.c_void_p], ctypes.c_int),
     "gyps_dl_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "gyps_adl_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "gyps_cfie_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "gyps_rhs_planewave_cfie": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "gyps_bw_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "gyps_sl_potential": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
@@ -322,14 +328,33 @@ def dl_apply(mesh: Mesh, k: float, X, prec: str = "fp32", stream=None):
     return y[:, 0] if one else y
 
 
-def bw_apply(mesh: Mesh, k: float, eta: float, X, prec: str = "fp32", stream=None):
-    """Y = (1/2 M + K - i eta V) X, the Brakhage-Werner combined operator (gyps_bw_apply)."""
+def adl_apply(mesh: Mesh, k: float, X, prec: str = "fp32", stream=None):
+    """Y = K' X, the Galerkin adjoint double layer (gyps_adl_apply)."""
     one = (hasattr(X, "dim") and X.dim() == 1) or (not hasattr(X, "dim") and np.asarray(X).ndim == 1)
     x, nrhs, ldx = _colmajor(X, mesh.nv, "X")
     y = _empty_colmajor(mesh.nv, nrhs, x.device)
-    _check(load().gyps_bw_apply(mesh.handle, float(k), float(eta), nrhs, x.data_ptr(), ldx, y.data_ptr(),
-                                max(y.stride(1), mesh.nv) if nrhs > 1 else mesh.nv, PREC[prec], _stream(stream)))
+    _check(load().gyps_adl_apply(mesh.handle, float(k), nrhs, x.data_ptr(), ldx, y.data_ptr(),
+                                 max(y.stride(1), mesh.nv) if nrhs > 1 else mesh.nv, PREC[prec], _stream(stream)))
     return y[:, 0] if one else y
+
+
+def _combined(fn, mesh, k, eta, X, prec, stream):
+    one = (hasattr(X, "dim") and X.dim() == 1) or (not hasattr(X, "dim") and np.asarray(X).ndim == 1)
+    x, nrhs, ldx = _colmajor(X, mesh.nv, "X")
+    y = _empty_colmajor(mesh.nv, nrhs, x.device)
+    _check(fn(mesh.handle, float(k), float(eta), nrhs, x.data_ptr(), ldx, y.data_ptr(),
+              max(y.stride(1), mesh.nv) if nrhs > 1 else mesh.nv, PREC[prec], _stream(stream)))
+    return y[:, 0] if one else y
+
+
+def bw_apply(mesh: Mesh, k: float, eta: float, X, prec: str = "fp32", stream=None):
+    """Y = (1/2 M + K - i eta V) X, the Brakhage-Werner combined operator (gyps_bw_apply)."""
+    return _combined(load().gyps_bw_apply, mesh, k, eta, X, prec, stream)
+
+
+def cfie_apply(mesh: Mesh, k: float, eta: float, X, prec: str = "fp32", stream=None):
+    """Y = (1/2 M + K' - i eta V) X, the direct combined-field operator (gyps_cfie_apply)."""
+    return _combined(load().gyps_cfie_apply, mesh, k, eta, X, prec, stream)
 
 
 def sl_potential(mesh: Mesh, k: float, pts, X, prec: str = "fp32", stream=None):
@@ -360,6 +385,16 @@ def rhs_planewave(mesh: Mesh, k: float, dirs, device=None, stream=None):
     f = _empty_colmajor(mesh.nv, dirs.shape[0], dev)
     _check(load().gyps_rhs_planewave(mesh.handle, float(k), dirs.shape[0], dirs.ctypes.data, f.data_ptr(), mesh.nv,
                                      _stream(stream)))
+    return f
+
+
+def rhs_planewave_cfie(mesh: Mesh, k: float, eta: float, dirs, device=None, stream=None):
+    """F (nv, nrhs): F_ij = int phi_i (d/dn - i eta) exp(i k d_j . x) (gyps_rhs_planewave_cfie)."""
+    dirs = np.ascontiguousarray(np.atleast_2d(np.asarray(dirs, dtype=np.float64)))
+    dev = mesh.device if device is None else device
+    f = _empty_colmajor(mesh.nv, dirs.shape[0], dev)
+    _check(load().gyps_rhs_planewave_cfie(mesh.handle, float(k), float(eta), dirs.shape[0], dirs.ctypes.data,
+                                          f.data_ptr(), mesh.nv, _stream(stream)))
     return f
 
 
@@ -490,14 +525,15 @@ class GmresReport:
     status: str
 
 
-FORMULATION = {"sl": 0, "bw": 1}
+FORMULATION = {"sl": 0, "bw": 1, "cfie": 2}
 
 
 def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, maxit: int = 1000,
                 prec: str = "fp32", check_prec: str = "fp64", x0=None, max_refine: int = 3, raise_on_fail=False,
                 precond: "Precond" = None, stream=None, formulation: str = "sl", eta: float = None):
-    """Solves A X = F (gyps_gmres_solve), A = V ("sl") or 1/2 M + K - i eta V
-    ("bw", eta defaults to k, or 1 at k = 0).  Returns (X, GmresReport)."""
+    """Solves A X = F (gyps_gmres_solve), A = V ("sl"), 1/2 M + K - i eta V ("bw") or
+    1/2 M + K' - i eta V ("cfie"; F from rhs_planewave_cfie with the same eta); eta
+    defaults to k, or 1 at k = 0.  Returns (X, GmresReport)."""
     if eta is None:
         eta = float(k) if k > 0 else 1.0
     f, nrhs, ldf = _colmajor(F, mesh.nv, "F")

@@ -204,8 +204,12 @@ gyps_status assemble_device(Mesh *m, double k, int prec, double2 *V, int64_t ldv
 }
 
 // a7: F_ij = sum_{k in supp phi_i} w_k lambda_i(x_k) exp(i k d_j . x_k).
+// F_ij = sum_k w_k phi_i(x_k) g(x_k) with g = exp(ik d_j . x), or, for the direct
+// combined-field system (cfie), g = (d/dn - i eta) exp(ik d_j . x)
+// = i (k d_j . n - eta) exp(ik d_j . x), n the unit normal (P1 - P0) x (P2 - P0)/|.|.
 __global__ void rhs_kernel(const int32_t *v2t_ptr, const int32_t *v2t, const double4_32a *pts64, const Rule rule,
-                           int64_t nv, double k, const double *dirs, double2 *F, int64_t ldf)
+                           int64_t nv, double k, const double *dirs, double2 *F, int64_t ldf, const double *vtx,
+                           const int32_t *tri, int cfie, double eta)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
@@ -216,25 +220,40 @@ __global__ void rhs_kernel(const int32_t *v2t_ptr, const int32_t *v2t, const dou
         int32_t te = v2t[e];
         int64_t t = te / 3;
         int m = te - 3 * (int)t;
+        double a = 0.0;  // k d . n - eta
+        if (cfie) {
+            const double *p0 = vtx + 3 * tri[3 * t], *p1 = vtx + 3 * tri[3 * t + 1], *p2 = vtx + 3 * tri[3 * t + 2];
+            const double ux = p1[0] - p0[0], uy = p1[1] - p0[1], uz = p1[2] - p0[2];
+            const double vx = p2[0] - p0[0], vy = p2[1] - p0[1], vz = p2[2] - p0[2];
+            const double nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+            a = k * (dx * nx + dy * ny + dz * nz) / sqrt(nx * nx + ny * ny + nz * nz) - eta;
+        }
         for (int kq = 0; kq < rule.q; ++kq) {
             double4_32a x = pts64[t * rule.q + kq];
             double sn, cs;
             sincos(k * (dx * x.x + dy * x.y + dz * x.z), &sn, &cs);
             double c = x.w * rule.bary[3 * kq + m];
-            fr += c * cs;
-            fi += c * sn;
+            if (cfie) {  // i a (cs + i sn)
+                fr -= c * a * sn;
+                fi += c * a * cs;
+            } else {
+                fr += c * cs;
+                fi += c * sn;
+            }
         }
     }
     F[i + (int64_t)j * ldf] = make_double2(fr, fi);
 }
 
-gyps_status rhs_device(Mesh *m, double k, int nrhs, const double *dirs_host, double2 *F, int64_t ldf, cudaStream_t s)
+gyps_status rhs_device(Mesh *m, double k, int nrhs, const double *dirs_host, double2 *F, int64_t ldf, cudaStream_t s,
+                       bool cfie, double eta)
 {
     double *d_dirs = nullptr;
     GYPS_CUDA(cudaMallocAsync((void **)&d_dirs, (size_t)nrhs * 3 * sizeof(double), s));
     GYPS_CUDA(cudaMemcpyAsync(d_dirs, dirs_host, (size_t)nrhs * 3 * sizeof(double), cudaMemcpyHostToDevice, s));
     dim3 g((unsigned)((m->nv + 127) / 128), (unsigned)nrhs);
-    rhs_kernel<<<g, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_pts64, m->rule, m->nv, k, d_dirs, F, ldf);
+    rhs_kernel<<<g, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_pts64, m->rule, m->nv, k, d_dirs, F, ldf, m->d_vtx,
+                                 m->d_tri, cfie ? 1 : 0, eta);
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(d_dirs, s);
     GYPS_CUDA(e);
@@ -267,8 +286,8 @@ extern "C" gyps_status gyps_sl_assemble(gyps_mesh_t h, double k, int prec, void 
     return GYPS_OK;
 }
 
-extern "C" gyps_status gyps_rhs_planewave(gyps_mesh_t h, double k, int nrhs, const double *dirs, void *F, int64_t ldf,
-                                          void *stream)
+static gyps_status rhs_entry(gyps_mesh_t h, double k, int nrhs, const double *dirs, void *F, int64_t ldf, void *stream,
+                             bool cfie, double eta)
 {
     Mesh *m;
     GYPS_TRY(check_mesh(h, &m));
@@ -276,16 +295,29 @@ extern "C" gyps_status gyps_rhs_planewave(gyps_mesh_t h, double k, int nrhs, con
     if (nrhs < 1 || nrhs > 4096) return set_error(GYPS_ERR_INVALID, "nrhs must be in 1..4096");
     if (ldf < m->nv) return set_error(GYPS_ERR_INVALID, "ldf < nv");
     if (!std::isfinite(k) || k < 0.0) return set_error(GYPS_ERR_INVALID, "k must be finite and >= 0");
+    if (!std::isfinite(eta)) return set_error(GYPS_ERR_INVALID, "eta must be finite");
     for (int i = 0; i < 3 * nrhs; ++i)
         if (!std::isfinite(dirs[i])) return set_error(GYPS_ERR_INVALID, "non-finite direction");
     cudaStream_t s = (cudaStream_t)stream;
-    if (is_device_pointer(F)) return rhs_device(m, k, nrhs, dirs, (double2 *)F, ldf, s);
+    if (is_device_pointer(F)) return rhs_device(m, k, nrhs, dirs, (double2 *)F, ldf, s, cfie, eta);
     const size_t bytes = (size_t)m->nv * nrhs * sizeof(double2);
     GYPS_TRY(grow(m, &m->ws_stage, &m->ws_stage_bytes, bytes));
     double2 *fd = reinterpret_cast<double2 *>(m->ws_stage);
-    GYPS_TRY(rhs_device(m, k, nrhs, dirs, fd, m->nv, s));
+    GYPS_TRY(rhs_device(m, k, nrhs, dirs, fd, m->nv, s, cfie, eta));
     GYPS_CUDA(cudaMemcpy2DAsync(F, ldf * sizeof(double2), fd, m->nv * sizeof(double2), m->nv * sizeof(double2), nrhs,
                                 cudaMemcpyDeviceToHost, s));
     GYPS_CUDA(cudaStreamSynchronize(s));
     return GYPS_OK;
+}
+
+extern "C" gyps_status gyps_rhs_planewave(gyps_mesh_t h, double k, int nrhs, const double *dirs, void *F, int64_t ldf,
+                                          void *stream)
+{
+    return rhs_entry(h, k, nrhs, dirs, F, ldf, stream, false, 0.0);
+}
+
+extern "C" gyps_status gyps_rhs_planewave_cfie(gyps_mesh_t h, double k, double eta, int nrhs, const double *dirs,
+                                               void *F, int64_t ldf, void *stream)
+{
+    return rhs_entry(h, k, nrhs, dirs, F, ldf, stream, true, eta);
 }

@@ -85,7 +85,7 @@ __global__ void dl_near_blocks_kernel(const double *vtx, const int32_t *tri, con
 template <int R>
 __global__ void __launch_bounds__(128) far_dl64_kernel(const double4_32a *pts, const double4_32a *nrm, int q,
                                                        const double2 *u64, int64_t ldu, int c0, int64_t nq, double k,
-                                                       double2 *v, int64_t ldv)
+                                                       bool adj, double2 *v, int64_t ldv)
 {
     __shared__ double4_32a sp[128];
     __shared__ double4_32a sn[128];
@@ -93,6 +93,8 @@ __global__ void __launch_bounds__(128) far_dl64_kernel(const double4_32a *pts, c
     const int64_t tg = (int64_t)blockIdx.x * 128 + threadIdx.x;
     const int64_t tq0 = (tg / q) * q;
     const double4_32a x = pts[min(tg, nq - 1)];
+    const double4_32a tn = nrm[min(tg, nq - 1) / q];  // adjoint: the normal at the target
+    const double sg = adj ? -1.0 : 1.0;
     double ar[R], ai[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) ar[j] = ai[j] = 0.0;
@@ -108,11 +110,11 @@ __global__ void __launch_bounds__(128) far_dl64_kernel(const double4_32a *pts, c
         const int n = (int)min((int64_t)128, nq - s0);
         for (int ll = 0; ll < n; ++ll) {
             if ((uint64_t)(s0 + ll - tq0) < (uint64_t)q) continue;  // same flat triangle: n . (x - y) = 0
-            const double4_32a y = sp[ll], nn = sn[ll];
+            const double4_32a y = sp[ll], nn = adj ? tn : sn[ll];
             const double dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
             const double r2 = dx * dx + dy * dy + dz * dz;
             const double ri = rsqrt(r2);
-            const double f = (nn.x * dx + nn.y * dy + nn.z * dz) * ri * ri * ri;
+            const double f = sg * (nn.x * dx + nn.y * dy + nn.z * dz) * ri * ri * ri;
             const double kr = k * (r2 * ri);
             double s, c;
             sincos(kr, &s, &c);
@@ -166,6 +168,7 @@ __global__ void nrm_panel_kernel(const double4_32a *nrm, int q, int64_t nq, int6
 struct DlArgs {
     const float *pos_panel, *nrm_panel, *den_panel;
     const float4 *tgt;
+    const double4_32a *tri_nrm;  // adjoint: normals at the targets
     double2 *v;
     int64_t ldv, nq, n_src_tiles, n_tgt_tiles;
     int q;
@@ -173,13 +176,13 @@ struct DlArgs {
     int *err;
 };
 
-template <int R, int T>
+template <int R, int T, bool ADJ>
 struct DlCfg {
     static constexpr int NT = 128;
     static constexpr int TT = NT * T;
     static constexpr int STAGES = 3;
     static constexpr int POS_BYTES = kPosTileFloats * 4;
-    static constexpr int NRM_BYTES = kPosTileFloats * 4;
+    static constexpr int NRM_BYTES = ADJ ? 0 : kPosTileFloats * 4;  // the adjoint takes target normals
     static constexpr int DEN_BYTES = kSrcPairs * 6 * R * 4;
     static constexpr int STAGE_BYTES = POS_BYTES + NRM_BYTES + DEN_BYTES;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 64;
@@ -187,17 +190,19 @@ struct DlCfg {
 
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
-template <int R, int T, bool LAP, bool CHECK>
+template <int R, int T, bool LAP, bool CHECK, bool ADJ>
 __device__ __forceinline__ void dl_tile(const float *sp, const float2 (&tx)[T], const float2 (&ty)[T],
-                                        const float2 (&tz)[T], const int64_t (&tq0)[T], int64_t src0, int q,
+                                        const float2 (&tz)[T], const float2 (&tnx)[T], const float2 (&tny)[T],
+                                        const float2 (&tnz)[T], const int64_t (&tq0)[T], int64_t src0, int q,
                                         float ks, float2 (&are)[T][R], float2 (&aim)[T][R])
 {
+    constexpr int DEN = ADJ ? kPosTileFloats : 2 * kPosTileFloats;  // float offset of the densities
     const float4 *XY = reinterpret_cast<const float4 *>(sp);
     const float2 *Z = reinterpret_cast<const float2 *>(sp + 4 * kSrcPairs);
     const float4 *NXY = reinterpret_cast<const float4 *>(sp + kPosTileFloats);
     const float2 *NZ = reinterpret_cast<const float2 *>(sp + kPosTileFloats + 4 * kSrcPairs);
-    const float4 *U = reinterpret_cast<const float4 *>(sp + 2 * kPosTileFloats);
-    const float2 *N = reinterpret_cast<const float2 *>(sp + 2 * kPosTileFloats + 4 * kSrcPairs * R);
+    const float4 *U = reinterpret_cast<const float4 *>(sp + DEN);
+    const float2 *N = reinterpret_cast<const float2 *>(sp + DEN + 4 * kSrcPairs * R);
     const float2 ks2 = make_float2(ks, ks);
     const float2 magic = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23: round to integer
     const float2 nmagic = make_float2(-12582912.0f, -12582912.0f);
@@ -205,9 +210,15 @@ __device__ __forceinline__ void dl_tile(const float *sp, const float2 (&tx)[T], 
     const float2 m2pi = make_float2(-6.28318530717958647692f, -6.28318530717958647692f);
 #pragma unroll 2
     for (int p = 0; p < kSrcPairs; ++p) {
-        const float4 xy = XY[p], nxy = NXY[p];
+        const float4 xy = XY[p];
         float2 sx = make_float2(xy.x, xy.y), sy = make_float2(xy.z, xy.w), sz = Z[p];
-        const float2 nx = make_float2(nxy.x, nxy.y), ny = make_float2(nxy.z, nxy.w), nz = NZ[p];
+        float2 nx = make_float2(0.0f, 0.0f), ny = nx, nz = nx;
+        if (!ADJ) {
+            const float4 nxy = NXY[p];
+            nx = make_float2(nxy.x, nxy.y);
+            ny = make_float2(nxy.z, nxy.w);
+            nz = NZ[p];
+        }
         if (!LAP) {
             sx = __fmul2_rn(sx, ks2);
             sy = __fmul2_rn(sy, ks2);
@@ -230,9 +241,9 @@ __device__ __forceinline__ void dl_tile(const float *sp, const float2 (&tx)[T], 
             r2 = __ffma2_rn(dy, dy, r2);
             r2 = __ffma2_rn(dz, dz, r2);
             const float2 rs = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-            float2 dn = __fmul2_rn(nx, dx);
-            dn = __ffma2_rn(ny, dy, dn);
-            dn = __ffma2_rn(nz, dz, dn);
+            float2 dn = __fmul2_rn(ADJ ? tnx[t] : nx, dx);
+            dn = __ffma2_rn(ADJ ? tny[t] : ny, dy, dn);
+            dn = __ffma2_rn(ADJ ? tnz[t] : nz, dz, dn);
             float2 f = __fmul2_rn(__fmul2_rn(dn, rs), __fmul2_rn(rs, rs));  // n . (x - y) / r^3
             if (LAP) {
                 if (CHECK) {
@@ -270,10 +281,10 @@ __device__ __forceinline__ void dl_tile(const float *sp, const float2 (&tx)[T], 
     }
 }
 
-template <int R, int T, bool LAP>
-__global__ void __launch_bounds__(DlCfg<R, T>::NT) far_dl32_kernel(const DlArgs a)
+template <int R, int T, bool LAP, bool ADJ>
+__global__ void __launch_bounds__(DlCfg<R, T, ADJ>::NT) far_dl32_kernel(const DlArgs a)
 {
-    using C = DlCfg<R, T>;
+    using C = DlCfg<R, T, ADJ>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE_BYTES);
     const int tid_x = threadIdx.x;
@@ -293,19 +304,20 @@ __global__ void __launch_bounds__(DlCfg<R, T>::NT) far_dl32_kernel(const DlArgs 
         const uint32_t dst = smem_addr(smem + s * C::STAGE_BYTES);
         mbar_expect_tx(bar, C::STAGE_BYTES);
         bulk_g2s(dst, a.pos_panel + st * kPosTileFloats, C::POS_BYTES, bar);
-        bulk_g2s(dst + C::POS_BYTES, a.nrm_panel + st * kPosTileFloats, C::NRM_BYTES, bar);
+        if (!ADJ) bulk_g2s(dst + C::POS_BYTES, a.nrm_panel + st * kPosTileFloats, C::NRM_BYTES, bar);
         bulk_g2s(dst + C::POS_BYTES + C::NRM_BYTES, a.den_panel + st * den_tile_floats(R), C::DEN_BYTES, bar);
     };
     int64_t issued = beg;
     if (tid_x == 0)
         for (; issued < end && issued < beg + C::STAGES - 1; ++issued) issue(issued);
 
-    float2 tx[T], ty[T], tz[T];
+    float2 tx[T], ty[T], tz[T], tnx[T], tny[T], tnz[T];
     int64_t tid[T], tq0[T];
     float2 are[T][R], aim[T][R];
     float hre[T][R], lre[T][R], him[T][R], lim[T][R];
     int64_t cur_tt = -1;
-    const double scale = (double)a.ks * (double)a.ks;
+    // k^2 of the scaled coordinates; the adjoint kernel n_x . (y - x) carries the minus sign
+    const double scale = (ADJ ? -1.0 : 1.0) * (double)a.ks * (double)a.ks;
     auto flush = [&]() {
 #pragma unroll
         for (int t = 0; t < T; ++t) {
@@ -345,6 +357,12 @@ __global__ void __launch_bounds__(DlCfg<R, T>::NT) far_dl32_kernel(const DlArgs 
                 tx[t] = make_float2(p.x, p.x);
                 ty[t] = make_float2(p.y, p.y);
                 tz[t] = make_float2(p.z, p.z);
+                if (ADJ) {
+                    const double4_32a n = a.tri_nrm[min(g, a.nq - 1) / a.q];
+                    tnx[t] = make_float2((float)n.x, (float)n.x);
+                    tny[t] = make_float2((float)n.y, (float)n.y);
+                    tnz[t] = make_float2((float)n.z, (float)n.z);
+                }
 #pragma unroll
                 for (int j = 0; j < R; ++j) hre[t][j] = lre[t][j] = him[t][j] = lim[t][j] = 0.0f;
             }
@@ -362,9 +380,9 @@ __global__ void __launch_bounds__(DlCfg<R, T>::NT) far_dl32_kernel(const DlArgs 
             const int64_t src0 = st * kSrcTile;
             // a triangle's q <= 7 points may straddle a tile boundary
             if (tb - 8 < src0 + kSrcTile && src0 < te + 8)
-                dl_tile<R, T, LAP, true>(sp, tx, ty, tz, tq0, src0, a.q, a.ks, are, aim);
+                dl_tile<R, T, LAP, true, ADJ>(sp, tx, ty, tz, tnx, tny, tnz, tq0, src0, a.q, a.ks, are, aim);
             else
-                dl_tile<R, T, LAP, false>(sp, tx, ty, tz, tq0, src0, a.q, a.ks, are, aim);
+                dl_tile<R, T, LAP, false, ADJ>(sp, tx, ty, tz, tnx, tny, tnz, tq0, src0, a.q, a.ks, are, aim);
 #pragma unroll
             for (int t = 0; t < T; ++t)
 #pragma unroll
@@ -393,11 +411,11 @@ __global__ void __launch_bounds__(DlCfg<R, T>::NT) far_dl32_kernel(const DlArgs 
     flush();
 }
 
-template <int R, int T>
+template <int R, int T, bool ADJ>
 static gyps_status run_far_dl32(Mesh *m, double k, const double2 *X, int64_t ldx, int c0, double2 *v, int64_t ldv,
                                 cudaStream_t s)
 {
-    using C = DlCfg<R, T>;
+    using C = DlCfg<R, T, ADJ>;
     float *panel = reinterpret_cast<float *>(m->ws_den);
     GYPS_CUDA(launch_interp32(m, X, ldx, c0, R, panel, s));
     DlArgs a;
@@ -405,6 +423,7 @@ static gyps_status run_far_dl32(Mesh *m, double k, const double2 *X, int64_t ldx
     a.nrm_panel = m->d_nrm_panel;
     a.den_panel = panel;
     a.tgt = m->d_pts32;
+    a.tri_nrm = m->d_tri_nrm;
     a.v = v + (int64_t)c0 * ldv;
     a.ldv = ldv;
     a.nq = m->nq;
@@ -413,7 +432,7 @@ static gyps_status run_far_dl32(Mesh *m, double k, const double2 *X, int64_t ldx
     a.q = m->q;
     a.ks = k > 0.0 ? (float)k : 1.0f;
     a.err = m->d_err;
-    auto kern = k > 0.0 ? far_dl32_kernel<R, T, false> : far_dl32_kernel<R, T, true>;
+    auto kern = k > 0.0 ? far_dl32_kernel<R, T, false, ADJ> : far_dl32_kernel<R, T, true, ADJ>;
     GYPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     int occ = 0;
     GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::NT, C::SMEM));
@@ -427,11 +446,32 @@ static gyps_status run_far_dl32(Mesh *m, double k, const double2 *X, int64_t ldx
     return GYPS_OK;
 }
 
-// Normals and the double-layer correction values (CSR of C), once per mesh.
+// valT[e] = val at the transposed position of e: entry (i, j) of row i takes C_ji
+// (the pattern is symmetric: triangles sharing a vertex form a symmetric relation;
+// columns are sorted within each row).
+__global__ void csr_transpose_values_kernel(int64_t nv, const int32_t *rowptr, const int32_t *col, const double *val,
+                                            double *valT)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int32_t j = col[e];
+        int32_t lo = rowptr[j], hi = rowptr[j + 1];
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (col[mid] < (int32_t)i) lo = mid + 1;
+            else hi = mid;
+        }
+        valT[e] = (lo < rowptr[j + 1] && col[lo] == (int32_t)i) ? val[lo] : 0.0;
+    }
+}
+
+// Normals, the double-layer correction values on C's pattern and their transpose
+// (the adjoint's correction), and the FP32 normal panel; once per mesh.
 static gyps_status dl_prepare(Mesh *m, cudaStream_t s)
 {
     if (m->d_cdl_val) return GYPS_OK;
-    GYPS_CUDA(cudaMalloc((void **)&m->d_tri_nrm, (size_t)m->nt * sizeof(double4_32a)));
+    if (!m->d_tri_nrm) GYPS_CUDA(cudaMalloc((void **)&m->d_tri_nrm, (size_t)m->nt * sizeof(double4_32a)));
     tri_normal_kernel<<<(unsigned)((m->nt + 255) / 256), 256, 0, s>>>(m->d_vtx, m->d_tri, m->nt, m->d_tri_nrm);
     GYPS_CUDA(cudaGetLastError());
     double *blocks = nullptr;
@@ -451,23 +491,34 @@ static gyps_status dl_prepare(Mesh *m, cudaStream_t s)
         if (val) cudaFree(val);
         return cuda_error(e, "double-layer correction");
     }
-    e = cudaMalloc((void **)&m->d_nrm_panel, (size_t)m->n_src_tiles * kPosTileFloats * sizeof(float));
+    if (!m->d_nrm_panel)
+        e = cudaMalloc((void **)&m->d_nrm_panel, (size_t)m->n_src_tiles * kPosTileFloats * sizeof(float));
     if (e == cudaSuccess) {
         nrm_panel_kernel<<<(unsigned)((m->nq_pad + 255) / 256), 256, 0, s>>>(m->d_tri_nrm, m->q, m->nq, m->nq_pad,
                                                                            m->d_nrm_panel);
         e = cudaGetLastError();
     }
+    double *valT = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&valT, (size_t)m->c_nnz * sizeof(double));
+    if (e == cudaSuccess) {
+        csr_transpose_values_kernel<<<(unsigned)((m->nv + 127) / 128), 128, 0, s>>>(m->nv, m->d_c_rowptr, m->d_c_col,
+                                                                                   val, valT);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaFree(val);
-        return cuda_error(e, "double-layer normal panel");
+        if (valT) cudaFree(valT);
+        return cuda_error(e, "double-layer normal panel / adjoint correction");
     }
+    m->d_cdlT_val = valT;
     m->d_cdl_val = val;
     return GYPS_OK;
 }
 
+// Y = K X, or Y = K' X (adj: normal at the test point, transposed correction).
 gyps_status dl_apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
-                            int prec, cudaStream_t s)
+                            int prec, bool adj, cudaStream_t s)
 {
     GYPS_TRY(dl_prepare(m, s));
     const int64_t ld = m->nq;
@@ -483,13 +534,13 @@ gyps_status dl_apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64
         for (int c0 = 0; c0 < nrhs;) {
             const int w = nrhs - c0 >= 4 ? 4 : nrhs - c0 >= 2 ? 2 : 1;
             if (prec == GYPS_PREC_DF64) {
-                GYPS_TRY(run_far_dl_df(m, k, u64, ld, c0, w, v, ld, s));
+                GYPS_TRY(run_far_dl_df(m, k, adj, u64, ld, c0, w, v, ld, s));
                 c0 += w;
                 continue;
             }
-            if (w == 4) far_dl64_kernel<4><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, k, v, ld);
-            else if (w == 2) far_dl64_kernel<2><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, k, v, ld);
-            else far_dl64_kernel<1><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, k, v, ld);
+            if (w == 4) far_dl64_kernel<4><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, k, adj, v, ld);
+            else if (w == 2) far_dl64_kernel<2><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, k, adj, v, ld);
+            else far_dl64_kernel<1><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ld, c0, m->nq, k, adj, v, ld);
             GYPS_CUDA(cudaGetLastError());
             c0 += w;
         }
@@ -500,27 +551,41 @@ gyps_status dl_apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64
         for (int c0 = 0; c0 < nrhs;) {
             const int rem = nrhs - c0;
             const int w = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
-            switch (w) {
-            case 8: GYPS_TRY((run_far_dl32<8, 2>(m, k, X, ldx, c0, v, ld, s))); break;
-            case 4: GYPS_TRY((run_far_dl32<4, 2>(m, k, X, ldx, c0, v, ld, s))); break;
-            case 2: GYPS_TRY((run_far_dl32<2, 4>(m, k, X, ldx, c0, v, ld, s))); break;
-            default: GYPS_TRY((run_far_dl32<1, 4>(m, k, X, ldx, c0, v, ld, s))); break;
+            if (adj) {
+                switch (w) {
+                case 8: GYPS_TRY((run_far_dl32<8, 2, true>(m, k, X, ldx, c0, v, ld, s))); break;
+                case 4: GYPS_TRY((run_far_dl32<4, 2, true>(m, k, X, ldx, c0, v, ld, s))); break;
+                case 2: GYPS_TRY((run_far_dl32<2, 4, true>(m, k, X, ldx, c0, v, ld, s))); break;
+                default: GYPS_TRY((run_far_dl32<1, 4, true>(m, k, X, ldx, c0, v, ld, s))); break;
+                }
+            } else {
+                switch (w) {
+                case 8: GYPS_TRY((run_far_dl32<8, 2, false>(m, k, X, ldx, c0, v, ld, s))); break;
+                case 4: GYPS_TRY((run_far_dl32<4, 2, false>(m, k, X, ldx, c0, v, ld, s))); break;
+                case 2: GYPS_TRY((run_far_dl32<2, 4, false>(m, k, X, ldx, c0, v, ld, s))); break;
+                default: GYPS_TRY((run_far_dl32<1, 4, false>(m, k, X, ldx, c0, v, ld, s))); break;
+                }
             }
             c0 += w;
         }
     }
     dim3 gp((unsigned)((m->nv + 127) / 128), (unsigned)nrhs);
     project_kernel<<<gp, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_pts64, m->rule, m->nv, v, ld, m->d_c_rowptr,
-                                      m->d_c_col, m->d_cdl_val, X, ldx, Y, ldy, 1);
+                                      m->d_c_col, adj ? m->d_cdlT_val : m->d_cdl_val, X, ldx, Y, ldy, 1);
     GYPS_CUDA(cudaGetLastError());
     return GYPS_OK;
 }
 
-// Combined operator of the indirect Brakhage-Werner formulation: u = (D - i eta S) phi
-// outside the surface; the exterior trace (1/2 + K - i eta V) phi = -u_inc holds on it
-// (jump of the double-layer potential), in Galerkin form with the mass matrix
-// M = Phi^T W Phi of Eq. (A=BWB).  Y holds V X on entry and T holds K X:
-//   Y = 1/2 Phi^T W Phi X + T - i eta Y.
+// Combined-field operators, in Galerkin form with the mass matrix M = Phi^T W Phi
+// of Eq. (A=BWB):
+//   indirect (Brakhage-Werner): u = (D - i eta S) phi outside the surface, whose
+//     exterior trace (1/2 + K - i eta V) phi = -u_inc (jump of the double-layer
+//     potential);
+//   direct: the exterior normal derivative of Green's representation
+//     u = u_inc - S (du/dn) gives (1/2 + K') du/dn = du_inc/dn, its trace
+//     V du/dn = u_inc; the combination (1/2 + K' - i eta V) du/dn = (d/dn - i eta) u_inc
+//     has the density of the first-kind system as its solution.
+// Y holds V X on entry and T holds K X (or K' X):  Y = 1/2 Phi^T W Phi X + T - i eta Y.
 __global__ void bw_combine_kernel(const int32_t *v2t_ptr, const int32_t *v2t, const int32_t *tri,
                                   const double4_32a *pts64, const Rule rule, int64_t nv, const double2 *X,
                                   int64_t ldx, const double2 *T, int64_t ldt, double eta, double2 *Y, int64_t ldy)
@@ -548,15 +613,15 @@ __global__ void bw_combine_kernel(const int32_t *v2t_ptr, const int32_t *v2t, co
     Y[i + c * ldy] = make_double2(0.5 * mr + kx.x + eta * vx.y, 0.5 * mi + kx.y - eta * vx.x);
 }
 
-// Y = (1/2 M + K - i eta V) X.  V in prec; K in prec for FP64 and
-// double-float, in FP32 otherwise.
-gyps_status bw_apply_device(Mesh *m, double k, double eta, int nrhs, const double2 *X, int64_t ldx, double2 *Y,
-                            int64_t ldy, int prec, cudaStream_t s)
+// Y = (1/2 M + K - i eta V) X, or with K' (adj).  V in prec; K in prec for FP64
+// and double-float, in FP32 otherwise.
+gyps_status combined_apply_device(Mesh *m, double k, double eta, bool adj, int nrhs, const double2 *X, int64_t ldx,
+                                  double2 *Y, int64_t ldy, int prec, cudaStream_t s)
 {
     GYPS_TRY(grow(m, &m->ws_bw, &m->ws_bw_bytes, (size_t)m->nv * nrhs * sizeof(double2)));
     double2 *T = reinterpret_cast<double2 *>(m->ws_bw);
     const int kprec = (prec == GYPS_PREC_FP64 || prec == GYPS_PREC_DF64) ? prec : GYPS_PREC_FP32;
-    GYPS_TRY(dl_apply_device(m, k, nrhs, X, ldx, T, m->nv, kprec, s));
+    GYPS_TRY(dl_apply_device(m, k, nrhs, X, ldx, T, m->nv, kprec, adj, s));
     GYPS_TRY(apply_device(m, k, nrhs, X, ldx, Y, ldy, prec, 0, 0, m->nt, s));
     dim3 g((unsigned)((m->nv + 127) / 128), (unsigned)nrhs);
     bw_combine_kernel<<<g, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_tri, m->d_pts64, m->rule, m->nv, X, ldx, T, m->nv,
@@ -569,8 +634,8 @@ gyps_status bw_apply_device(Mesh *m, double k, double eta, int nrhs, const doubl
 
 using namespace gyps;
 
-extern "C" gyps_status gyps_dl_apply(gyps_mesh_t h, double k, int nrhs, const void *X, int64_t ldx, void *Y,
-                                     int64_t ldy, int prec, void *stream)
+static gyps_status dl_entry(gyps_mesh_t h, double k, int nrhs, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                            int prec, void *stream, bool adj)
 {
     Mesh *m;
     GYPS_TRY(check_mesh(h, &m));
@@ -601,7 +666,7 @@ extern "C" gyps_status gyps_dl_apply(gyps_mesh_t h, double k, int nrhs, const vo
     }
     double2 *yout = dy ? (double2 *)Y : ys;
     const int64_t lyout = dy ? ldy : m->nv;
-    GYPS_TRY(dl_apply_device(m, k, nrhs, xin, lxin, yout, lyout, prec, s));
+    GYPS_TRY(dl_apply_device(m, k, nrhs, xin, lxin, yout, lyout, prec, adj, s));
     if (!dy)
         GYPS_CUDA(cudaMemcpy2DAsync(Y, ldy * sizeof(double2), ys, m->nv * sizeof(double2), m->nv * sizeof(double2), nrhs,
                                     cudaMemcpyDeviceToHost, s));
@@ -609,8 +674,8 @@ extern "C" gyps_status gyps_dl_apply(gyps_mesh_t h, double k, int nrhs, const vo
     return check_err_word(m, s);
 }
 
-extern "C" gyps_status gyps_bw_apply(gyps_mesh_t h, double k, double eta, int nrhs, const void *X, int64_t ldx,
-                                     void *Y, int64_t ldy, int prec, void *stream)
+static gyps_status combined_entry(gyps_mesh_t h, double k, double eta, int nrhs, const void *X, int64_t ldx, void *Y,
+                                  int64_t ldy, int prec, void *stream, bool adj)
 {
     Mesh *m;
     GYPS_TRY(check_mesh(h, &m));
@@ -646,10 +711,34 @@ extern "C" gyps_status gyps_bw_apply(gyps_mesh_t h, double k, double eta, int nr
     }
     double2 *yout = dy ? (double2 *)Y : ys;
     const int64_t lyout = dy ? ldy : m->nv;
-    GYPS_TRY(bw_apply_device(m, k, eta, nrhs, xin, lxin, yout, lyout, prec, s));
+    GYPS_TRY(combined_apply_device(m, k, eta, adj, nrhs, xin, lxin, yout, lyout, prec, s));
     if (!dy)
         GYPS_CUDA(cudaMemcpy2DAsync(Y, ldy * sizeof(double2), ys, m->nv * sizeof(double2), m->nv * sizeof(double2), nrhs,
                                     cudaMemcpyDeviceToHost, s));
     GYPS_CUDA(cudaStreamSynchronize(s));
     return check_err_word(m, s);
+}
+
+extern "C" gyps_status gyps_dl_apply(gyps_mesh_t h, double k, int nrhs, const void *X, int64_t ldx, void *Y,
+                                     int64_t ldy, int prec, void *stream)
+{
+    return dl_entry(h, k, nrhs, X, ldx, Y, ldy, prec, stream, false);
+}
+
+extern "C" gyps_status gyps_adl_apply(gyps_mesh_t h, double k, int nrhs, const void *X, int64_t ldx, void *Y,
+                                      int64_t ldy, int prec, void *stream)
+{
+    return dl_entry(h, k, nrhs, X, ldx, Y, ldy, prec, stream, true);
+}
+
+extern "C" gyps_status gyps_bw_apply(gyps_mesh_t h, double k, double eta, int nrhs, const void *X, int64_t ldx,
+                                     void *Y, int64_t ldy, int prec, void *stream)
+{
+    return combined_entry(h, k, eta, nrhs, X, ldx, Y, ldy, prec, stream, false);
+}
+
+extern "C" gyps_status gyps_cfie_apply(gyps_mesh_t h, double k, double eta, int nrhs, const void *X, int64_t ldx,
+                                       void *Y, int64_t ldy, int prec, void *stream)
+{
+    return combined_entry(h, k, eta, nrhs, X, ldx, Y, ldy, prec, stream, true);
 }

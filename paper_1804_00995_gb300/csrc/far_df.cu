@@ -193,10 +193,11 @@ __global__ void __launch_bounds__(128) far_df_kernel(const double4_32a *tgt, con
 // The double layer's kernel H = (1 - i k r) exp(i k r) n_y . (x - y) / r^3 in
 // double-float, the quadrature points as targets and sources; pairs inside one
 // triangle (its q consecutive points, the point itself included) give 0.
+// adj: the adjoint's kernel -(1 - i k r) exp(i k r) n_x . (x - y) / r^3 (normal at the target).
 template <int R>
 __global__ void __launch_bounds__(128) far_dl_df_kernel(const double4_32a *pts, const double4_32a *nrm, int q,
                                                         const double2 *u64, int64_t ldu, int c0, int64_t nq, double k,
-                                                        double2 *v, int64_t ldv)
+                                                        bool adj, double2 *v, int64_t ldv)
 {
     __shared__ float4 tab[kTab];
     __shared__ float4 sxy[128];     // (x hi, x lo, y hi, y lo)
@@ -210,6 +211,9 @@ __global__ void __launch_bounds__(128) far_dl_df_kernel(const double4_32a *pts, 
     const double4_32a x = pts[min(tg, nq - 1)];
     const df tx = from_double(x.x), ty = from_double(x.y), tz = from_double(x.z);
     const df kd = from_double(k);
+    const double4_32a tn = nrm[min(tg, nq - 1) / q];
+    const double sg = adj ? -1.0 : 1.0;  // the sign of the adjoint's kernel rides on its normal
+    const df tnx = from_double(sg * tn.x), tny = from_double(sg * tn.y), tnz = from_double(sg * tn.z);
     df ar[R], ai[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) ar[j] = ai[j] = df{0.0f, 0.0f};
@@ -242,7 +246,8 @@ __global__ void __launch_bounds__(128) far_dl_df_kernel(const double4_32a *pts, 
             const Phase ph = phase_of(r2, kd, tab);
             const float4 nxy = snxy[ll];
             const float2 nz = snz[ll];
-            const df dn = add(add(mul(df{nxy.x, nxy.y}, dx), mul(df{nxy.z, nxy.w}, dy)), mul(df{nz.x, nz.y}, dz));
+            const df nnx = adj ? tnx : df{nxy.x, nxy.y}, nny = adj ? tny : df{nxy.z, nxy.w}, nnz = adj ? tnz : df{nz.x, nz.y};
+            const df dn = add(add(mul(nnx, dx), mul(nny, dy)), mul(nnz, dz));
             const df f = mul(dn, mul(ph.rs, mul(ph.rs, ph.rs)));  // n . (x - y) / r^3
             // (1 - i k r) exp(i k r) f = (cos + kr sin) f + i (sin - kr cos) f
             const df gr = mul(add(ph.cs, mul(ph.phi, ph.sn)), f);
@@ -299,16 +304,16 @@ gyps_status run_far_df(Mesh *m, double k, const double4_32a *tgt, bool self, con
 }
 
 // v[t, c0 .. c0 + w) over all quadrature points: the double-float far part of the double layer.
-gyps_status run_far_dl_df(Mesh *m, double k, const double2 *u64, int64_t ldu, int c0, int w, double2 *v, int64_t ldv,
-                          cudaStream_t s)
+gyps_status run_far_dl_df(Mesh *m, double k, bool adj, const double2 *u64, int64_t ldu, int c0, int w, double2 *v,
+                          int64_t ldv, cudaStream_t s)
 {
     GYPS_TRY(dfl::ensure_table(m->device, s));
     const unsigned grid = (unsigned)((m->nq + 127) / 128);
     StageTimer tf(m, s, 1);
     switch (w) {
-    case 4: dfl::far_dl_df_kernel<4><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ldu, c0, m->nq, k, v, ldv); break;
-    case 2: dfl::far_dl_df_kernel<2><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ldu, c0, m->nq, k, v, ldv); break;
-    default: dfl::far_dl_df_kernel<1><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ldu, c0, m->nq, k, v, ldv); break;
+    case 4: dfl::far_dl_df_kernel<4><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ldu, c0, m->nq, k, adj, v, ldv); break;
+    case 2: dfl::far_dl_df_kernel<2><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ldu, c0, m->nq, k, adj, v, ldv); break;
+    default: dfl::far_dl_df_kernel<1><<<grid, 128, 0, s>>>(m->d_pts64, m->d_tri_nrm, m->q, u64, ldu, c0, m->nq, k, adj, v, ldv); break;
     }
     GYPS_CUDA(cudaGetLastError());
     tf.done(1);

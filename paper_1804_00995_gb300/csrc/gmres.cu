@@ -185,11 +185,13 @@ struct Solver {
     int form = GYPS_FORM_SINGLE_LAYER;
     double eta = 0.0;
 
-    // Y = A X for the system's operator A: V (first kind), or 1/2 M + K - i eta V
-    // (Brakhage-Werner); X and Y are nv x nrhs.
+    // Y = A X for the system's operator A: V (first kind), 1/2 M + K - i eta V
+    // (Brakhage-Werner) or 1/2 M + K' - i eta V (direct combined field); X and Y
+    // are nv x nrhs.
     gyps_status op(const double2 *X, int64_t ldx, double2 *Y, int prec)
     {
-        if (form == GYPS_FORM_BRAKHAGE_WERNER) return bw_apply_device(m, k, eta, nrhs, X, ldx, Y, nv, prec, s);
+        if (form == GYPS_FORM_BRAKHAGE_WERNER || form == GYPS_FORM_DIRECT_CFIE)
+            return combined_apply_device(m, k, eta, form == GYPS_FORM_DIRECT_CFIE, nrhs, X, ldx, Y, nv, prec, s);
         return apply_device(m, k, nrhs, X, ldx, Y, nv, prec, 0, 0, m->nt, s);
     }
 
@@ -527,9 +529,10 @@ extern "C" gyps_status gyps_gmres_solve(gyps_mesh_t h, double k, int nrhs, const
     const gyps_gmres_opts &o = *opts;
     if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 4096 || o.maxit < 1 || o.max_refine < 0)
         return set_error(GYPS_ERR_INVALID, "bad GMRES options");
-    if (o.formulation != GYPS_FORM_SINGLE_LAYER && o.formulation != GYPS_FORM_BRAKHAGE_WERNER)
+    if (o.formulation != GYPS_FORM_SINGLE_LAYER && o.formulation != GYPS_FORM_BRAKHAGE_WERNER &&
+        o.formulation != GYPS_FORM_DIRECT_CFIE)
         return set_error(GYPS_ERR_INVALID, "unknown formulation");
-    if (o.formulation == GYPS_FORM_BRAKHAGE_WERNER) {
+    if (o.formulation != GYPS_FORM_SINGLE_LAYER) {
         if (!std::isfinite(o.eta)) return set_error(GYPS_ERR_INVALID, "eta must be finite");
         if (o.precond) return set_error(GYPS_ERR_UNSUPPORTED, "the learned preconditioner models the single layer");
         if (o.prec == GYPS_PREC_TC_BF16X3 && nrhs < 16)

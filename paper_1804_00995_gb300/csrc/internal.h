@@ -96,6 +96,7 @@ struct Mesh {
     float4 *d_tri_cen32 = nullptr;                        // the same in FP32, radius widened (candidate test)
     double4_32a *d_tri_nrm = nullptr;                     // double layer: unit normal per triangle
     double *d_cdl_val = nullptr;                          // double layer: correction values on C's pattern
+    double *d_cdlT_val = nullptr;                         // adjoint double layer: the transposed values
     float *d_nrm_panel = nullptr;                         // double layer: FP32 normals, position-panel layout
     float pad = 0.0f;                                     // distance of padding points
     // mesh graph for the learned preconditioner (built on first use)
@@ -157,8 +158,8 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
                          int prec, uint32_t flags, int64_t tri_begin, int64_t tri_end, cudaStream_t s);
 gyps_status run_far_df(Mesh *m, double k, const double4_32a *tgt, bool self, const double2 *u64, int64_t ldu, int c0,
                        int w, double2 *v, int64_t ldv, int64_t t_begin, int64_t t_end, cudaStream_t s);
-gyps_status run_far_dl_df(Mesh *m, double k, const double2 *u64, int64_t ldu, int c0, int w, double2 *v, int64_t ldv,
-                          cudaStream_t s);
+gyps_status run_far_dl_df(Mesh *m, double k, bool adj, const double2 *u64, int64_t ldu, int c0, int w, double2 *v,
+                          int64_t ldv, cudaStream_t s);
 // Far part of the potential at npts points (tgt32 / tgt64: the points): v[i, c] = sum_l G(x_i, y_l) u_l,c
 // with u = W Phi X, no self pairs; prec FP32 | FP64 | DF64; v: npts x nrhs, ld ldv, overwritten.
 gyps_status far_points(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, const float4 *tgt32,
@@ -171,16 +172,18 @@ cudaError_t launch_near_spmv(const Mesh &m, int nrhs, const double2 *X, int64_t 
 // a2 in FP32: the density panel of columns c0 .. c0+w-1 (w = 1, 2, 4 or 8)
 cudaError_t launch_interp32(const Mesh *m, const double2 *X, int64_t ldx, int c0, int w, float *panel, cudaStream_t s);
 
-// Double layer Y = K X and the combined operator Y = (1/2 M + K - i eta V) X (device pointers)
+// Double layer Y = K X (adj: K' X) and the combined operators Y = (1/2 M + K - i eta V) X,
+// (1/2 M + K' - i eta V) X (device pointers)
 gyps_status dl_apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
-                            int prec, cudaStream_t s);
-gyps_status bw_apply_device(Mesh *m, double k, double eta, int nrhs, const double2 *X, int64_t ldx, double2 *Y,
-                            int64_t ldy, int prec, cudaStream_t s);
+                            int prec, bool adj, cudaStream_t s);
+gyps_status combined_apply_device(Mesh *m, double k, double eta, bool adj, int nrhs, const double2 *X, int64_t ldx,
+                                  double2 *Y, int64_t ldy, int prec, cudaStream_t s);
 
 // a6, a7
 gyps_status assemble_device(Mesh *m, double k, int prec, double2 *V, int64_t ldv, cudaStream_t s);
+// F = int phi (exp(ik d.x)), or with cfie: int phi (d/dn - i eta) exp(ik d.x)
 gyps_status rhs_device(Mesh *m, double k, int nrhs, const double *dirs_host, double2 *F, int64_t ldf,
-                       cudaStream_t s);
+                       cudaStream_t s, bool cfie = false, double eta = 0.0);
 
 // a11: learned preconditioner Z = M(R) (device pointers)
 gyps_status precond_apply_device(gyps_precond_t p, Mesh *m, double k, int nrhs, const double2 *R, int64_t ldr,
