@@ -24,6 +24,10 @@ It follows the paper's formulation step by step:
 * The adjoint double layer ``K'`` (normal at the test point) and the direct
   combined-field operator ``1/2 M + K' - i eta V`` whose solution is the density of
   the paper's sound-soft problem.
+* The EFIE of the electromagnetic listing after Sec. 6.4 with RWG functions:
+  the vector and divergence parts of ``T`` through the same kernel, their
+  '[1/r]' corrections from the P1 closed form, and the Mie amplitudes of the
+  perfectly conducting sphere.
 
 Readings where the paper is silent (all listed with the design notes): the
 3-point rule is the interior (2/3, 1/6, 1/6) rule; "close enough" means sharing
@@ -85,6 +89,7 @@ def _load():
             lib.or_adl_kernel_matvec.argtypes = [ctypes.c_int64, dp, dp, i64p, ctypes.c_int64, dp,
                                                  ctypes.c_double, ctypes.c_int64, dp, dp]
             lib.or_p1_dn_inv_r.argtypes = [dp, dp, dp, dp, dp]
+            lib.or_efie_near_blocks.argtypes = [dp, i32p, dp, ctypes.c_int, ctypes.c_int64, i64p, i64p, dp, dp]
             lib.or_p1_dn_inv_r.restype = None
             lib.or_dl_near_blocks.argtypes = [dp, i32p, ctypes.c_int, ctypes.c_int64, i64p, i64p, dp]
             lib.or_num_threads.restype = ctypes.c_int
@@ -489,6 +494,218 @@ class Mesh:
         dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
         p = np.exp(1j * k * (self.x @ dirs.T))               # (Nq, nd)
         return np.asarray(self.phi.T @ (self.w[:, None] * p))
+
+
+# --------------------------------------------------------------------------
+# EFIE with RWG functions (the electromagnetic listing after Sec. 6.4):
+#   T = ik/(4pi) int int phi_m . phi_n G - i/(4pi k) int int div phi_m div phi_n G
+#     + the same two terms with the '[1/r]' regularisation (Sec. 5.2)
+# --------------------------------------------------------------------------
+
+def rwg_topology(tri, nv):
+    """RWG functions of a closed, consistently oriented mesh, one per edge.
+
+    Edges are the vertex pairs (a < b) in lexicographic order.  In triangle
+    t = (v0, v1, v2) the local edge j runs v_{j+1} -> v_{j+2}, opposite v_j; t is
+    the edge's plus triangle (sign +1) where the edge runs a -> b, its minus
+    triangle (sign -1) where it runs b -> a.  Returns edges (nE, 2), tedge (nt, 3)
+    edge ids and tsign (nt, 3)."""
+    tri = np.asarray(tri, dtype=np.int64)
+    a, b = tri[:, [1, 2, 0]], tri[:, [2, 0, 1]]
+    key = np.minimum(a, b) * nv + np.maximum(a, b)
+    uniq, inv, counts = np.unique(key.reshape(-1), return_inverse=True, return_counts=True)
+    if np.any(counts != 2):
+        raise ValueError("RWG functions need a closed mesh (every edge in two triangles)")
+    tsign = np.where(a < b, 1.0, -1.0)
+    plus = np.zeros(uniq.shape[0])
+    np.add.at(plus, inv, tsign.reshape(-1))
+    if np.any(plus != 0.0):
+        raise ValueError("inconsistent orientation: an edge runs the same way in both triangles")
+    edges = np.stack([uniq // nv, uniq % nv], axis=1)
+    return edges, inv.reshape(tri.shape), tsign
+
+
+def rwg_eval(P, j, s, y):
+    """The RWG function of local edge j of the triangle P (3 x 3) with sign s at the
+    points y (n, 3): s l_j / (2 A) (y - P_j), and its divergence s l_j / A."""
+    A = 0.5 * np.linalg.norm(np.cross(P[1] - P[0], P[2] - P[0]))
+    l = np.linalg.norm(P[(j + 2) % 3] - P[(j + 1) % 3])
+    return s * l / (2.0 * A) * (np.atleast_2d(y) - P[j]), s * l / A
+
+
+def rwg_basis(vtx, tri, q):
+    """Phi_c (Nq, nE), c = 0, 1, 2: the vector components of the RWG functions at
+    the Gauss points, and Dv (Nq, nE) their divergence; 3 nonzeros per row."""
+    vtx = np.asarray(vtx, dtype=np.float64)
+    tri = np.asarray(tri, dtype=np.int64)
+    nt = tri.shape[0]
+    edges, tedge, tsign = rwg_topology(tri, vtx.shape[0])
+    x, _ = quad_points(vtx, tri, q)
+    rows, cols, vals, dvals = [], [], [[], [], []], []
+    for t in range(nt):
+        P = vtx[tri[t]]
+        pts = x[t * q:(t + 1) * q]
+        for j in range(3):
+            f, d = rwg_eval(P, j, tsign[t, j], pts)
+            rows.append(np.arange(t * q, (t + 1) * q))
+            cols.append(np.full(q, tedge[t, j]))
+            for c in range(3):
+                vals[c].append(f[:, c])
+            dvals.append(np.full(q, d))
+    rows, cols = np.concatenate(rows), np.concatenate(cols)
+    ne = edges.shape[0]
+    phi = [sp.csr_matrix((np.concatenate(vals[c]), (rows, cols)), shape=(nt * q, ne)) for c in range(3)]
+    dv = sp.csr_matrix((np.concatenate(dvals), (rows, cols)), shape=(nt * q, ne))
+    return phi, dv
+
+
+def efie_near_matrices(vtx, tri, q):
+    """CA, CB (nE, nE) real: on every ordered pair (a, b) of triangles sharing a
+    vertex, for each Gauss point x_k of a, the analytic int_b f / |x_k - y| minus the
+    Gauss sum over b's points (the point itself left out), paired with w_k times the
+    test function of a:  CA with f = phi_j^b (dotted with phi_i^a(x_k)), CB with
+    f = div phi_j^b (times div phi_i^a).  The analytic integrals follow from the P1
+    ones: phi_j = s l_j / (2A) sum_m lambda_m (P_m - P_j) on b (C, or_efie_near_blocks)."""
+    lib = _load()
+    vtx = np.ascontiguousarray(vtx, dtype=np.float64)
+    tri32 = np.ascontiguousarray(tri, dtype=np.int32)
+    nv = vtx.shape[0]
+    edges, tedge, tsign = rwg_topology(tri32, nv)
+    tsign = np.ascontiguousarray(tsign, dtype=np.float64)
+    pa, pb = near_pairs(tri32, nv)
+    pa = np.ascontiguousarray(pa, dtype=np.int64)
+    pb = np.ascontiguousarray(pb, dtype=np.int64)
+    ba = np.zeros((pa.shape[0], 3, 3))
+    bb = np.zeros((pa.shape[0], 3, 3))
+    if lib.or_efie_near_blocks(_dp(vtx), _i32p(tri32), _dp(tsign), int(q), pa.shape[0], _i64p(pa), _i64p(pb),
+                               _dp(ba), _dp(bb)) != 0:
+        raise ValueError("bad quadrature order")
+    rows = np.repeat(tedge[pa], 3, axis=1).reshape(-1)
+    cols = np.tile(tedge[pb], (1, 3)).reshape(-1)
+    ne = edges.shape[0]
+    CA = sp.coo_matrix((ba.reshape(-1), (rows, cols)), shape=(ne, ne)).tocsr()
+    CB = sp.coo_matrix((bb.reshape(-1), (rows, cols)), shape=(ne, ne)).tocsr()
+    CA.sum_duplicates()
+    CB.sum_duplicates()
+    return CA, CB
+
+
+def efie_near_matrices_py(vtx, tri, q):
+    """The same matrices from a direct loop over pairs and Gauss points in numpy
+    (slow; a cross-check of the C form on small meshes)."""
+    vtx = np.asarray(vtx, dtype=np.float64)
+    tri = np.asarray(tri, dtype=np.int64)
+    nv = vtx.shape[0]
+    edges, tedge, tsign = rwg_topology(tri, nv)
+    x, w = quad_points(vtx, tri, q)
+    pa, pb = near_pairs(tri, nv)
+    ne = edges.shape[0]
+    ra, rb, va, vb = [], [], [], []
+    for a, b in zip(pa, pb):
+        Pa, Pb = vtx[tri[a]], vtx[tri[b]]
+        xa, wa = x[a * q:(a + 1) * q], w[a * q:(a + 1) * q]
+        yb, wb = x[b * q:(b + 1) * q], w[b * q:(b + 1) * q]
+        Ab = 0.5 * np.linalg.norm(np.cross(Pb[1] - Pb[0], Pb[2] - Pb[0]))
+        for kk in range(q):
+            I = p1_inv_r(xa[kk], Pb[0], Pb[1], Pb[2])          # int_b lambda_m / R
+            r = np.linalg.norm(yb - xa[kk], axis=1)
+            inv = np.zeros(q)
+            mask = r > 0.0
+            if a == b:
+                mask[kk] = False                                  # the point itself
+            inv[mask] = wb[mask] / r[mask]
+            for jb in range(3):
+                sj = tsign[b, jb]
+                lj = np.linalg.norm(Pb[(jb + 2) % 3] - Pb[(jb + 1) % 3])
+                vec_an = sj * lj / (2.0 * Ab) * (I[:, None] * (Pb - Pb[jb])).sum(axis=0)
+                div_an = sj * lj / Ab * I.sum()
+                fb, db = rwg_eval(Pb, jb, sj, yb)
+                vec_g = (inv[:, None] * fb).sum(axis=0)
+                div_g = db * inv.sum()
+                for ia in range(3):
+                    fa, da = rwg_eval(Pa, ia, tsign[a, ia], xa[kk])
+                    ra.append(tedge[a, ia])
+                    rb.append(tedge[b, jb])
+                    va.append(wa[kk] * float(fa[0] @ (vec_an - vec_g)))
+                    vb.append(wa[kk] * da * (div_an - div_g))
+    CA = sp.coo_matrix((va, (ra, rb)), shape=(ne, ne)).tocsr()
+    CB = sp.coo_matrix((vb, (ra, rb)), shape=(ne, ne)).tocsr()
+    CA.sum_duplicates()
+    CB.sum_duplicates()
+    return CA, CB
+
+
+class EfieMesh(Mesh):
+    """The mesh with the RWG space ``fem(mesh, 'RWG')`` on ``dom(mesh, q)``."""
+
+    def __init__(self, vtx, tri, q):
+        super().__init__(vtx, tri, q)
+        self.edges, self.tedge, self.tsign = rwg_topology(self.tri, self.nv)
+        self.ne = self.edges.shape[0]
+        self.rwg, self.div = rwg_basis(self.vtx, self.tri, self.q)
+        self._cab = None
+
+    @property
+    def efie_near(self):
+        if self._cab is None:
+            self._cab = efie_near_matrices(self.vtx, self.tri, self.q)
+        return self._cab
+
+    def efie_apply(self, k, x):
+        """T x, T = ik/(4pi) sum_c Phi_c^T W G W Phi_c - i/(4pi k) Dv^T W G W Dv
+        + ik/(4pi) CA - i/(4pi k) CB (the listing's T with its two regularize terms);
+        x: (nE,) or (nE, nrhs) complex; k > 0."""
+        if not k > 0.0:
+            raise ValueError("the EFIE needs k > 0")
+        x = np.asarray(x, dtype=np.complex128)
+        one = x.ndim == 1
+        if one:
+            x = x[:, None]
+        nrhs = x.shape[1]
+        u = np.concatenate([self.w[:, None] * (f @ x) for f in (*self.rwg, self.div)], axis=1)
+        v = kernel_matvec(self.x, np.arange(self.nq), self.x, u, k)
+        wv = self.w[:, None] * v
+        vec = sum(self.rwg[c].T @ wv[:, c * nrhs:(c + 1) * nrhs] for c in range(3))
+        dv = self.div.T @ wv[:, 3 * nrhs:]
+        CA, CB = self.efie_near
+        y = 1j * k / (4.0 * np.pi) * (vec + CA @ x) - 1j / (4.0 * np.pi * k) * (dv + CB @ x)
+        return y[:, 0] if one else y
+
+    def rhs_planewave_efie(self, k, dirs, pols):
+        """F_m = int phi_m . p exp(ik d.x) by the domain's rule, one column per
+        (direction d_j, polarisation p_j) (the listing's integral(sigma, Vh, PWE))."""
+        dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+        pols = np.atleast_2d(np.asarray(pols, dtype=np.float64))
+        e = np.exp(1j * k * (self.x @ dirs.T))                   # (Nq, nd)
+        comp = sum(self.rwg[c].T @ (self.w[:, None] * e * pols[None, :, c]) for c in range(3))
+        return np.asarray(comp)
+
+
+def mie_pec_amplitudes(k, cos_theta):
+    """S1, S2 of a perfectly conducting unit sphere (Mie series in the
+    perfectly-conducting limit: a_n = psi_n'(k)/xi_n'(k), b_n = psi_n(k)/xi_n(k),
+    psi_n(x) = x j_n(x), xi_n(x) = x h_n(x)); the angle functions pi_n, tau_n by
+    their recurrences."""
+    from scipy.special import spherical_jn, spherical_yn
+    mu = np.asarray(cos_theta, dtype=np.float64)
+    nmax = int(np.ceil(k + 4.0 * k ** (1.0 / 3.0) + 10))
+    s1 = np.zeros(mu.shape, dtype=np.complex128)
+    s2 = np.zeros(mu.shape, dtype=np.complex128)
+    pi_prev, pi_cur = np.zeros_like(mu), np.ones_like(mu)   # pi_0, pi_1
+    for n in range(1, nmax + 1):
+        if n > 1:
+            pi_prev, pi_cur = pi_cur, ((2 * n - 1) * mu * pi_cur - n * pi_prev) / (n - 1)
+        tau = n * mu * pi_cur - (n + 1) * pi_prev
+        j, jp = spherical_jn(n, k), spherical_jn(n, k, derivative=True)
+        h = j + 1j * spherical_yn(n, k)
+        hp = jp + 1j * spherical_yn(n, k, derivative=True)
+        psi, dpsi = k * j, j + k * jp
+        xi, dxi = k * h, h + k * hp
+        an, bn = dpsi / dxi, psi / xi
+        c = (2 * n + 1) / (n * (n + 1))
+        s1 += c * (an * pi_cur + bn * tau)
+        s2 += c * (an * tau + bn * pi_cur)
+    return s1, s2
 
 
 # --------------------------------------------------------------------------

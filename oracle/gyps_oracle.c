@@ -291,6 +291,96 @@ int or_near_blocks(const double *vtx, const int32_t *tri, int q,
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* EFIE correction blocks with RWG functions on a near pair (a, b): for the   */
+/* local edges i of a and j of b (edge j of a triangle joins its vertices    */
+/* j+1 and j+2 and is opposite vertex j; sign s from tsign, length l),        */
+/*   RWG on b: f_j(y) = s l / (2 A_b) (y - P_j),  div f_j = s l / A_b,         */
+/*   int_b f_j / R = s l / (2 A_b) sum_m (P_m - P_j) int_b lambda_m / R,       */
+/* and                                                                        */
+/*   blkA[i][j] = sum_{k in a} w_k f_i(x_k) . (int_b f_j / R - G_kj),          */
+/*   blkB[i][j] = sum_{k in a} w_k div f_i (int_b div f_j / R - D_kj),         */
+/* with the Gauss sums G_kj = sum_{l in b, l != k} w_l f_j(y_l) / |x_k - y_l|  */
+/* and D_kj the same for div f_j (l == k only when a == b).                   */
+/*   tsign: nt x 3 (+1 / -1); blkA, blkB: npairs x 3 x 3                      */
+/* ------------------------------------------------------------------------ */
+int or_efie_near_blocks(const double *vtx, const int32_t *tri, const double *tsign, int q, int64_t npairs,
+                        const int64_t *pa, const int64_t *pb, double *blkA, double *blkB)
+{
+    double bary[21], wr[7];
+    if (or_quad_rule(q, bary, wr) != 0) return -1;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < npairs; ++p) {
+        int64_t a = pa[p], b = pb[p];
+        const double *A[3], *B[3];
+        for (int m = 0; m < 3; ++m) {
+            A[m] = vtx + 3 * (int64_t)tri[3 * a + m];
+            B[m] = vtx + 3 * (int64_t)tri[3 * b + m];
+        }
+        double ea[3], fa[3], na[3], eb[3], fb[3], nb[3];
+        for (int c = 0; c < 3; ++c) {
+            ea[c] = A[1][c] - A[0][c]; fa[c] = A[2][c] - A[0][c];
+            eb[c] = B[1][c] - B[0][c]; fb[c] = B[2][c] - B[0][c];
+        }
+        cross3(ea, fa, na);
+        cross3(eb, fb, nb);
+        double area_a = 0.5 * sqrt(dot3(na, na)), area_b = 0.5 * sqrt(dot3(nb, nb));
+        double ca[3], cb[3];  /* s l / (2 A) per local edge */
+        for (int j = 0; j < 3; ++j) {
+            double da[3], db[3];
+            for (int c = 0; c < 3; ++c) {
+                da[c] = A[(j + 2) % 3][c] - A[(j + 1) % 3][c];
+                db[c] = B[(j + 2) % 3][c] - B[(j + 1) % 3][c];
+            }
+            ca[j] = tsign[3 * a + j] * sqrt(dot3(da, da)) / (2.0 * area_a);
+            cb[j] = tsign[3 * b + j] * sqrt(dot3(db, db)) / (2.0 * area_b);
+        }
+        double bA[9] = {0}, bB[9] = {0};
+        for (int kq = 0; kq < q; ++kq) {
+            double xk[3];
+            for (int c = 0; c < 3; ++c)
+                xk[c] = bary[3 * kq] * A[0][c] + bary[3 * kq + 1] * A[1][c] + bary[3 * kq + 2] * A[2][c];
+            double wk = wr[kq] * area_a;
+            double I[3];
+            or_p1_inv_r(xk, B[0], B[1], B[2], I);
+            /* Gauss sums: sum_l eta_l y_l / r and sum_l eta_l / r */
+            double gy[3] = {0.0, 0.0, 0.0}, g1 = 0.0;
+            for (int lq = 0; lq < q; ++lq) {
+                if (a == b && lq == kq) continue;
+                double yl[3];
+                for (int c = 0; c < 3; ++c)
+                    yl[c] = bary[3 * lq] * B[0][c] + bary[3 * lq + 1] * B[1][c] + bary[3 * lq + 2] * B[2][c];
+                double dd[3] = {xk[0] - yl[0], xk[1] - yl[1], xk[2] - yl[2]};
+                double e = wr[lq] * area_b / sqrt(dot3(dd, dd));
+                for (int c = 0; c < 3; ++c) gy[c] += e * yl[c];
+                g1 += e;
+            }
+            double isum = I[0] + I[1] + I[2];
+            for (int j = 0; j < 3; ++j) {
+                /* int_b f_j / R - Gauss, and the same for div f_j */
+                double vec[3];
+                for (int c = 0; c < 3; ++c) {
+                    double an = I[0] * (B[0][c] - B[j][c]) + I[1] * (B[1][c] - B[j][c]) + I[2] * (B[2][c] - B[j][c]);
+                    double gs = gy[c] - g1 * B[j][c];
+                    vec[c] = cb[j] * (an - gs);
+                }
+                double dvj = 2.0 * cb[j] * (isum - g1);
+                for (int i = 0; i < 3; ++i) {
+                    double fi[3];
+                    for (int c = 0; c < 3; ++c) fi[c] = ca[i] * (xk[c] - A[i][c]);
+                    bA[3 * i + j] += wk * dot3(fi, vec);
+                    bB[3 * i + j] += wk * 2.0 * ca[i] * dvj;
+                }
+            }
+        }
+        for (int e = 0; e < 9; ++e) {
+            blkA[9 * p + e] = bA[e];
+            blkB[9 * p + e] = bB[e];
+        }
+    }
+    return 0;
+}
+
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
 /* ------------------------------------------------------------------------ */
 /* Double layer (the next operator after the single layer; the paper's       */
