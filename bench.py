@@ -48,7 +48,8 @@ def parse():
     p.add_argument("--impl", default="gyps", choices=["gyps", "reference"])
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "batch12_r64", "precond_ellipsoids", "sphere163842_k64_q3_r16",
-                            "assemble_sphere10242", "field_sphere10242_k16", "dl_sphere10242_k16_q7"])
+                            "assemble_sphere10242", "field_sphere10242_k16", "dl_sphere10242_k16_q7",
+                            "efie_sphere10242_k8_q3"])
     p.add_argument("--precond-meshes", type=int, default=125, help="training meshes (16 solves each)")
     p.add_argument("--precond-steps", type=int, default=3000)
     p.add_argument("--precond-test", type=int, default=8)
@@ -710,6 +711,139 @@ def run_dl(args):
     print(json.dumps(line), flush=True)
 
 
+def mie_pec_sphere(k, cos_theta):
+    """S1, S2 of the perfectly conducting unit sphere (Mie series, a_n = psi_n'/xi_n',
+    b_n = psi_n/xi_n); measurement only."""
+    from scipy.special import spherical_jn, spherical_yn
+    mu = np.asarray(cos_theta, dtype=np.float64)
+    s1 = np.zeros(mu.shape, dtype=np.complex128)
+    s2 = np.zeros(mu.shape, dtype=np.complex128)
+    p0, p1 = np.zeros_like(mu), np.ones_like(mu)
+    for n in range(1, int(np.ceil(k + 4.0 * k ** (1.0 / 3.0) + 10)) + 1):
+        if n > 1:
+            p0, p1 = p1, ((2 * n - 1) * mu * p1 - n * p0) / (n - 1)
+        tau = n * mu * p1 - (n + 1) * p0
+        j, jp = spherical_jn(n, k), spherical_jn(n, k, derivative=True)
+        h, hp = j + 1j * spherical_yn(n, k), jp + 1j * spherical_yn(n, k, derivative=True)
+        an, bn = (j + k * jp) / (h + k * hp), j / h
+        c = (2 * n + 1) / (n * (n + 1))
+        s1 += c * (an * p1 + bn * tau)
+        s2 += c * (an * tau + bn * p1)
+    return s1, s2
+
+
+def rwg_current_at_points(g, mesh, v, t, x):
+    """The surface current sum_e x_e phi_e at the mesh's Gauss points (numpy, from the
+    RWG definition: local edge j of a triangle joins vertices j+1 and j+2, sign +1
+    where it runs from the smaller to the larger index, phi = s l/(2A) (y - P_j));
+    measurement only."""
+    ne, edges = g.rwg_edges(mesh)
+    key = edges[:, 0].astype(np.int64) * mesh.nv + edges[:, 1]
+    qp = mesh.quad_points().cpu().numpy()
+    P = v[t]
+    two_a = np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)
+    J = np.zeros((mesh.nt, mesh.q, 3), dtype=np.complex128)
+    y = qp[:, :3].reshape(mesh.nt, mesh.q, 3)
+    for j in range(3):
+        a, b = t[:, (j + 1) % 3].astype(np.int64), t[:, (j + 2) % 3].astype(np.int64)
+        e = np.searchsorted(key, np.minimum(a, b) * mesh.nv + np.maximum(a, b))
+        c = np.where(a < b, 1.0, -1.0) * np.linalg.norm(P[:, (j + 2) % 3] - P[:, (j + 1) % 3], axis=1) / two_a
+        J += (x[e] * c)[:, None, None] * (y - P[:, None, j, :])
+    return qp, J.reshape(-1, 3)
+
+
+def run_efie(args):
+    """Workload efie_sphere10242_k8_q3: the EFIE of the electromagnetic listing
+    after Sec. 6.4 with RWG functions on the icosphere of 20480 triangles (30720
+    edges), q = 3 (61440 Gauss points), k = 8.  One step = one FP32 apply of T to
+    one random current (four density columns through the FP32 far kernel, FP64
+    correction); once each: the FP64 and double-float applies; then GMRES to 1e-6
+    on -T J = int phi . E_inc (x-polarised plane wave along z; FP32 operator,
+    double-float checks) and the far field of J against the Mie amplitudes of the
+    perfectly conducting sphere (E- and H-plane, 24 directions)."""
+    import torch
+
+    import paper_1804_00995_gb300 as g
+    from paper_1804_00995_gb300 import build as gb
+    gb.build()
+    cfg = synth.WORKLOADS["efie_sphere10242_k8_q3"]
+    v, t = synth.icosphere(cfg["level"])
+    mesh = g.Mesh(v, t, cfg["q"])
+    k = cfg["k"]
+    ne, _ = g.rwg_edges(mesh)
+    x = torch.as_tensor(synth.random_complex(np.random.default_rng(1), ne, 1)).cuda()
+    for _ in range(args.warmup):
+        g.efie_apply(mesh, k, x, prec="fp32")
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(smi_id_of(torch.cuda.get_device_properties(0)))
+    mesh.profile(True)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        y32 = g.efie_apply(mesh, k, x, prec="fp32")
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = mesh.profile_read()
+    mesh.profile(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    far_ms = prof["far_ms"] / max(prof["far_launches"], 1)
+    once = {}
+    for prec in ("fp64", "df64"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        y = g.efie_apply(mesh, k, x, prec=prec)
+        torch.cuda.synchronize()
+        once[prec] = {"ms": (time.perf_counter() - t0) * 1e3, "y": y}
+    y64 = once["fp64"].pop("y")
+    once["df64"]["rel_diff_vs_fp64"] = float(torch.linalg.norm(once["df64"].pop("y") - y64) / torch.linalg.norm(y64))
+    rel32 = float(torch.linalg.norm(y32 - y64) / torch.linalg.norm(y64))
+    d, p = np.asarray(cfg["dirs"][0]), np.asarray(cfg["pols"][0])
+    F = g.rhs_planewave_efie(mesh, k, d[None, :], p[None, :])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, rep = g.gmres_solve(mesh, k, F, tol=cfg["tol"], restart=300, maxit=3000, prec="fp32", check_prec="df64",
+                           max_refine=4, formulation="efie")
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    qp, Jq = rwg_current_at_points(g, mesh, v, t, J.cpu().numpy()[:, 0])
+    th = np.linspace(0.05, np.pi - 0.05, 12)
+    s1, s2 = mie_pec_sphere(k, np.cos(th))
+    err = 0.0
+    for xd, s in ((np.stack([np.sin(th), 0 * th, np.cos(th)], 1), s2), (np.stack([0 * th, np.sin(th), np.cos(th)], 1), s1)):
+        I = np.exp(-1j * k * (xd @ qp[:, :3].T)) @ (qp[:, 3:4] * Jq)
+        amp = k / (4.0 * np.pi) * np.linalg.norm(I - np.sum(I * xd, axis=1)[:, None] * xd, axis=1)
+        err = max(err, float(np.abs(amp / (np.abs(s) / k) - 1.0).max()))
+    pairs = float(mesh.nq) ** 2
+    achieved = pairs / (far_ms * 1e-3) / 1e9
+    props = torch.cuda.get_device_properties(0)
+    try:
+        peak_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
+    except Exception:
+        peak_mhz = clk.get("sm_max_mhz") or 2070.0
+    roof = sm_peak_pairs(props.multi_processor_count, peak_mhz) / 1e9
+    line = {
+        "metric": "GPairs/s EFIE apply (Gauss-point pairs per second, 4 density columns each)",
+        "value": pairs / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "efie_sphere10242_k8_q3", "nt": mesh.nt, "ne": ne, "nq": mesh.nq, "k": k,
+                   "columns_per_apply": 4, "near": "fp64 '[1/r]' correction (RWG from the P1 closed form)",
+                   "l2": "inputs 4 MB, not flushed (alu bound)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": roof, "unit": "GPairs/s", "frac": achieved / roof,
+                     "traffic": None, "kernel": "far32_kernel<4,2,false>", "far_ms_per_launch": far_ms,
+                     "peak_basis": "3 MUFU results per pair at 16 per clock per SM, measured sm_max_mhz"},
+        "fp32_rel_diff_vs_fp64": rel32, "once": once,
+        "solve": {"seconds": t_solve, "iterations": rep.iterations, "refinements": rep.refinements,
+                  "true_residual_df64": float(rep.true_residual[0]), "status": rep.status,
+                  "far_field_max_rel_error_vs_mie": err},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def solve_large(g, mesh, v, t, k, F, dirs, args):
     """Workload sphere163842_k64_q3_r16, --solve: (flexible) GMRES to 1e-6 on all
     16 plane waves, tensor-core working operator, double-float operator for the
@@ -863,6 +997,9 @@ def main():
         return
     if args.workload == "dl_sphere10242_k16_q7":
         run_dl(args)
+        return
+    if args.workload == "efie_sphere10242_k8_q3":
+        run_efie(args)
         return
     if args.workload == "sphere163842_k64_q3_r16":
         run_large(args)

@@ -66,8 +66,10 @@ typedef enum {
                                      interior Dirichlet eigenvalue */
     GYPS_FORM_BRAKHAGE_WERNER = 1, /* (1/2 M + K - i eta V) X = F: the density of u = (D - i eta S) phi,
                                      uniquely solvable for every k when eta > 0 */
-    GYPS_FORM_DIRECT_CFIE = 2      /* (1/2 M + K' - i eta V) X = F: X = du/dn of the total field, the same
+    GYPS_FORM_DIRECT_CFIE = 2,     /* (1/2 M + K' - i eta V) X = F: X = du/dn of the total field, the same
                                      density as the first-kind system; F from gyps_rhs_planewave_cfie */
+    GYPS_FORM_EFIE = 3             /* -T J = F (the electromagnetic listing after Sec. 6.4 with beta = 1):
+                                     J the RWG coefficients (ne unknowns), F from gyps_rhs_planewave_efie */
 } gyps_formulation;
 
 /* gyps_sl_apply flags */
@@ -238,6 +240,42 @@ gyps_status gyps_cfie_apply(gyps_mesh_t mesh, double k, double eta, int nrhs, co
                             void *Y, int64_t ldy, int prec, void *stream);
 
 /*
+ * RWG functions (the EFIE of the electromagnetic listing after Sec. 6.4), one per
+ * edge of a closed, consistently oriented mesh.  Edges are the vertex pairs
+ * (a < b) in lexicographic order; local edge j of a triangle joins its vertices
+ * j+1 and j+2 (opposite P_j); the triangle where the edge runs a -> b is its plus
+ * triangle.  phi(y) = s l_j / (2 A) (y - P_j), div phi = s l_j / A, s = +1 / -1.
+ * gyps_rwg_edges builds the functions (and the EFIE correction) on first use and
+ * returns their number; edges: HOST ne x 2 int32 vertex pairs, or NULL.
+ * Errors: INVALID (open or inconsistently oriented mesh), CUDA, OOM.
+ */
+gyps_status gyps_rwg_edges(gyps_mesh_t mesh, int64_t *ne, int32_t *edges, void *stream);
+
+/*
+ * EFIE operator of the listing (T with its two regularize terms):
+ *     Y = T X,  T = ik/(4pi) (sum_c Phi_c^T W G W Phi_c + CA) - i/(4pi k) (Dv^T W G W Dv + CB),
+ * Phi_c (c = x, y, z) and Dv the RWG functions and their divergence at the Gauss
+ * points, G the single layer's kernel (four density columns per right-hand side
+ * through the same far sum), CA / CB the '[1/r]' corrections on triangles sharing
+ * a vertex (analytic inner integrals from the P1 ones, minus the Gauss sums).
+ *   X, Y  ne x nrhs complex double2 (host or device), leading dims >= ne, not overlapping.
+ *   k     > 0.   prec  GYPS_PREC_FP32 (AUTO), GYPS_PREC_FP64 or GYPS_PREC_DF64.
+ * Synchronous. Errors: INVALID (k <= 0, sizes, open mesh), UNSUPPORTED (tensor
+ * cores), CUDA, OOM, TIMEOUT.
+ */
+gyps_status gyps_efie_apply(gyps_mesh_t mesh, double k, int nrhs, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                            int prec, void *stream);
+
+/*
+ * EFIE right-hand sides (the listing's integral(sigma, Vh, PWE)):
+ *     F_ej = sum_k w_k phi_e(x_k) . p_j exp(i k d_j . x_k),
+ * dirs, pols: HOST nrhs x 3 (propagation directions d_j, polarisations p_j, used
+ * as given).  F: ne x nrhs complex double2, leading dimension ldf >= ne.
+ */
+gyps_status gyps_rhs_planewave_efie(gyps_mesh_t mesh, double k, int nrhs, const double *dirs, const double *pols,
+                                    void *F, int64_t ldf, void *stream);
+
+/*
  * Single-layer potential at points (the radiation operator of the listing in
  * Sec. 6.4: Sdom = integral(points, S2, Gxy, Vh)/(4 pi)
  * + regularize(points, S2, '[1/r]', Vh)/(4 pi)):
@@ -312,7 +350,9 @@ typedef struct {
  * GMRES, A = V (Sec. 6.4, Eq. Singlelayerwf) or, with opts->formulation =
  * GYPS_FORM_BRAKHAGE_WERNER, A = 1/2 M + K - i opts->eta V (gyps_bw_apply;
  * pass -F for the sound-soft problem), or with GYPS_FORM_DIRECT_CFIE,
- * A = 1/2 M + K' - i opts->eta V (gyps_cfie_apply; F from gyps_rhs_planewave_cfie).  Arnoldi with classical Gram-Schmidt
+ * A = 1/2 M + K' - i opts->eta V (gyps_cfie_apply; F from gyps_rhs_planewave_cfie),
+ * or with GYPS_FORM_EFIE, A = -T (gyps_efie_apply; ne unknowns per column, F from
+ * gyps_rhs_planewave_efie; FP32 / FP64 / double-float only).  Arnoldi with classical Gram-Schmidt
  * applied twice, in FP64 on the device, Givens rotations on the host, one
  * Krylov space per column, the operator applied to all columns at once with
  * `opts->prec`.  After the

@@ -105,6 +105,12 @@ _SIGS = {
                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "gyps_rhs_planewave_cfie": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
+    "gyps_rwg_edges": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p, ctypes.c_void_p],
+                       ctypes.c_int),
+    "gyps_efie_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "gyps_rhs_planewave_efie": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "gyps_bw_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "gyps_sl_potential": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
@@ -388,6 +394,40 @@ def rhs_planewave(mesh: Mesh, k: float, dirs, device=None, stream=None):
     return f
 
 
+def rwg_edges(mesh: Mesh, stream=None):
+    """(ne, edges (ne, 2) int32 vertex pairs): the RWG functions of the mesh (gyps_rwg_edges)."""
+    ne = ctypes.c_int64()
+    _check(load().gyps_rwg_edges(mesh.handle, ctypes.byref(ne), None, _stream(stream)))
+    edges = np.zeros((ne.value, 2), dtype=np.int32)
+    _check(load().gyps_rwg_edges(mesh.handle, ctypes.byref(ne), edges.ctypes.data, _stream(stream)))
+    return ne.value, edges
+
+
+def efie_apply(mesh: Mesh, k: float, X, prec: str = "fp32", stream=None):
+    """Y = T X, the EFIE operator on the RWG coefficients (gyps_efie_apply); X: (ne,) or (ne, nrhs)."""
+    ne, _ = rwg_edges(mesh, stream)
+    one = (hasattr(X, "dim") and X.dim() == 1) or (not hasattr(X, "dim") and np.asarray(X).ndim == 1)
+    x, nrhs, ldx = _colmajor(X, ne, "X")
+    y = _empty_colmajor(ne, nrhs, x.device)
+    _check(load().gyps_efie_apply(mesh.handle, float(k), nrhs, x.data_ptr(), ldx, y.data_ptr(),
+                                  max(y.stride(1), ne) if nrhs > 1 else ne, PREC[prec], _stream(stream)))
+    return y[:, 0] if one else y
+
+
+def rhs_planewave_efie(mesh: Mesh, k: float, dirs, pols, device=None, stream=None):
+    """F (ne, nrhs): F_ej = int phi_e . p_j exp(i k d_j . x) (gyps_rhs_planewave_efie)."""
+    ne, _ = rwg_edges(mesh, stream)
+    dirs = np.ascontiguousarray(np.atleast_2d(np.asarray(dirs, dtype=np.float64)))
+    pols = np.ascontiguousarray(np.atleast_2d(np.asarray(pols, dtype=np.float64)))
+    if dirs.shape != pols.shape:
+        raise ValueError("one polarisation per direction")
+    dev = mesh.device if device is None else device
+    f = _empty_colmajor(ne, dirs.shape[0], dev)
+    _check(load().gyps_rhs_planewave_efie(mesh.handle, float(k), dirs.shape[0], dirs.ctypes.data, pols.ctypes.data,
+                                          f.data_ptr(), ne, _stream(stream)))
+    return f
+
+
 def rhs_planewave_cfie(mesh: Mesh, k: float, eta: float, dirs, device=None, stream=None):
     """F (nv, nrhs): F_ij = int phi_i (d/dn - i eta) exp(i k d_j . x) (gyps_rhs_planewave_cfie)."""
     dirs = np.ascontiguousarray(np.atleast_2d(np.asarray(dirs, dtype=np.float64)))
@@ -525,25 +565,27 @@ class GmresReport:
     status: str
 
 
-FORMULATION = {"sl": 0, "bw": 1, "cfie": 2}
+FORMULATION = {"sl": 0, "bw": 1, "cfie": 2, "efie": 3}
 
 
 def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, maxit: int = 1000,
                 prec: str = "fp32", check_prec: str = "fp64", x0=None, max_refine: int = 3, raise_on_fail=False,
                 precond: "Precond" = None, stream=None, formulation: str = "sl", eta: float = None):
-    """Solves A X = F (gyps_gmres_solve), A = V ("sl"), 1/2 M + K - i eta V ("bw") or
-    1/2 M + K' - i eta V ("cfie"; F from rhs_planewave_cfie with the same eta); eta
-    defaults to k, or 1 at k = 0.  Returns (X, GmresReport)."""
+    """Solves A X = F (gyps_gmres_solve), A = V ("sl"), 1/2 M + K - i eta V ("bw"),
+    1/2 M + K' - i eta V ("cfie"; F from rhs_planewave_cfie with the same eta) or -T
+    ("efie"; RWG coefficients, F from rhs_planewave_efie); eta defaults to k, or 1 at
+    k = 0.  Returns (X, GmresReport)."""
     if eta is None:
         eta = float(k) if k > 0 else 1.0
-    f, nrhs, ldf = _colmajor(F, mesh.nv, "F")
+    n = rwg_edges(mesh, stream)[0] if formulation == "efie" else mesh.nv
+    f, nrhs, ldf = _colmajor(F, n, "F")
     if x0 is not None:
-        x, _, _ = _colmajor(x0.clone() if hasattr(x0, "clone") else x0, mesh.nv, "x0")
+        x, _, _ = _colmajor(x0.clone() if hasattr(x0, "clone") else x0, n, "x0")
         x = x.to(f.device)
-        if x.stride(1) != mesh.nv and nrhs > 1:
+        if x.stride(1) != n and nrhs > 1:
             x = x.t().contiguous().t()
     else:
-        x = _empty_colmajor(mesh.nv, nrhs, f.device)
+        x = _empty_colmajor(n, nrhs, f.device)
     opts = _GmresOpts(float(tol), int(restart), int(maxit), PREC[prec], PREC[check_prec], 1 if x0 is not None else 0,
                       int(max_refine), precond.handle.value if precond is not None else None,
                       FORMULATION[formulation], float(eta))
@@ -553,7 +595,7 @@ def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, 
     rep = _GmresReport(0, 0, 0, 0, 0, est.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                        tru.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                        conv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
-    code = load().gyps_gmres_solve(mesh.handle, float(k), nrhs, f.data_ptr(), ldf, x.data_ptr(), mesh.nv,
+    code = load().gyps_gmres_solve(mesh.handle, float(k), nrhs, f.data_ptr(), ldf, x.data_ptr(), n,
                                    ctypes.byref(opts), ctypes.byref(rep), _stream(stream))
     if code not in (0, 4) or (code == 4 and raise_on_fail):
         _check(code)

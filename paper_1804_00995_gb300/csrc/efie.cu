@@ -1,0 +1,476 @@
+// EFIE with RWG functions (the electromagnetic listing after Sec. 6.4):
+//   T = ik/(4pi) int int phi_m . phi_n G - i/(4pi k) int int div phi_m div phi_n G
+//     + ik/(4pi) regularize(phi, '[1/r]', phi) - i/(4pi k) regularize(div phi, '[1/r]', div phi),
+// in the single layer's factorisation: per right-hand side four density columns
+// at the Gauss points (the three components of W Phi_RWG x and W Div x) go through
+// the same kernel sum v = G u, and the projection takes them back to the edges.
+// RWG function of local edge j of triangle t (edge j joins vertices j+1 and j+2,
+// opposite vertex P_j; sign s = +1 in the edge's plus triangle, where it runs from
+// the smaller to the larger vertex index, -1 in the minus one):
+//   phi(y) = s l_j / (2 A_t) (y - P_j),  div phi = s l_j / A_t.
+// The correction on triangles sharing a vertex: analytic int_b phi_j / R from the
+// P1 integrals, int_b phi_j / R = s l_j / (2 A_b) sum_m (P_m - P_j) int_b lambda_m / R,
+// minus the Gauss sum (the point itself left out), tested by the Gauss rule of a.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+#include "p1_geom.cuh"
+
+namespace gyps {
+
+constexpr double kInv4PiE = 0.0795774715459476678844418816862571810;
+
+// local edge data of triangle t: P (3 vertices), area, s l / (2A) per local edge
+struct RwgTri {
+    double3 P[3];
+    double c[3];
+};
+
+__device__ inline RwgTri rwg_tri(const double *vtx, const int32_t *tri, const int32_t *tedge, int64_t t)
+{
+    RwgTri r;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) r.P[m] = ld3(vtx, tri[3 * t + m]);
+    const double3 n = cross(r.P[1] - r.P[0], r.P[2] - r.P[0]);
+    const double two_area = sqrt(dot(n, n));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const double3 e = r.P[(j + 2) % 3] - r.P[(j + 1) % 3];
+        const double s = (tedge[3 * t + j] & 1) ? -1.0 : 1.0;
+        r.c[j] = s * sqrt(dot(e, e)) / two_area;  // s l / (2A)
+    }
+    return r;
+}
+
+// Densities at the Gauss points: column 4 c + m of right-hand side c, m < 3 the
+// components of w_l sum_j x_e(j) phi_j(y_l), m = 3 the divergence w_l sum_j x_e(j) div phi_j.
+// FP32 panel of R = 4 or 8 columns (interp32 layout) for right-hand sides c0, c0 + R/4.
+template <int R>
+__global__ void rwg_interp32_kernel(const double *vtx, const int32_t *tri, const int32_t *tedge,
+                                    const double4_32a *pts64, int q, int64_t nq, int64_t nq_pad, const double2 *X,
+                                    int64_t ldx, int c0, float *panel)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nq_pad) return;
+    const int64_t tile = l / kSrcTile;
+    const int p = (int)(l % kSrcTile) >> 1, lane = (int)(l & 1);
+    float *base = panel + tile * den_tile_floats(R);
+    double ur[R], ui[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) ur[j] = ui[j] = 0.0;
+    if (l < nq) {
+        const int64_t t = l / q;
+        const RwgTri g = rwg_tri(vtx, tri, tedge, t);
+        const double4_32a y = pts64[l];
+        const double3 yy = make_double3(y.x, y.y, y.z);
+#pragma unroll
+        for (int cc = 0; cc < R / 4; ++cc) {
+            const double2 *xc = X + (int64_t)(c0 + cc) * ldx;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const double2 xe = xc[tedge[3 * t + j] >> 1];
+                const double3 f = g.c[j] * (yy - g.P[j]);
+                const double d = 2.0 * g.c[j];
+                ur[4 * cc + 0] += f.x * xe.x; ui[4 * cc + 0] += f.x * xe.y;
+                ur[4 * cc + 1] += f.y * xe.x; ui[4 * cc + 1] += f.y * xe.y;
+                ur[4 * cc + 2] += f.z * xe.x; ui[4 * cc + 2] += f.z * xe.y;
+                ur[4 * cc + 3] += d * xe.x;   ui[4 * cc + 3] += d * xe.y;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            ur[j] *= y.w;
+            ui[j] *= y.w;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        float *u4 = base + 4 * ((int64_t)p * R + j);
+        u4[lane] = (float)ur[j];
+        u4[2 + lane] = (float)ui[j];
+        base[4 * kSrcPairs * R + 2 * ((int64_t)p * R + j) + lane] = -(float)ui[j];
+    }
+}
+
+// The same in FP64 for all right-hand sides: u64[l + (4 c + m) ld].
+__global__ void rwg_interp64_kernel(const double *vtx, const int32_t *tri, const int32_t *tedge,
+                                    const double4_32a *pts64, int q, int64_t nq, int64_t ld, const double2 *X,
+                                    int64_t ldx, int nrhs, double2 *u64)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (l >= nq || c >= nrhs) return;
+    const int64_t t = l / q;
+    const RwgTri g = rwg_tri(vtx, tri, tedge, t);
+    const double4_32a y = pts64[l];
+    const double3 yy = make_double3(y.x, y.y, y.z);
+    const double2 *xc = X + (int64_t)c * ldx;
+    double3 vr = make_double3(0.0, 0.0, 0.0), vi = vr;
+    double dr = 0.0, di = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const double2 xe = xc[tedge[3 * t + j] >> 1];
+        const double3 f = g.c[j] * (yy - g.P[j]);
+        vr = vr + xe.x * f;
+        vi = vi + xe.y * f;
+        dr += 2.0 * g.c[j] * xe.x;
+        di += 2.0 * g.c[j] * xe.y;
+    }
+    double2 *u = u64 + l + (int64_t)(4 * c) * ld;
+    u[0] = make_double2(y.w * vr.x, y.w * vi.x);
+    u[ld] = make_double2(y.w * vr.y, y.w * vi.y);
+    u[2 * ld] = make_double2(y.w * vr.z, y.w * vi.z);
+    u[3 * ld] = make_double2(y.w * dr, y.w * di);
+}
+
+// Correction blocks of the near pair (a, b): A[i][j] (vector part) and B[i][j]
+// (divergence part) for local edges i of a and j of b, without the k factors.
+__global__ void efie_blocks_kernel(const double *vtx, const int32_t *tri, const int32_t *tedge,
+                                   const double4_32a *pts64, int q, int64_t npairs, const int32_t *pair_a,
+                                   const int32_t *pair_b, double *blocks)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs) return;
+    const int64_t a = pair_a[p], b = pair_b[p];
+    const RwgTri ga = rwg_tri(vtx, tri, tedge, a), gb = rwg_tri(vtx, tri, tedge, b);
+    double bA[9], bB[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) bA[e] = bB[e] = 0.0;
+    for (int kq = 0; kq < q; ++kq) {
+        const double4_32a xk4 = pts64[a * q + kq];
+        const double3 xk = make_double3(xk4.x, xk4.y, xk4.z);
+        double I[3];
+        p1_over_r(xk, gb.P, I);
+        double3 gy = make_double3(0.0, 0.0, 0.0);
+        double g1 = 0.0;
+        for (int lq = 0; lq < q; ++lq) {
+            if (a == b && lq == kq) continue;
+            const double4_32a y4 = pts64[b * q + lq];
+            const double3 y = make_double3(y4.x, y4.y, y4.z);
+            const double3 d = xk - y;
+            const double e = y4.w / sqrt(dot(d, d));
+            gy = gy + e * y;
+            g1 += e;
+        }
+        const double isum = I[0] + I[1] + I[2];
+        const double3 iy = I[0] * gb.P[0] + I[1] * gb.P[1] + I[2] * gb.P[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            // int_b phi_j / R - Gauss = c_j ((sum_m I_m P_m - isum P_j) - (gy - g1 P_j))
+            const double3 vec = gb.c[j] * ((iy - isum * gb.P[j]) - (gy - g1 * gb.P[j]));
+            const double dv = 2.0 * gb.c[j] * (isum - g1);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double3 fi = ga.c[i] * (xk - ga.P[i]);
+                bA[3 * i + j] += xk4.w * dot(fi, vec);
+                bB[3 * i + j] += xk4.w * 2.0 * ga.c[i] * dv;
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        blocks[18 * p + e] = bA[e];
+        blocks[18 * p + 9 + e] = bB[e];
+    }
+}
+
+// Y[e, c] = sign (ik/(4pi) (sum_k w_k phi_e(x_k) . v_vec + CA x) - i/(4pi k) (sum_k w_k div phi_e v_div + CB x)),
+// one thread per edge and right-hand side: the Gauss points of its two triangles and
+// the correction blocks of their near pairs.
+__global__ void efie_project_kernel(const double *vtx, const int32_t *tri, const int32_t *tedge, const int32_t *etri,
+                                    const double4_32a *pts64, int q, int64_t ne, const double2 *v, int64_t ldv,
+                                    const int32_t *pair_ptr, const int32_t *pair_b, const double *blocks,
+                                    const double2 *X, int64_t ldx, double k, double sign, double2 *Y, int64_t ldy)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (e >= ne) return;
+    const double2 *xc = X + (int64_t)c * ldx;
+    const double2 *v0 = v + (int64_t)(4 * c) * ldv;
+    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;  // vector and divergence parts
+    for (int side = 0; side < 2; ++side) {
+        const int32_t code = etri[2 * e + side];
+        const int64_t t = code / 3;
+        const int i = code - 3 * (int)t;
+        const RwgTri g = rwg_tri(vtx, tri, tedge, t);
+        for (int kq = 0; kq < q; ++kq) {
+            const int64_t l = t * q + kq;
+            const double4_32a x = pts64[l];
+            const double3 f = g.c[i] * (make_double3(x.x, x.y, x.z) - g.P[i]);
+            const double2 vx = v0[l], vy = v0[l + ldv], vz = v0[l + 2 * ldv], vd = v0[l + 3 * ldv];
+            ar += x.w * (f.x * vx.x + f.y * vy.x + f.z * vz.x);
+            ai += x.w * (f.x * vx.y + f.y * vy.y + f.z * vz.y);
+            br += x.w * 2.0 * g.c[i] * vd.x;
+            bi += x.w * 2.0 * g.c[i] * vd.y;
+        }
+        for (int32_t p = pair_ptr[t]; p < pair_ptr[t + 1]; ++p) {
+            const int64_t b = pair_b[p];
+            const double *blk = blocks + 18 * (int64_t)p;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const double2 xf = xc[tedge[3 * b + j] >> 1];
+                ar += blk[3 * i + j] * xf.x;
+                ai += blk[3 * i + j] * xf.y;
+                br += blk[9 + 3 * i + j] * xf.x;
+                bi += blk[9 + 3 * i + j] * xf.y;
+            }
+        }
+    }
+    // ik/(4pi) (ar + i ai) - i/(4pi k) (br + i bi)
+    const double ca = sign * k * kInv4PiE, cb = sign * kInv4PiE / k;
+    Y[e + (int64_t)c * ldy] = make_double2(-ca * ai + cb * bi, ca * ar - cb * br);
+}
+
+// F[e, j] = sum_k w_k phi_e(x_k) . p_j exp(i k d_j . x_k); dp: nrhs x 6 (d, p).
+__global__ void efie_rhs_kernel(const double *vtx, const int32_t *tri, const int32_t *tedge, const int32_t *etri,
+                                const double4_32a *pts64, int q, int64_t ne, double k, const double *dp, double2 *F,
+                                int64_t ldf)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (e >= ne) return;
+    const double3 d = make_double3(dp[6 * j], dp[6 * j + 1], dp[6 * j + 2]);
+    const double3 pol = make_double3(dp[6 * j + 3], dp[6 * j + 4], dp[6 * j + 5]);
+    double fr = 0.0, fi = 0.0;
+    for (int side = 0; side < 2; ++side) {
+        const int32_t code = etri[2 * e + side];
+        const int64_t t = code / 3;
+        const int i = code - 3 * (int)t;
+        const RwgTri g = rwg_tri(vtx, tri, tedge, t);
+        for (int kq = 0; kq < q; ++kq) {
+            const double4_32a x = pts64[t * q + kq];
+            const double3 xx = make_double3(x.x, x.y, x.z);
+            const double fp = x.w * dot(g.c[i] * (xx - g.P[i]), pol);
+            double sn, cs;
+            sincos(k * dot(d, xx), &sn, &cs);
+            fr += fp * cs;
+            fi += fp * sn;
+        }
+    }
+    F[e + (int64_t)j * ldf] = make_double2(fr, fi);
+}
+
+// RWG topology on the host (edges in lexicographic order of their vertex pairs),
+// then the correction blocks on the device.
+gyps_status efie_prepare(Mesh *m, cudaStream_t s)
+{
+    if (m->d_efie_blocks) return GYPS_OK;
+    std::vector<int32_t> tri((size_t)m->nt * 3);
+    GYPS_CUDA(cudaMemcpyAsync(tri.data(), m->d_tri, tri.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GYPS_CUDA(cudaStreamSynchronize(s));
+    struct Half {
+        int64_t key;
+        int32_t code;  // 3 t + j
+        bool plus;
+    };
+    std::vector<Half> h((size_t)m->nt * 3);
+    for (int64_t t = 0; t < m->nt; ++t)
+        for (int j = 0; j < 3; ++j) {
+            const int64_t a = tri[3 * t + (j + 1) % 3], b = tri[3 * t + (j + 2) % 3];
+            h[3 * t + j] = {std::min(a, b) * m->nv + std::max(a, b), (int32_t)(3 * t + j), a < b};
+        }
+    std::sort(h.begin(), h.end(), [](const Half &x, const Half &y) { return x.key < y.key; });
+    if (h.size() % 2 != 0) return set_error(GYPS_ERR_INVALID, "RWG functions need a closed mesh");
+    const int64_t ne = (int64_t)h.size() / 2;
+    std::vector<int32_t> tedge((size_t)m->nt * 3), etri((size_t)ne * 2), edges((size_t)ne * 2);
+    for (int64_t e = 0; e < ne; ++e) {
+        const Half &x = h[2 * e], &y = h[2 * e + 1];
+        if (x.key != y.key || (2 * e + 2 < (int64_t)h.size() && h[2 * e + 2].key == x.key) ||
+            (e > 0 && h[2 * e - 1].key == x.key))
+            return set_error(GYPS_ERR_INVALID, "RWG functions need a closed mesh (every edge in two triangles)");
+        if (x.plus == y.plus)
+            return set_error(GYPS_ERR_INVALID, "RWG functions need a consistently oriented mesh");
+        const Half &pl = x.plus ? x : y, &mi = x.plus ? y : x;
+        etri[2 * e] = pl.code;
+        etri[2 * e + 1] = mi.code;
+        tedge[pl.code] = (int32_t)(e << 1);
+        tedge[mi.code] = (int32_t)((e << 1) | 1);
+        edges[2 * e] = (int32_t)(x.key / m->nv);
+        edges[2 * e + 1] = (int32_t)(x.key % m->nv);
+    }
+    int32_t *d_tedge = nullptr, *d_etri = nullptr;
+    double *d_blocks = nullptr;
+    cudaError_t err = cudaMalloc((void **)&d_tedge, tedge.size() * sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMalloc((void **)&d_etri, etri.size() * sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMalloc((void **)&d_blocks, (size_t)m->npairs * 18 * sizeof(double));
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(d_tedge, tedge.data(), tedge.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(d_etri, etri.data(), etri.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) {
+        efie_blocks_kernel<<<(unsigned)((m->npairs + 127) / 128), 128, 0, s>>>(
+            m->d_vtx, m->d_tri, d_tedge, m->d_pts64, m->q, m->npairs, m->d_pair_a, m->d_pair_b, d_blocks);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) {
+        cudaFree(d_tedge);
+        cudaFree(d_etri);
+        cudaFree(d_blocks);
+        return cuda_error(err, "EFIE topology / correction");
+    }
+    m->ne = ne;
+    m->d_tedge = d_tedge;
+    m->d_etri = d_etri;
+    m->h_edges = std::move(edges);
+    m->d_efie_blocks = d_blocks;
+    return GYPS_OK;
+}
+
+gyps_status efie_apply_device(Mesh *m, double k, double sign, int nrhs, const double2 *X, int64_t ldx, double2 *Y,
+                              int64_t ldy, int prec, cudaStream_t s)
+{
+    if (prec == GYPS_PREC_AUTO) prec = GYPS_PREC_FP32;
+    if (prec != GYPS_PREC_FP64 && prec != GYPS_PREC_FP32 && prec != GYPS_PREC_DF64)
+        return set_error(GYPS_ERR_UNSUPPORTED, "EFIE: FP64, FP32 or DF64");
+    GYPS_TRY(efie_prepare(m, s));
+    const int64_t ld = m->nq;
+    const int ncol = 4 * nrhs;
+    GYPS_TRY(grow(m, &m->ws_v, &m->ws_v_bytes, (size_t)(ld * ncol) * sizeof(double2)));
+    double2 *v = reinterpret_cast<double2 *>(m->ws_v);
+    if (m->prof) ++m->prof_applies;
+    if (prec == GYPS_PREC_FP32) {
+        GYPS_CUDA(cudaMemsetAsync(v, 0, (size_t)(ld * ncol) * sizeof(double2), s));
+        GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(m->n_src_tiles * den_tile_floats(8)) * sizeof(float)));
+        float *panel = reinterpret_cast<float *>(m->ws_den);
+        const unsigned gi = (unsigned)((m->nq_pad + 255) / 256);
+        for (int c0 = 0; c0 < nrhs;) {
+            const int w = nrhs - c0 >= 2 ? 2 : 1;  // right-hand sides per pass (4 columns each)
+            if (w == 2)
+                rwg_interp32_kernel<8><<<gi, 256, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_pts64, m->q, m->nq,
+                                                          m->nq_pad, X, ldx, c0, panel);
+            else
+                rwg_interp32_kernel<4><<<gi, 256, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_pts64, m->q, m->nq,
+                                                          m->nq_pad, X, ldx, c0, panel);
+            GYPS_CUDA(cudaGetLastError());
+            GYPS_TRY(far32_panel(m, k, panel, 4 * w, v + (int64_t)(4 * c0) * ld, ld, s));
+            c0 += w;
+        }
+    } else {
+        GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(ld * ncol) * sizeof(double2)));
+        double2 *u64 = reinterpret_cast<double2 *>(m->ws_den);
+        dim3 gi((unsigned)((m->nq + 255) / 256), (unsigned)nrhs);
+        rwg_interp64_kernel<<<gi, 256, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_pts64, m->q, m->nq, ld, X, ldx,
+                                               nrhs, u64);
+        GYPS_CUDA(cudaGetLastError());
+        for (int c0 = 0; c0 < ncol;) {
+            const int left = ncol - c0;
+            if (prec == GYPS_PREC_DF64) {
+                const int w = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+                GYPS_TRY(run_far_df(m, k, m->d_pts64, true, u64, ld, c0, w, v, ld, 0, m->nq, s));
+                c0 += w;
+            } else {
+                const int w = left >= 4 ? 4 : left >= 2 ? 2 : 1;
+                GYPS_TRY(far64_cols(m, k, u64, ld, c0, w, v, ld, s));
+                c0 += w;
+            }
+        }
+    }
+    dim3 gp((unsigned)((m->ne + 127) / 128), (unsigned)nrhs);
+    efie_project_kernel<<<gp, 128, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_etri, m->d_pts64, m->q, m->ne, v, ld,
+                                           m->d_pair_ptr, m->d_pair_b, m->d_efie_blocks, X, ldx, k, sign, Y, ldy);
+    GYPS_CUDA(cudaGetLastError());
+    return GYPS_OK;
+}
+
+}  // namespace gyps
+
+using namespace gyps;
+
+extern "C" gyps_status gyps_rwg_edges(gyps_mesh_t h, int64_t *ne, int32_t *edges, void *stream)
+{
+    Mesh *m;
+    GYPS_TRY(check_mesh(h, &m));
+    if (!ne) return set_error(GYPS_ERR_INVALID, "NULL argument");
+    GYPS_TRY(efie_prepare(m, (cudaStream_t)stream));
+    *ne = m->ne;
+    if (edges) std::copy(m->h_edges.begin(), m->h_edges.end(), edges);
+    return GYPS_OK;
+}
+
+extern "C" gyps_status gyps_efie_apply(gyps_mesh_t h, double k, int nrhs, const void *X, int64_t ldx, void *Y,
+                                       int64_t ldy, int prec, void *stream)
+{
+    Mesh *m;
+    GYPS_TRY(check_mesh(h, &m));
+    if (nrhs < 1 || nrhs > 4096) return set_error(GYPS_ERR_INVALID, "nrhs must be in 1..4096");
+    if (!X || !Y) return set_error(GYPS_ERR_INVALID, "NULL argument");
+    if (!std::isfinite(k) || !(k > 0.0)) return set_error(GYPS_ERR_INVALID, "the EFIE needs a finite k > 0");
+    if (prec == GYPS_PREC_AUTO) prec = GYPS_PREC_FP32;
+    if (prec == GYPS_PREC_TC_BF16X3) return set_error(GYPS_ERR_UNSUPPORTED, "EFIE: FP64, FP32 or DF64");
+    if (prec != GYPS_PREC_FP64 && prec != GYPS_PREC_FP32 && prec != GYPS_PREC_DF64)
+        return set_error(GYPS_ERR_INVALID, "unknown precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    GYPS_TRY(efie_prepare(m, s));
+    const int64_t ne = m->ne;
+    if (ldx < ne || ldy < ne) return set_error(GYPS_ERR_INVALID, "leading dimension < number of edges");
+    const bool dx = is_device_pointer(X), dy = is_device_pointer(Y);
+    if (dx && dy && (const char *)X < (const char *)Y + ldy * nrhs * 16 &&
+        (const char *)Y < (const char *)X + ldx * nrhs * 16)
+        return set_error(GYPS_ERR_INVALID, "X and Y overlap");
+    const size_t blk = (size_t)ne * nrhs * sizeof(double2);
+    double2 *xs = nullptr, *ys = nullptr;
+    if (!dx || !dy) {
+        GYPS_TRY(grow(m, &m->ws_stage, &m->ws_stage_bytes, 2 * blk));
+        xs = reinterpret_cast<double2 *>(m->ws_stage);
+        ys = xs + (size_t)ne * nrhs;
+    }
+    const double2 *xin = (const double2 *)X;
+    int64_t lxin = ldx;
+    if (!dx) {
+        GYPS_CUDA(cudaMemcpy2DAsync(xs, ne * sizeof(double2), X, ldx * sizeof(double2), ne * sizeof(double2), nrhs,
+                                    cudaMemcpyHostToDevice, s));
+        xin = xs;
+        lxin = ne;
+    }
+    double2 *yout = dy ? (double2 *)Y : ys;
+    const int64_t lyout = dy ? ldy : ne;
+    GYPS_TRY(efie_apply_device(m, k, 1.0, nrhs, xin, lxin, yout, lyout, prec, s));
+    if (!dy)
+        GYPS_CUDA(cudaMemcpy2DAsync(Y, ldy * sizeof(double2), ys, ne * sizeof(double2), ne * sizeof(double2), nrhs,
+                                    cudaMemcpyDeviceToHost, s));
+    GYPS_CUDA(cudaStreamSynchronize(s));
+    return check_err_word(m, s);
+}
+
+extern "C" gyps_status gyps_rhs_planewave_efie(gyps_mesh_t h, double k, int nrhs, const double *dirs,
+                                               const double *pols, void *F, int64_t ldf, void *stream)
+{
+    Mesh *m;
+    GYPS_TRY(check_mesh(h, &m));
+    if (!F || !dirs || !pols) return set_error(GYPS_ERR_INVALID, "NULL argument");
+    if (nrhs < 1 || nrhs > 4096) return set_error(GYPS_ERR_INVALID, "nrhs must be in 1..4096");
+    if (!std::isfinite(k) || k < 0.0) return set_error(GYPS_ERR_INVALID, "k must be finite and >= 0");
+    std::vector<double> dp((size_t)nrhs * 6);
+    for (int j = 0; j < nrhs; ++j)
+        for (int c = 0; c < 3; ++c) {
+            dp[6 * j + c] = dirs[3 * j + c];
+            dp[6 * j + 3 + c] = pols[3 * j + c];
+        }
+    for (double x : dp)
+        if (!std::isfinite(x)) return set_error(GYPS_ERR_INVALID, "non-finite direction or polarisation");
+    cudaStream_t s = (cudaStream_t)stream;
+    GYPS_TRY(efie_prepare(m, s));
+    const int64_t ne = m->ne;
+    if (ldf < ne) return set_error(GYPS_ERR_INVALID, "ldf < number of edges");
+    const bool df = is_device_pointer(F);
+    const size_t bytes = (size_t)ne * nrhs * sizeof(double2);
+    const size_t bdp = (dp.size() * sizeof(double) + 255) / 256 * 256;
+    GYPS_TRY(grow(m, &m->ws_stage, &m->ws_stage_bytes, bdp + (df ? 0 : bytes)));
+    unsigned char *st = reinterpret_cast<unsigned char *>(m->ws_stage);
+    double *d_dp = reinterpret_cast<double *>(st);
+    GYPS_CUDA(cudaMemcpyAsync(d_dp, dp.data(), dp.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    double2 *fout = df ? (double2 *)F : reinterpret_cast<double2 *>(st + bdp);
+    const int64_t lf = df ? ldf : ne;
+    dim3 g((unsigned)((ne + 127) / 128), (unsigned)nrhs);
+    efie_rhs_kernel<<<g, 128, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_etri, m->d_pts64, m->q, ne, k, d_dp, fout,
+                                      lf);
+    GYPS_CUDA(cudaGetLastError());
+    if (!df)
+        GYPS_CUDA(cudaMemcpy2DAsync(F, ldf * sizeof(double2), fout, ne * sizeof(double2), ne * sizeof(double2), nrhs,
+                                    cudaMemcpyDeviceToHost, s));
+    GYPS_CUDA(cudaStreamSynchronize(s));
+    return GYPS_OK;
+}

@@ -433,6 +433,34 @@ static gyps_status run_far64(Mesh *m, double k, const double4_32a *tgt, bool sel
 // Splits nrhs into register-resident chunks of 8, 4, 2 and 1 columns.
 static int chunk_width(int left) { return left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1; }
 
+// FP32 far sum of a density panel prepared by the caller (R = 1, 2, 4 or 8 columns,
+// interp32 layout), over all quadrature points as targets, added into v (k > 0).
+gyps_status far32_panel(Mesh *m, double k, const float *panel, int R, double2 *v, int64_t ldv, cudaStream_t s)
+{
+    StageTimer tf(m, s, 1);
+    switch (R) {
+    case 8: GYPS_TRY((launch_far32<8, 2, false>(m, far_args(m, panel, v, ldv, 0, m->nq, FarCfg<8, 2>::TT, k), s))); break;
+    case 4: GYPS_TRY((launch_far32<4, 2, false>(m, far_args(m, panel, v, ldv, 0, m->nq, FarCfg<4, 2>::TT, k), s))); break;
+    case 2: GYPS_TRY((launch_far32<2, 4, false>(m, far_args(m, panel, v, ldv, 0, m->nq, FarCfg<2, 4>::TT, k), s))); break;
+    case 1: GYPS_TRY((launch_far32<1, 4, false>(m, far_args(m, panel, v, ldv, 0, m->nq, FarCfg<1, 4>::TT, k), s))); break;
+    default: return set_error(GYPS_ERR_INVALID, "panel width");
+    }
+    tf.done(1);
+    return GYPS_OK;
+}
+
+// FP64 far sum of u64 columns [c0, c0 + w), w = 1, 2 or 4, all quadrature points as targets.
+gyps_status far64_cols(Mesh *m, double k, const double2 *u64, int64_t ldu, int c0, int w, double2 *v, int64_t ldv,
+                       cudaStream_t s)
+{
+    switch (w) {
+    case 4: return run_far64<4>(m, k, m->d_pts64, true, u64, ldu, c0, v, ldv, 0, m->nq, s);
+    case 2: return run_far64<2>(m, k, m->d_pts64, true, u64, ldu, c0, v, ldv, 0, m->nq, s);
+    case 1: return run_far64<1>(m, k, m->d_pts64, true, u64, ldu, c0, v, ldv, 0, m->nq, s);
+    default: return set_error(GYPS_ERR_INVALID, "column width");
+    }
+}
+
 gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
                          int prec, uint32_t flags, int64_t tri_begin, int64_t tri_end, cudaStream_t s)
 {

@@ -186,10 +186,11 @@ struct Solver {
     double eta = 0.0;
 
     // Y = A X for the system's operator A: V (first kind), 1/2 M + K - i eta V
-    // (Brakhage-Werner) or 1/2 M + K' - i eta V (direct combined field); X and Y
-    // are nv x nrhs.
+    // (Brakhage-Werner), 1/2 M + K' - i eta V (direct combined field), all
+    // nv x nrhs, or -T (the EFIE, ne x nrhs).
     gyps_status op(const double2 *X, int64_t ldx, double2 *Y, int prec)
     {
+        if (form == GYPS_FORM_EFIE) return efie_apply_device(m, k, -1.0, nrhs, X, ldx, Y, nv, prec, s);
         if (form == GYPS_FORM_BRAKHAGE_WERNER || form == GYPS_FORM_DIRECT_CFIE)
             return combined_apply_device(m, k, eta, form == GYPS_FORM_DIRECT_CFIE, nrhs, X, ldx, Y, nv, prec, s);
         return apply_device(m, k, nrhs, X, ldx, Y, nv, prec, 0, 0, m->nt, s);
@@ -418,12 +419,13 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
     S.nrhs = nrhs;
     S.restart = o.restart;
     S.s = s;
-    S.nv = m->nv;
+    const int64_t n = o.formulation == GYPS_FORM_EFIE ? m->ne : m->nv;  // unknowns per column
+    S.nv = n;
     S.form = o.formulation;
     S.eta = o.eta;
-    S.grid_v = dim3((unsigned)((m->nv + 255) / 256), (unsigned)nrhs);
-    S.grid_r = dim3((unsigned)std::min<int64_t>((m->nv + 255) / 256, 64), (unsigned)nrhs);
-    const size_t blk = (size_t)m->nv * nrhs * sizeof(double2);
+    S.grid_v = dim3((unsigned)((n + 255) / 256), (unsigned)nrhs);
+    S.grid_r = dim3((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)nrhs);
+    const size_t blk = (size_t)n * nrhs * sizeof(double2);
     GYPS_CUDA(cudaMalloc((void **)&S.w.Q, blk * (o.restart + 1)));
     GYPS_CUDA(cudaMalloc((void **)&S.w.W, blk));
     GYPS_CUDA(cudaMalloc((void **)&S.w.R, blk));
@@ -439,13 +441,13 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
     GYPS_CUDA(cudaMallocHost((void **)&S.w.hh, (size_t)(o.restart + 1) * nrhs * sizeof(double2)));
     GYPS_CUDA(cudaMallocHost((void **)&S.w.hn, nrhs * sizeof(double)));
 
-    if (!o.use_x0) GYPS_CUDA(cudaMemset2DAsync(X, ldx * sizeof(double2), 0, m->nv * sizeof(double2), nrhs, s));
+    if (!o.use_x0) GYPS_CUDA(cudaMemset2DAsync(X, ldx * sizeof(double2), 0, n * sizeof(double2), nrhs, s));
 
     std::vector<double> fn;
     {
         // ||F|| per column
         double2 *Fc = S.w.R;
-        GYPS_CUDA(cudaMemcpy2DAsync(Fc, m->nv * sizeof(double2), F, ldf * sizeof(double2), m->nv * sizeof(double2), nrhs,
+        GYPS_CUDA(cudaMemcpy2DAsync(Fc, n * sizeof(double2), F, ldf * sizeof(double2), n * sizeof(double2), nrhs,
                                     cudaMemcpyDeviceToDevice, s));
         GYPS_TRY(S.norms(Fc, fn));
     }
@@ -480,9 +482,9 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
         GYPS_CUDA(cudaMalloc((void **)&Xd, blk));
         GYPS_CUDA(cudaMemsetAsync(Xd, 0, blk, s));
         int before = S.iters;
-        gyps_status st = S.solve(Bd, m->nv, Xd, m->nv, true, tol_d, o.prec, budget, est);
+        gyps_status st = S.solve(Bd, n, Xd, n, true, tol_d, o.prec, budget, est);
         if (st == GYPS_OK) {
-            zadd_kernel<<<S.grid_v, 256, 0, s>>>(Xd, m->nv, X, ldx);
+            zadd_kernel<<<S.grid_v, 256, 0, s>>>(Xd, n, X, ldx);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) st = cuda_error(e, "zadd_kernel");
         }
@@ -524,14 +526,21 @@ extern "C" gyps_status gyps_gmres_solve(gyps_mesh_t h, double k, int nrhs, const
     GYPS_TRY(check_mesh(h, &m));
     if (!F || !X || !opts) return set_error(GYPS_ERR_INVALID, "NULL argument");
     if (nrhs < 1 || nrhs > 4096) return set_error(GYPS_ERR_INVALID, "nrhs must be in 1..4096");
-    if (ldf < m->nv || ldx < m->nv) return set_error(GYPS_ERR_INVALID, "leading dimension < nv");
     if (!std::isfinite(k) || k < 0.0) return set_error(GYPS_ERR_INVALID, "k must be finite and >= 0");
     const gyps_gmres_opts &o = *opts;
     if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 4096 || o.maxit < 1 || o.max_refine < 0)
         return set_error(GYPS_ERR_INVALID, "bad GMRES options");
     if (o.formulation != GYPS_FORM_SINGLE_LAYER && o.formulation != GYPS_FORM_BRAKHAGE_WERNER &&
-        o.formulation != GYPS_FORM_DIRECT_CFIE)
+        o.formulation != GYPS_FORM_DIRECT_CFIE && o.formulation != GYPS_FORM_EFIE)
         return set_error(GYPS_ERR_INVALID, "unknown formulation");
+    if (o.formulation == GYPS_FORM_EFIE) {
+        if (!(k > 0.0)) return set_error(GYPS_ERR_INVALID, "the EFIE needs k > 0");
+        if (o.prec == GYPS_PREC_TC_BF16X3 || o.check_prec == GYPS_PREC_TC_BF16X3)
+            return set_error(GYPS_ERR_UNSUPPORTED, "EFIE: FP64, FP32 or DF64");
+        GYPS_TRY(efie_prepare(m, (cudaStream_t)stream));
+    }
+    const int64_t n = o.formulation == GYPS_FORM_EFIE ? m->ne : m->nv;
+    if (ldf < n || ldx < n) return set_error(GYPS_ERR_INVALID, "leading dimension < number of unknowns");
     if (o.formulation != GYPS_FORM_SINGLE_LAYER) {
         if (!std::isfinite(o.eta)) return set_error(GYPS_ERR_INVALID, "eta must be finite");
         if (o.precond) return set_error(GYPS_ERR_UNSUPPORTED, "the learned preconditioner models the single layer");
@@ -541,24 +550,24 @@ extern "C" gyps_status gyps_gmres_solve(gyps_mesh_t h, double k, int nrhs, const
     cudaStream_t s = (cudaStream_t)stream;
     const bool df = is_device_pointer(F), dx = is_device_pointer(X);
     if (df && dx) return gmres_device(m, k, nrhs, (const double2 *)F, ldf, (double2 *)X, ldx, o, report, s);
-    const size_t blk = (size_t)m->nv * nrhs * sizeof(double2);
+    const size_t blk = (size_t)n * nrhs * sizeof(double2);
     double2 *fs = nullptr, *xs = nullptr;
     GYPS_CUDA(cudaMalloc((void **)&fs, 2 * blk));
-    xs = fs + (size_t)m->nv * nrhs;
+    xs = fs + (size_t)n * nrhs;
     gyps_status st = GYPS_OK;
     const double2 *fin = (const double2 *)F;
     int64_t lf = ldf;
     if (!df) {
-        cudaError_t e = cudaMemcpy2DAsync(fs, m->nv * sizeof(double2), F, ldf * sizeof(double2), m->nv * sizeof(double2),
+        cudaError_t e = cudaMemcpy2DAsync(fs, n * sizeof(double2), F, ldf * sizeof(double2), n * sizeof(double2),
                                           nrhs, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) st = cuda_error(e, "copy F");
         fin = fs;
-        lf = m->nv;
+        lf = n;
     }
     double2 *xio = dx ? (double2 *)X : xs;
-    int64_t lx = dx ? ldx : m->nv;
+    int64_t lx = dx ? ldx : n;
     if (st == GYPS_OK && !dx && o.use_x0) {
-        cudaError_t e = cudaMemcpy2DAsync(xs, m->nv * sizeof(double2), X, ldx * sizeof(double2), m->nv * sizeof(double2),
+        cudaError_t e = cudaMemcpy2DAsync(xs, n * sizeof(double2), X, ldx * sizeof(double2), n * sizeof(double2),
                                           nrhs, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) st = cuda_error(e, "copy X");
     }
@@ -566,8 +575,8 @@ extern "C" gyps_status gyps_gmres_solve(gyps_mesh_t h, double k, int nrhs, const
     if (st == GYPS_OK) {
         solve_st = gmres_device(m, k, nrhs, fin, lf, xio, lx, o, report, s);
         if ((solve_st == GYPS_OK || solve_st == GYPS_ERR_NOT_CONVERGED) && !dx) {
-            cudaError_t e = cudaMemcpy2DAsync(X, ldx * sizeof(double2), xs, m->nv * sizeof(double2),
-                                              m->nv * sizeof(double2), nrhs, cudaMemcpyDeviceToHost, s);
+            cudaError_t e = cudaMemcpy2DAsync(X, ldx * sizeof(double2), xs, n * sizeof(double2),
+                                              n * sizeof(double2), nrhs, cudaMemcpyDeviceToHost, s);
             if (e != cudaSuccess) st = cuda_error(e, "copy X back");
         }
     }

@@ -98,6 +98,12 @@ struct Mesh {
     double *d_cdl_val = nullptr;                          // double layer: correction values on C's pattern
     double *d_cdlT_val = nullptr;                         // adjoint double layer: the transposed values
     float *d_nrm_panel = nullptr;                         // double layer: FP32 normals, position-panel layout
+    // EFIE: RWG functions, one per edge (built on first use)
+    int64_t ne = 0;
+    int32_t *d_tedge = nullptr;                           // nt x 3: (edge << 1) | (minus triangle)
+    int32_t *d_etri = nullptr;                            // ne x 2: 3 t + j of the plus and the minus triangle
+    double *d_efie_blocks = nullptr;                      // npairs x 18: the two 3 x 3 correction blocks
+    std::vector<int32_t> h_edges;                         // ne x 2 vertex pairs (a < b)
     float pad = 0.0f;                                     // distance of padding points
     // mesh graph for the learned preconditioner (built on first use)
     int32_t *d_adj_ptr = nullptr, *d_adj = nullptr;       // vertex neighbours over mesh edges
@@ -168,6 +174,17 @@ gyps_status far_tc(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, d
                    cudaStream_t s);
 cudaError_t launch_near_spmv(const Mesh &m, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
                              cudaStream_t s);
+
+// Far sums over all quadrature points as targets from densities prepared by the caller:
+// an FP32 panel of R = 1, 2, 4 or 8 columns (added into v), or FP64 columns [c0, c0 + w), w <= 4.
+gyps_status far32_panel(Mesh *m, double k, const float *panel, int R, double2 *v, int64_t ldv, cudaStream_t s);
+gyps_status far64_cols(Mesh *m, double k, const double2 *u64, int64_t ldu, int c0, int w, double2 *v, int64_t ldv,
+                       cudaStream_t s);
+// EFIE with RWG functions: topology and correction (once per mesh; INVALID for an open or
+// inconsistently oriented mesh) and Y = sign T X (device pointers, ne x nrhs)
+gyps_status efie_prepare(Mesh *m, cudaStream_t s);
+gyps_status efie_apply_device(Mesh *m, double k, double sign, int nrhs, const double2 *X, int64_t ldx, double2 *Y,
+                              int64_t ldy, int prec, cudaStream_t s);
 
 // a2 in FP32: the density panel of columns c0 .. c0+w-1 (w = 1, 2, 4 or 8)
 cudaError_t launch_interp32(const Mesh *m, const double2 *X, int64_t ldx, int c0, int w, float *panel, cudaStream_t s);

@@ -140,6 +140,9 @@ WORKLOADS = {
     "sphere642_k5_q3_dense": dict(level=3, q=3, k=5.0, dirs=[(0.0, 0.0, 1.0)], tol=1e-8),
     "sphere10242_k16_q7": dict(level=5, q=7, k=16.0, dirs=[(1.0, 0.0, 0.0)], tol=1e-6),
     "sphere163842_k64_q3_r16": dict(level=7, q=3, k=64.0, ndirs=16, seed=7, tol=1e-6),
+    # EFIE (electromagnetic listing after Sec. 6.4): RWG on the 20480-triangle sphere,
+    # x-polarised plane wave along z
+    "efie_sphere10242_k8_q3": dict(level=5, q=3, k=8.0, dirs=[(0.0, 0.0, 1.0)], pols=[(1.0, 0.0, 0.0)], tol=1e-6),
 }
 
 

@@ -29,3 +29,13 @@ def test_bench_mie_scattered_field_cancels_the_incident_wave_on_the_sphere():
     for k, d in ((5.0, np.array([0.0, 0.0, 1.0])), (16.0, np.array([1.0, 0.0, 0.0]))):
         s = bench.mie_scattered_sphere(k, d, pts)
         assert np.max(np.abs(s + np.exp(1j * k * pts @ d))) < 1e-9
+
+
+def test_bench_pec_mie_matches_the_oracle():
+    import bench
+    import oracle
+    mu = np.cos(np.linspace(0.05, np.pi - 0.05, 9))
+    for k in (1.0, 8.0):
+        a1, a2 = bench.mie_pec_sphere(k, mu)
+        b1, b2 = oracle.mie_pec_amplitudes(k, mu)
+        assert np.abs(a1 - b1).max() < 1e-12 * np.abs(b1).max() and np.abs(a2 - b2).max() < 1e-12 * np.abs(b2).max()
