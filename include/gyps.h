@@ -44,7 +44,7 @@ typedef enum {
     GYPS_ERR_OOM = 3,           /* device allocation failed */
     GYPS_ERR_NOT_CONVERGED = 4, /* GMRES hit maxit; X holds the last iterate */
     GYPS_ERR_NAN = 5,           /* a non-finite value appeared in the solve */
-    GYPS_ERR_TIMEOUT = 6,       /* a device wait exceeded its iteration limit */
+    GYPS_ERR_TIMEOUT = 6,       /* a device wait exceeded its iteration limit, or GMRES its wall-clock limit */
     GYPS_ERR_UNSUPPORTED = 7    /* option not available on this device/build */
 } gyps_status;
 
@@ -329,7 +329,10 @@ typedef struct {
     int32_t max_refine;  /* refinement sweeps when the check exceeds tol (0 = none) */
     gyps_precond_t precond; /* NULL, or a learned preconditioner: flexible GMRES with z = M(q) */
     int32_t formulation; /* gyps_formulation (0: single layer) */
-    double eta;          /* coupling of the Brakhage-Werner operator (e.g. k); unused otherwise */
+    double eta;          /* coupling of the combined-field operators (e.g. k); unused otherwise */
+    double timeout_ms;   /* wall-clock limit of the solve (0 = none): checked before every inner
+                            iteration; when it passes, the cycle ends with the iterations done, the
+                            true residual is computed and TIMEOUT is returned unless it meets tol */
 } gyps_gmres_opts;
 
 /* GMRES report, HOST.  Arrays are caller-owned, length nrhs, may be NULL. */
@@ -368,7 +371,8 @@ typedef struct {
  * current iterate) and the report says so.  The check-precision residual judges the result either way.
  * The learned preconditioner models V: with the combined-field operators it is
  * UNSUPPORTED.
- * Returns NOT_CONVERGED (X = last iterate) when a column misses tol, NAN
+ * Returns NOT_CONVERGED (X = last iterate) when a column misses tol, TIMEOUT
+ * (X = last iterate, report filled) when opts->timeout_ms passed first, NAN
  * when a non-finite value appears.
  */
 gyps_status gyps_gmres_solve(gyps_mesh_t mesh, double k, int nrhs, const void *F, int64_t ldf,

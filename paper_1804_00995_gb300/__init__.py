@@ -68,7 +68,7 @@ class _GmresOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("check_prec", ctypes.c_int32), ("use_x0", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("precond", ctypes.c_void_p), ("formulation", ctypes.c_int32),
-                ("eta", ctypes.c_double)]
+                ("eta", ctypes.c_double), ("timeout_ms", ctypes.c_double)]
 
 
 class _GmresReport(ctypes.Structure):
@@ -570,11 +570,13 @@ FORMULATION = {"sl": 0, "bw": 1, "cfie": 2, "efie": 3}
 
 def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, maxit: int = 1000,
                 prec: str = "fp32", check_prec: str = "fp64", x0=None, max_refine: int = 3, raise_on_fail=False,
-                precond: "Precond" = None, stream=None, formulation: str = "sl", eta: float = None):
+                precond: "Precond" = None, stream=None, formulation: str = "sl", eta: float = None,
+                timeout_ms: float = 0.0):
     """Solves A X = F (gyps_gmres_solve), A = V ("sl"), 1/2 M + K - i eta V ("bw"),
     1/2 M + K' - i eta V ("cfie"; F from rhs_planewave_cfie with the same eta) or -T
     ("efie"; RWG coefficients, F from rhs_planewave_efie); eta defaults to k, or 1 at
-    k = 0.  Returns (X, GmresReport)."""
+    k = 0.  timeout_ms > 0 bounds the wall-clock time (status TIMEOUT, X = last iterate).
+    Returns (X, GmresReport); NOT_CONVERGED and TIMEOUT raise only with raise_on_fail."""
     if eta is None:
         eta = float(k) if k > 0 else 1.0
     n = rwg_edges(mesh, stream)[0] if formulation == "efie" else mesh.nv
@@ -588,7 +590,7 @@ def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, 
         x = _empty_colmajor(n, nrhs, f.device)
     opts = _GmresOpts(float(tol), int(restart), int(maxit), PREC[prec], PREC[check_prec], 1 if x0 is not None else 0,
                       int(max_refine), precond.handle.value if precond is not None else None,
-                      FORMULATION[formulation], float(eta))
+                      FORMULATION[formulation], float(eta), float(timeout_ms))
     est = np.zeros(nrhs)
     tru = np.zeros(nrhs)
     conv = np.zeros(nrhs, dtype=np.int32)
@@ -597,7 +599,12 @@ def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, 
                        conv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     code = load().gyps_gmres_solve(mesh.handle, float(k), nrhs, f.data_ptr(), ldf, x.data_ptr(), n,
                                    ctypes.byref(opts), ctypes.byref(rep), _stream(stream))
-    if code not in (0, 4) or (code == 4 and raise_on_fail):
+    wall_clock = False
+    if code == 6:  # TIMEOUT: GMRES's own wall-clock limit, or a device wait that ran out (always raised)
+        buf = ctypes.create_string_buffer(512)
+        load().gyps_last_error(buf, 512)
+        wall_clock = b"wall-clock" in buf.value
+    if code not in (0, 4, 6) or (code == 6 and not wall_clock) or (code in (4, 6) and raise_on_fail):
         _check(code)
     report = GmresReport(rep.iterations, rep.applies, rep.check_applies, rep.refinements, rep.precond_fallback, est,
                          tru, conv.astype(bool), _STATUS[code])

@@ -6,6 +6,7 @@
 // the residual equation is solved again (iterative refinement) while it is
 // above tolerance.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -184,6 +185,14 @@ struct Solver {
     int fallback = 0;
     int form = GYPS_FORM_SINGLE_LAYER;
     double eta = 0.0;
+    // wall-clock limit (timeout_ms > 0): checked before every inner iteration
+    bool has_deadline = false, timed_out = false;
+    std::chrono::steady_clock::time_point deadline;
+    bool past_deadline()
+    {
+        if (has_deadline && !timed_out && std::chrono::steady_clock::now() >= deadline) timed_out = true;
+        return timed_out;
+    }
 
     // Y = A X for the system's operator A: V (first kind), 1/2 M + K - i eta V
     // (Brakhage-Werner), 1/2 M + K' - i eta V (direct combined field), all
@@ -291,6 +300,10 @@ struct Solver {
             bool dropped = false;          // preconditioner dropped inside this cycle
             const bool cycle_pre = pre_on;
             for (; j < m && budget > 0; ++j) {
+                if (past_deadline()) {  // finish this cycle with the iterations done, then stop
+                    budget = 0;
+                    break;
+                }
                 double2 *qj = w.Q + (size_t)j * nv * nrhs;
                 double2 *qn = w.Q + (size_t)(j + 1) * nv * nrhs;
                 const double2 *vin = qj;
@@ -423,6 +436,11 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
     S.nv = n;
     S.form = o.formulation;
     S.eta = o.eta;
+    if (o.timeout_ms > 0.0) {
+        S.has_deadline = true;
+        S.deadline = std::chrono::steady_clock::now() +
+                     std::chrono::microseconds((int64_t)std::min(o.timeout_ms * 1e3, 9.0e15));
+    }
     S.grid_v = dim3((unsigned)((n + 255) / 256), (unsigned)nrhs);
     S.grid_r = dim3((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)nrhs);
     const size_t blk = (size_t)n * nrhs * sizeof(double2);
@@ -461,7 +479,7 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
     if (o.check_prec != o.prec)
         for (int c = 0; c < nrhs; ++c) tol_first[c] *= 0.5;
     GYPS_TRY(S.solve(F, ldf, X, ldx, !o.use_x0, tol_first, o.prec, budget, est));
-    budget = o.maxit - S.iters;
+    budget = S.timed_out ? 0 : o.maxit - S.iters;
 
     std::vector<double> tres;
     int refinements = 0;
@@ -471,7 +489,7 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
         GYPS_TRY(S.norms(S.w.R, tres));
         bool all = true;
         for (int c = 0; c < nrhs; ++c) all = all && tres[c] <= tol_abs[c];
-        if (all || refinements >= o.max_refine || budget <= 0) break;
+        if (all || refinements >= o.max_refine || budget <= 0 || S.past_deadline()) break;
         // solve V D = R in the working precision, then X += D
         std::vector<double> tol_d(nrhs);
         for (int c = 0; c < nrhs; ++c) tol_d[c] = 0.5 * tol_abs[c];
@@ -510,6 +528,7 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
             if (rep->converged) rep->converged[c] = tres[c] <= tol_abs[c];
         }
     }
+    if (!ok && S.timed_out) return set_error(GYPS_ERR_TIMEOUT, "GMRES stopped at its wall-clock limit");
     if (!ok) return set_error(GYPS_ERR_NOT_CONVERGED, "GMRES did not reach the tolerance on every column");
     return GYPS_OK;
 }
@@ -528,7 +547,8 @@ extern "C" gyps_status gyps_gmres_solve(gyps_mesh_t h, double k, int nrhs, const
     if (nrhs < 1 || nrhs > 4096) return set_error(GYPS_ERR_INVALID, "nrhs must be in 1..4096");
     if (!std::isfinite(k) || k < 0.0) return set_error(GYPS_ERR_INVALID, "k must be finite and >= 0");
     const gyps_gmres_opts &o = *opts;
-    if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 4096 || o.maxit < 1 || o.max_refine < 0)
+    if (!(o.tol > 0.0) || o.restart < 1 || o.restart > 4096 || o.maxit < 1 || o.max_refine < 0 ||
+        !(o.timeout_ms >= 0.0))
         return set_error(GYPS_ERR_INVALID, "bad GMRES options");
     if (o.formulation != GYPS_FORM_SINGLE_LAYER && o.formulation != GYPS_FORM_BRAKHAGE_WERNER &&
         o.formulation != GYPS_FORM_DIRECT_CFIE && o.formulation != GYPS_FORM_EFIE)

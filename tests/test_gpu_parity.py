@@ -271,3 +271,24 @@ def test_sphere10242_k16_q7_gmres_against_mie(g):
     e = lam - ref
     err = np.sqrt(np.real(e.conj() @ (mm @ e)) / np.real(ref.conj() @ (mm @ ref)))
     assert err < 0.05, err
+
+
+def test_gmres_wall_clock_limit(g):
+    """timeout_ms: a limit that passes before the first inner iteration returns
+    TIMEOUT with the report filled and X finite; a generous limit changes nothing."""
+    v, t = synth.icosphere(3)
+    gm = g.Mesh(v, t, 3)
+    F = g.rhs_planewave(gm, 5.0, [[0.0, 0.0, 1.0]])
+    x, rep = g.gmres_solve(gm, 5.0, F, tol=1e-12, restart=50, maxit=500, prec="fp32", check_prec="fp64",
+                           timeout_ms=1e-6)
+    assert rep.status == "TIMEOUT" and rep.iterations <= 1 and not rep.converged.any()
+    assert torch.isfinite(torch.view_as_real(x)).all() and np.isfinite(rep.true_residual).all()
+    with pytest.raises(g.GypsError) as e:
+        g.gmres_solve(gm, 5.0, F, tol=1e-12, prec="fp32", timeout_ms=1e-6, raise_on_fail=True)
+    assert e.value.status == "TIMEOUT"
+    x2, rep2 = g.gmres_solve(gm, 5.0, F, tol=1e-8, restart=200, maxit=500, prec="fp32", check_prec="fp64",
+                             timeout_ms=6e5)
+    assert rep2.status == "OK" and rep2.converged.all()
+    with pytest.raises(g.GypsError) as e:
+        g.gmres_solve(gm, 5.0, F, timeout_ms=-1.0)
+    assert e.value.status == "INVALID"
