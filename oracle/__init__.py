@@ -28,6 +28,9 @@ It follows the paper's formulation step by step:
   the vector and divergence parts of ``T`` through the same kernel, their
   '[1/r]' corrections from the P1 closed form, and the Mie amplitudes of the
   perfectly conducting sphere.
+* Its MFIE part ``nxK`` (kernel grad_y exp(ikr)/r, 'grady[1/r]' correction from
+  the closed form of int lambda (x - y)/R^3) and the combined LHS / RHS of the
+  listing, -beta T + (1 - beta)(Id/2 - nxK).
 
 Readings where the paper is silent (all listed with the design notes): the
 3-point rule is the interior (2/3, 1/6, 1/6) rule; "close enough" means sharing
@@ -90,6 +93,11 @@ def _load():
                                                  ctypes.c_double, ctypes.c_int64, dp, dp]
             lib.or_p1_dn_inv_r.argtypes = [dp, dp, dp, dp, dp]
             lib.or_efie_near_blocks.argtypes = [dp, i32p, dp, ctypes.c_int, ctypes.c_int64, i64p, i64p, dp, dp]
+            lib.or_p1_grad_inv_r.argtypes = [dp, dp, dp, dp, dp]
+            lib.or_p1_grad_inv_r.restype = None
+            lib.or_grad_cross_matvec.argtypes = [ctypes.c_int64, dp, i64p, ctypes.c_int64, dp, i64p, ctypes.c_double,
+                                                 ctypes.c_int64, dp, dp]
+            lib.or_mfie_near_blocks.argtypes = [dp, i32p, dp, ctypes.c_int, ctypes.c_int64, i64p, i64p, dp]
             lib.or_p1_dn_inv_r.restype = None
             lib.or_dl_near_blocks.argtypes = [dp, i32p, ctypes.c_int, ctypes.c_int64, i64p, i64p, dp]
             lib.or_num_threads.restype = ctypes.c_int
@@ -294,6 +302,15 @@ def adl_kernel_matvec(xt, nrm_t, tid, ys, u, k):
     lib.or_adl_kernel_matvec(nt, _dp(xt), _dp(nrm_t), tidp, ns, _dp(ys), float(k), nrhs,
                              _dp(uflat.view(np.float64)), _dp(vflat.view(np.float64)))
     return vflat.reshape((nt, nrhs), order="F")
+
+
+def p1_grad_inv_r(x, p0, p1, p2):
+    """int_T lambda_j(y) (x - y)/|x - y|^3 dy, (3, 3): row j, column the component (closed form)."""
+    lib = _load()
+    out = np.zeros(9)
+    args = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, p0, p1, p2)]
+    lib.or_p1_grad_inv_r(*[_dp(a) for a in args], _dp(out))
+    return out.reshape(3, 3)
 
 
 def p1_dn_inv_r(x, p0, p1, p2):
@@ -635,6 +652,47 @@ def efie_near_matrices_py(vtx, tri, q):
     return CA, CB
 
 
+def grad_cross_matvec(xt, tri_t, ys, tri_s, u, k):
+    """v_t = sum_l F(r_tl) (x_t - y_l) x u_l, F = (1 - ikr) exp(ikr)/r^3 (grad_y exp(ikr)/r =
+    F (x - y)), pairs with tri_t[t] == tri_s[l] left out; u: (ns, 3, nrhs) complex -> (nt, 3, nrhs)."""
+    lib = _load()
+    xt = np.ascontiguousarray(xt, dtype=np.float64)
+    ys = np.ascontiguousarray(ys, dtype=np.float64)
+    tri_t = np.ascontiguousarray(tri_t, dtype=np.int64)
+    tri_s = np.ascontiguousarray(tri_s, dtype=np.int64)
+    u = np.asarray(u, dtype=np.complex128)
+    nt, ns, nrhs = xt.shape[0], ys.shape[0], u.shape[2]
+    uflat = np.ascontiguousarray(np.transpose(u, (2, 1, 0)).reshape(-1))   # ((3 j + c) ns + l)
+    vflat = np.zeros(nt * 3 * nrhs, dtype=np.complex128)
+    lib.or_grad_cross_matvec(nt, _dp(xt), _i64p(tri_t), ns, _dp(ys), _i64p(tri_s), float(k), nrhs,
+                             _dp(uflat.view(np.float64)), _dp(vflat.view(np.float64)))
+    return np.transpose(vflat.reshape(nrhs, 3, nt), (2, 1, 0))
+
+
+def mfie_near_matrix(vtx, tri, q):
+    """C (nE, nE) real, the MFIE's 'grady[1/r]' correction (times 1/(4pi)) on every ordered
+    pair of triangles sharing a vertex (0 inside one triangle; C, or_mfie_near_blocks)."""
+    lib = _load()
+    vtx = np.ascontiguousarray(vtx, dtype=np.float64)
+    tri32 = np.ascontiguousarray(tri, dtype=np.int32)
+    nv = vtx.shape[0]
+    edges, tedge, tsign = rwg_topology(tri32, nv)
+    tsign = np.ascontiguousarray(tsign, dtype=np.float64)
+    pa, pb = near_pairs(tri32, nv)
+    pa = np.ascontiguousarray(pa, dtype=np.int64)
+    pb = np.ascontiguousarray(pb, dtype=np.int64)
+    blk = np.zeros((pa.shape[0], 3, 3))
+    if lib.or_mfie_near_blocks(_dp(vtx), _i32p(tri32), _dp(tsign), int(q), pa.shape[0], _i64p(pa), _i64p(pb),
+                               _dp(blk)) != 0:
+        raise ValueError("bad quadrature order")
+    rows = np.repeat(tedge[pa], 3, axis=1).reshape(-1)
+    cols = np.tile(tedge[pb], (1, 3)).reshape(-1)
+    ne = edges.shape[0]
+    c = sp.coo_matrix((blk.reshape(-1), (rows, cols)), shape=(ne, ne)).tocsr()
+    c.sum_duplicates()
+    return c
+
+
 class EfieMesh(Mesh):
     """The mesh with the RWG space ``fem(mesh, 'RWG')`` on ``dom(mesh, q)``."""
 
@@ -670,6 +728,53 @@ class EfieMesh(Mesh):
         CA, CB = self.efie_near
         y = 1j * k / (4.0 * np.pi) * (vec + CA @ x) - 1j / (4.0 * np.pi * k) * (dv + CB @ x)
         return y[:, 0] if one else y
+
+    @property
+    def mfie_near(self):
+        if getattr(self, "_cm", None) is None:
+            self._cm = mfie_near_matrix(self.vtx, self.tri, self.q)
+        return self._cm
+
+    def rwg_mass(self):
+        """Id = int phi_m . phi_n by the domain's rule (the listing's integral(sigma, Vh, Vh))."""
+        return sum(self.rwg[c].T @ sp.diags(self.w) @ self.rwg[c] for c in range(3)).tocsr()
+
+    def mfie_apply(self, k, x):
+        """nxK x = (1/4pi) sum_k w_k (n_k x phi_m(x_k)) . sum_l F (x_k - y_l) x (w_l J(y_l)) + C x,
+        J = sum_n x_n phi_n, F (x - y) = grad_y exp(ik|x-y|)/|x-y| (the listing's nxK)."""
+        x = np.asarray(x, dtype=np.complex128)
+        one = x.ndim == 1
+        if one:
+            x = x[:, None]
+        u = np.stack([self.w[:, None] * (self.rwg[c] @ x) for c in range(3)], axis=1)   # (nq, 3, nrhs)
+        tid = np.repeat(np.arange(self.nt), self.q)
+        v = grad_cross_matvec(self.x, tid, self.x, tid, u, k)
+        n = self.point_normals()
+        vxn = np.cross(v, n[:, :, None], axis=1)             # (n x phi) . v = phi . (v x n)
+        y = sum(self.rwg[c].T @ (self.w[:, None] * vxn[:, c, :]) for c in range(3)) / (4.0 * np.pi)
+        y = y + self.mfie_near @ x
+        return y[:, 0] if one else y
+
+    def emcfie_apply(self, k, beta, x):
+        """The listing's LHS: -beta T + (1 - beta) (1/2 Id - nxK)."""
+        x = np.asarray(x, dtype=np.complex128)
+        out = (1.0 - beta) * (0.5 * (self.rwg_mass() @ x) - self.mfie_apply(k, x))
+        if beta != 0.0:
+            out = out - beta * self.efie_apply(k, x)
+        return out
+
+    def rhs_planewave_mfie(self, k, dirs, pols):
+        """int (n x phi_m) . H_inc = int phi_m . (H_inc x n), H_inc = (d x p) exp(ik d.x)."""
+        dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+        pols = np.atleast_2d(np.asarray(pols, dtype=np.float64))
+        hp = np.cross(dirs, pols)                             # (nd, 3)
+        e = np.exp(1j * k * (self.x @ dirs.T))                # (nq, nd)
+        hxn = np.cross(hp[None, :, :], self.point_normals()[:, None, :])   # (nq, nd, 3)
+        return np.asarray(sum(self.rwg[c].T @ (self.w[:, None] * e * hxn[:, :, c]) for c in range(3)))
+
+    def rhs_planewave_emcfie(self, k, beta, dirs, pols):
+        """The listing's RHS: beta int phi . E_inc - (1 - beta) int (n x phi) . H_inc."""
+        return beta * self.rhs_planewave_efie(k, dirs, pols) - (1.0 - beta) * self.rhs_planewave_mfie(k, dirs, pols)
 
     def rhs_planewave_efie(self, k, dirs, pols):
         """F_m = int phi_m . p exp(ik d.x) by the domain's rule, one column per

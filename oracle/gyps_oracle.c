@@ -291,6 +291,76 @@ int or_near_blocks(const double *vtx, const int32_t *tri, int q,
     return 0;
 }
 
+/* int_T lambda_j(y) (x - y) / |x - y|^3 dy for j = 0, 1, 2 over the flat triangle T
+ * (out[3 j + c], the gradient in y of the P1 single layer's kernel), in closed form.
+ * With n the unit normal (P1 - P0) x (P2 - P0) / |.|, h = n . (x - P0), rho the
+ * projection of x onto the plane of T and s = y - rho (in the plane):
+ *   normal part    n h int_T lambda_j / R^3                  (the double layer's closed form),
+ *   in-plane part  int_T lambda_j (-s) / R^3
+ *                = lambda_j(rho) sum_e m_e L_e - g_j I0 + sum_e (g_j . m_e) E_e,
+ * g_j = grad lambda_j, m_e the outward in-plane unit normal of edge e, L_e = int_e 1/R,
+ * I0 = int_T 1/R, E_e = int_e (y - rho)/R = (A - rho) L_e + u (R_B - R_A - l_A L_e) for
+ * the edge from A to B with unit direction u and l_A = u . (A - rho).  Both come from the
+ * divergence theorem in the plane: the in-plane gradient of 1/R is -s/R^3, and that of
+ * s_i/R is e_i/R - s_i s/R^3. */
+void or_p1_dn_inv_r(const double *x, const double *P0, const double *P1, const double *P2, double *out);
+
+void or_p1_grad_inv_r(const double *x, const double *P0, const double *P1, const double *P2, double *out)
+{
+    const double *P[3] = {P0, P1, P2};
+    double e1[3], e2[3], nn[3];
+    for (int c = 0; c < 3; ++c) {
+        e1[c] = P1[c] - P0[c];
+        e2[c] = P2[c] - P0[c];
+    }
+    cross3(e1, e2, nn);
+    double twoA = sqrt(dot3(nn, nn));
+    double n[3] = {nn[0] / twoA, nn[1] / twoA, nn[2] / twoA};
+    double xp0[3] = {x[0] - P0[0], x[1] - P0[1], x[2] - P0[2]};
+    double h = dot3(xp0, n);
+    double rho[3] = {x[0] - h * n[0], x[1] - h * n[1], x[2] - h * n[2]};
+    double I[3], D[3];
+    or_p1_inv_r(x, P0, P1, P2, I);
+    or_p1_dn_inv_r(x, P0, P1, P2, D);
+    double I0 = I[0] + I[1] + I[2];
+    double ML[3] = {0.0, 0.0, 0.0}, M[3][3], E[3][3];
+    for (int e = 0; e < 3; ++e) {
+        const double *A = P[e], *B = P[(e + 1) % 3];
+        double u[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+        double len = sqrt(dot3(u, u));
+        u[0] /= len; u[1] /= len; u[2] /= len;
+        cross3(u, n, M[e]);
+        double ar[3] = {A[0] - rho[0], A[1] - rho[1], A[2] - rho[2]};
+        double br[3] = {B[0] - rho[0], B[1] - rho[1], B[2] - rho[2]};
+        double la = dot3(ar, u), lb = dot3(br, u);
+        double p = dot3(ar, M[e]);
+        double R02 = p * p + h * h;
+        double xa[3] = {x[0] - A[0], x[1] - A[1], x[2] - A[2]};
+        double xb[3] = {x[0] - B[0], x[1] - B[1], x[2] - B[2]};
+        double Ra = sqrt(dot3(xa, xa)), Rb = sqrt(dot3(xb, xb));
+        double L = 0.0;
+        if (R02 > 1e-30 * twoA) L = log(r_plus_l(Rb, lb, R02) / r_plus_l(Ra, la, R02));
+        for (int c = 0; c < 3; ++c) {
+            ML[c] += M[e][c] * L;
+            E[e][c] = ar[c] * L + u[c] * (Rb - Ra - la * L);
+        }
+    }
+    for (int j = 0; j < 3; ++j) {
+        const double *A = P[(j + 1) % 3], *B = P[(j + 2) % 3];
+        double ab[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+        double g[3];
+        cross3(n, ab, g);
+        g[0] /= twoA; g[1] /= twoA; g[2] /= twoA;
+        double rj[3] = {rho[0] - P[j][0], rho[1] - P[j][1], rho[2] - P[j][2]};
+        double lam = 1.0 + dot3(g, rj);
+        for (int c = 0; c < 3; ++c) {
+            double w = lam * ML[c] - g[c] * I0;
+            for (int e = 0; e < 3; ++e) w += dot3(g, M[e]) * E[e][c];
+            out[3 * j + c] = n[c] * D[j] + w;
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* EFIE correction blocks with RWG functions on a near pair (a, b): for the   */
 /* local edges i of a and j of b (edge j of a triangle joins its vertices    */
@@ -377,6 +447,139 @@ int or_efie_near_blocks(const double *vtx, const int32_t *tri, const double *tsi
             blkA[9 * p + e] = bA[e];
             blkB[9 * p + e] = bB[e];
         }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* MFIE part of the electromagnetic listing (nxK = integral(sigma, sigma,    */
+/* nx(Vh), grady[exp(ikr)/r], Vh) / (4 pi) + regularize(..., 'grady[1/r]')):  */
+/*   grad_y exp(ikr)/r = F(r) (x - y),  F = (1 - i k r) exp(i k r) / r^3.    */
+/* v[t] = sum_l F(r_tl) (x_t - y_l) x u_l  (3-vectors, cross product), with  */
+/* the pairs inside one triangle left out (tri_t[t] == tri_s[l]): their      */
+/* vector is normal to the triangle and meets an in-plane test function.     */
+/*   u: ns x 3 x nrhs complex (u[((3 j + c) ns + l)]), v: nt x 3 x nrhs.    */
+/* ------------------------------------------------------------------------ */
+int or_grad_cross_matvec(int64_t nt, const double *xt, const int64_t *tri_t, int64_t ns, const double *ys,
+                         const int64_t *tri_s, double k, int64_t nrhs, const double *u, double *v)
+{
+    #pragma omp parallel
+    {
+        double *acc = (double *)calloc((size_t)(6 * nrhs), sizeof(double));
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t t = 0; t < nt; ++t) {
+            for (int64_t j = 0; j < 6 * nrhs; ++j) acc[j] = 0.0;
+            const double *x = xt + 3 * t;
+            for (int64_t l = 0; l < ns; ++l) {
+                if (tri_t[t] == tri_s[l]) continue;
+                const double *y = ys + 3 * l;
+                double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+                double r = sqrt(dot3(d, d));
+                double c = cos(k * r), sn = sin(k * r);
+                double fr = (c + k * r * sn) / (r * r * r), fi = (sn - k * r * c) / (r * r * r);
+                for (int64_t j = 0; j < nrhs; ++j) {
+                    double ur[3], ui[3];
+                    for (int a = 0; a < 3; ++a) {
+                        ur[a] = u[2 * ((3 * j + a) * ns + l)];
+                        ui[a] = u[2 * ((3 * j + a) * ns + l) + 1];
+                    }
+                    double cr[3], ci[3];
+                    cross3(d, ur, cr);
+                    cross3(d, ui, ci);
+                    for (int a = 0; a < 3; ++a) {
+                        acc[6 * j + 2 * a] += fr * cr[a] - fi * ci[a];
+                        acc[6 * j + 2 * a + 1] += fr * ci[a] + fi * cr[a];
+                    }
+                }
+            }
+            for (int64_t j = 0; j < nrhs; ++j)
+                for (int a = 0; a < 3; ++a) {
+                    v[2 * ((3 * j + a) * nt + t)] = acc[6 * j + 2 * a];
+                    v[2 * ((3 * j + a) * nt + t) + 1] = acc[6 * j + 2 * a + 1];
+                }
+        }
+        free(acc);
+    }
+    return 0;
+}
+
+/* MFIE correction blocks on the near pair (a, b), a != b (pairs inside one
+ * triangle give 0): for local RWG edges i of a and j of b,
+ *   blk[i][j] = (1/4pi) sum_{k in a} w_k (n_a x f_i(x_k)) .
+ *               (int_b (x_k - y)/R^3 x f_j(y) dy - sum_{l in b} w_l (x_k - y_l)/r^3 x f_j(y_l)),
+ * int_b (x - y)/R^3 x f_j = c_j sum_m (int_b lambda_m (x - y)/R^3) x (P_m - P_j),
+ * f_j = c_j (y - P_j), c_j = s l_j / (2 A_b).   blk: npairs x 3 x 3. */
+int or_mfie_near_blocks(const double *vtx, const int32_t *tri, const double *tsign, int q, int64_t npairs,
+                        const int64_t *pa, const int64_t *pb, double *blk)
+{
+    double bary[21], wr[7];
+    if (or_quad_rule(q, bary, wr) != 0) return -1;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < npairs; ++p) {
+        int64_t a = pa[p], b = pb[p];
+        double out[9] = {0};
+        if (a != b) {
+            const double *A[3], *B[3];
+            for (int m = 0; m < 3; ++m) {
+                A[m] = vtx + 3 * (int64_t)tri[3 * a + m];
+                B[m] = vtx + 3 * (int64_t)tri[3 * b + m];
+            }
+            double ea[3], fa[3], na[3], eb[3], fb[3], nb[3];
+            for (int c = 0; c < 3; ++c) {
+                ea[c] = A[1][c] - A[0][c]; fa[c] = A[2][c] - A[0][c];
+                eb[c] = B[1][c] - B[0][c]; fb[c] = B[2][c] - B[0][c];
+            }
+            cross3(ea, fa, na);
+            cross3(eb, fb, nb);
+            double two_a = sqrt(dot3(na, na)), two_b = sqrt(dot3(nb, nb));
+            double un[3] = {na[0] / two_a, na[1] / two_a, na[2] / two_a};
+            double ca[3], cb[3];
+            for (int j = 0; j < 3; ++j) {
+                double da[3], db[3];
+                for (int c = 0; c < 3; ++c) {
+                    da[c] = A[(j + 2) % 3][c] - A[(j + 1) % 3][c];
+                    db[c] = B[(j + 2) % 3][c] - B[(j + 1) % 3][c];
+                }
+                ca[j] = tsign[3 * a + j] * sqrt(dot3(da, da)) / two_a;
+                cb[j] = tsign[3 * b + j] * sqrt(dot3(db, db)) / two_b;
+            }
+            for (int kq = 0; kq < q; ++kq) {
+                double xk[3];
+                for (int c = 0; c < 3; ++c)
+                    xk[c] = bary[3 * kq] * A[0][c] + bary[3 * kq + 1] * A[1][c] + bary[3 * kq + 2] * A[2][c];
+                double wk = wr[kq] * 0.5 * two_a;
+                double V[9];
+                or_p1_grad_inv_r(xk, B[0], B[1], B[2], V);
+                for (int j = 0; j < 3; ++j) {
+                    double an[3] = {0.0, 0.0, 0.0};
+                    for (int m = 0; m < 3; ++m) {
+                        double pm[3] = {B[m][0] - B[j][0], B[m][1] - B[j][1], B[m][2] - B[j][2]};
+                        double cr[3];
+                        cross3(V + 3 * m, pm, cr);
+                        for (int c = 0; c < 3; ++c) an[c] += cb[j] * cr[c];
+                    }
+                    for (int lq = 0; lq < q; ++lq) {
+                        double yl[3];
+                        for (int c = 0; c < 3; ++c)
+                            yl[c] = bary[3 * lq] * B[0][c] + bary[3 * lq + 1] * B[1][c] + bary[3 * lq + 2] * B[2][c];
+                        double d[3] = {xk[0] - yl[0], xk[1] - yl[1], xk[2] - yl[2]};
+                        double r = sqrt(dot3(d, d));
+                        double e = wr[lq] * 0.5 * two_b / (r * r * r);
+                        double fj[3] = {cb[j] * (yl[0] - B[j][0]), cb[j] * (yl[1] - B[j][1]), cb[j] * (yl[2] - B[j][2])};
+                        double cr[3];
+                        cross3(d, fj, cr);
+                        for (int c = 0; c < 3; ++c) an[c] -= e * cr[c];
+                    }
+                    for (int i = 0; i < 3; ++i) {
+                        double fi[3] = {ca[i] * (xk[0] - A[i][0]), ca[i] * (xk[1] - A[i][1]), ca[i] * (xk[2] - A[i][2])};
+                        double nf[3];
+                        cross3(un, fi, nf);
+                        out[3 * i + j] += wk * dot3(nf, an) / (4.0 * M_PI);
+                    }
+                }
+            }
+        }
+        for (int e = 0; e < 9; ++e) blk[9 * p + e] = out[e];
     }
     return 0;
 }

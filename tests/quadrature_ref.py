@@ -47,3 +47,31 @@ def monomial_integral(area, a, b, c):
     """int_T l1^a l2^b l3^c = 2 area a! b! c! / (a + b + c + 2)!."""
     from math import factorial
     return 2.0 * area * factorial(a) * factorial(b) * factorial(c) / factorial(a + b + c + 2)
+
+
+def inner_integral_vec(x, P, ng=60):
+    """int_T lambda_j(y) (x - y)/|x - y|^3 dy for j = 0, 1, 2: (3, 3), row j (the same
+    Duffy split about the projection of x)."""
+    P = [np.asarray(p, dtype=np.float64) for p in P]
+    x = np.asarray(x, dtype=np.float64)
+    n = np.cross(P[1] - P[0], P[2] - P[0])
+    n /= np.linalg.norm(n)
+    d = (x - P[0]) @ n
+    rho = x - d * n
+    g, wg = leggauss(ng)
+    g = (g + 1) / 2
+    wg = wg / 2
+    U, V = np.meshgrid(g, g, indexing="ij")
+    W = np.outer(wg, wg)
+    tot = np.zeros((3, 3))
+    for i in range(3):
+        a, b = P[i], P[(i + 1) % 3]
+        s = 0.5 * (np.cross(a - rho, b - rho) @ n)
+        Y = rho[None, None, :] + U[..., None] * (a - rho) + (U * V)[..., None] * (b - a)
+        D = x - Y
+        R = np.linalg.norm(D, axis=-1)
+        jac = 2.0 * s * U
+        lam = barycentric(P, Y.reshape(-1, 3))                  # (3, n)
+        f = (W * jac / R ** 3)[..., None] * D                  # (ng, ng, 3)
+        tot = tot + lam @ f.reshape(-1, 3)
+    return tot
