@@ -760,7 +760,9 @@ def run_efie(args):
     correction); once each: the FP64 and double-float applies; then GMRES to 1e-6
     on -T J = int phi . E_inc (x-polarised plane wave along z; FP32 operator,
     double-float checks) and the far field of J against the Mie amplitudes of the
-    perfectly conducting sphere (E- and H-plane, 24 directions)."""
+    perfectly conducting sphere (E- and H-plane, 24 directions); then the listing's
+    combined system -beta T + (1 - beta)(Id/2 - nxK) at beta = 0.5 for the same wave
+    (the MFIE part in FP64 for its double-float check)."""
     import torch
 
     import paper_1804_00995_gb300 as g
@@ -809,14 +811,40 @@ def run_efie(args):
                            max_refine=4, formulation="efie")
     torch.cuda.synchronize()
     t_solve = time.perf_counter() - t0
-    qp, Jq = rwg_current_at_points(g, mesh, v, t, J.cpu().numpy()[:, 0])
     th = np.linspace(0.05, np.pi - 0.05, 12)
     s1, s2 = mie_pec_sphere(k, np.cos(th))
-    err = 0.0
-    for xd, s in ((np.stack([np.sin(th), 0 * th, np.cos(th)], 1), s2), (np.stack([0 * th, np.sin(th), np.cos(th)], 1), s1)):
-        I = np.exp(-1j * k * (xd @ qp[:, :3].T)) @ (qp[:, 3:4] * Jq)
-        amp = k / (4.0 * np.pi) * np.linalg.norm(I - np.sum(I * xd, axis=1)[:, None] * xd, axis=1)
-        err = max(err, float(np.abs(amp / (np.abs(s) / k) - 1.0).max()))
+
+    def far_field_error(Jc):
+        qp, Jq = rwg_current_at_points(g, mesh, v, t, Jc)
+        e = 0.0
+        for xd, s in ((np.stack([np.sin(th), 0 * th, np.cos(th)], 1), s2),
+                      (np.stack([0 * th, np.sin(th), np.cos(th)], 1), s1)):
+            I = np.exp(-1j * k * (xd @ qp[:, :3].T)) @ (qp[:, 3:4] * Jq)
+            amp = k / (4.0 * np.pi) * np.linalg.norm(I - np.sum(I * xd, axis=1)[:, None] * xd, axis=1)
+            e = max(e, float(np.abs(amp / (np.abs(s) / k) - 1.0).max()))
+        return e
+
+    err = far_field_error(J.cpu().numpy()[:, 0])
+    # the listing's combined system at beta = 0.5 (EFIE + MFIE), same wave
+    for _ in range(2):
+        g.mfie_apply(mesh, k, x, prec="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        g.mfie_apply(mesh, k, x, prec="fp32")
+    torch.cuda.synchronize()
+    mfie_ms = (time.perf_counter() - t0) / 5 * 1e3
+    Fc = g.rhs_planewave_emcfie(mesh, k, 0.5, d[None, :], p[None, :])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Jc, repc = g.gmres_solve(mesh, k, Fc, tol=cfg["tol"], restart=300, maxit=3000, prec="fp32", check_prec="df64",
+                             max_refine=4, formulation="emcfie", eta=0.5)
+    torch.cuda.synchronize()
+    t_cfie = time.perf_counter() - t0
+    cfie = {"beta": 0.5, "seconds": t_cfie, "iterations": repc.iterations, "refinements": repc.refinements,
+            "true_residual": float(repc.true_residual[0]), "status": repc.status,
+            "far_field_max_rel_error_vs_mie": far_field_error(Jc.cpu().numpy()[:, 0]),
+            "mfie_fp32_apply_ms": mfie_ms}
     pairs = float(mesh.nq) ** 2
     achieved = pairs / (far_ms * 1e-3) / 1e9
     props = torch.cuda.get_device_properties(0)
@@ -839,6 +867,7 @@ def run_efie(args):
         "solve": {"seconds": t_solve, "iterations": rep.iterations, "refinements": rep.refinements,
                   "true_residual_df64": float(rep.true_residual[0]), "status": rep.status,
                   "far_field_max_rel_error_vs_mie": err},
+        "combined_field_solve": cfie,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -68,8 +68,10 @@ typedef enum {
                                      uniquely solvable for every k when eta > 0 */
     GYPS_FORM_DIRECT_CFIE = 2,     /* (1/2 M + K' - i eta V) X = F: X = du/dn of the total field, the same
                                      density as the first-kind system; F from gyps_rhs_planewave_cfie */
-    GYPS_FORM_EFIE = 3             /* -T J = F (the electromagnetic listing after Sec. 6.4 with beta = 1):
+    GYPS_FORM_EFIE = 3,            /* -T J = F (the electromagnetic listing after Sec. 6.4 with beta = 1):
                                      J the RWG coefficients (ne unknowns), F from gyps_rhs_planewave_efie */
+    GYPS_FORM_EM_CFIE = 4          /* (-beta T + (1 - beta)(Id/2 - nxK)) J = F, the listing's LHS with
+                                     beta = opts->eta in [0, 1]; F from gyps_rhs_planewave_emcfie */
 } gyps_formulation;
 
 /* gyps_sl_apply flags */
@@ -276,6 +278,31 @@ gyps_status gyps_rhs_planewave_efie(gyps_mesh_t mesh, double k, int nrhs, const 
                                     void *F, int64_t ldf, void *stream);
 
 /*
+ * MFIE part of the electromagnetic listing:
+ *     Y = nxK X,  nxK_mn = (1/4pi) int int (n_x x phi_m(x)) . (grad_y exp(ik|x-y|)/|x-y| x phi_n(y))
+ *                          + regularize(..., 'grady[1/r]', ...),
+ * grad_y exp(ikr)/r = (1 - ikr) exp(ikr) (x - y)/r^3 between the Gauss points (pairs inside one
+ * triangle give 0: their vector is normal to it), the correction on triangles sharing a vertex
+ * from the closed form of int lambda (x - y)/R^3 minus its Gauss sum.  The combined operator
+ *     Y = (-beta T + (1 - beta)(Id/2 - nxK)) X,   Id = int phi_m . phi_n by the mesh's rule,
+ * is the listing's LHS.  X, Y: ne x nrhs (host or device), leading dims >= ne, not
+ * overlapping; k > 0; prec GYPS_PREC_FP32 (AUTO), GYPS_PREC_FP64 or GYPS_PREC_DF64 (the MFIE
+ * part in FP64 for DF64).  Errors as gyps_efie_apply.
+ */
+gyps_status gyps_mfie_apply(gyps_mesh_t mesh, double k, int nrhs, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                            int prec, void *stream);
+gyps_status gyps_emcfie_apply(gyps_mesh_t mesh, double k, double beta, int nrhs, const void *X, int64_t ldx,
+                              void *Y, int64_t ldy, int prec, void *stream);
+
+/*
+ * The listing's RHS:  F_ej = sum_k w_k (beta phi_e . p_j - (1 - beta)(n x phi_e) . (d_j x p_j))
+ * exp(i k d_j . x_k)  (beta int phi . E_inc - (1 - beta) int (n x phi) . H_inc, H_inc = d x E_inc).
+ * Arguments as gyps_rhs_planewave_efie; beta must be finite.
+ */
+gyps_status gyps_rhs_planewave_emcfie(gyps_mesh_t mesh, double k, double beta, int nrhs, const double *dirs,
+                                      const double *pols, void *F, int64_t ldf, void *stream);
+
+/*
  * Single-layer potential at points (the radiation operator of the listing in
  * Sec. 6.4: Sdom = integral(points, S2, Gxy, Vh)/(4 pi)
  * + regularize(points, S2, '[1/r]', Vh)/(4 pi)):
@@ -329,7 +356,7 @@ typedef struct {
     int32_t max_refine;  /* refinement sweeps when the check exceeds tol (0 = none) */
     gyps_precond_t precond; /* NULL, or a learned preconditioner: flexible GMRES with z = M(q) */
     int32_t formulation; /* gyps_formulation (0: single layer) */
-    double eta;          /* coupling of the combined-field operators (e.g. k); unused otherwise */
+    double eta;          /* coupling of the combined-field operators (e.g. k); beta for GYPS_FORM_EM_CFIE */
     double timeout_ms;   /* wall-clock limit of the solve (0 = none): checked before every inner
                             iteration; when it passes, the cycle ends with the iterations done, the
                             true residual is computed and TIMEOUT is returned unless it meets tol */
@@ -355,7 +382,9 @@ typedef struct {
  * pass -F for the sound-soft problem), or with GYPS_FORM_DIRECT_CFIE,
  * A = 1/2 M + K' - i opts->eta V (gyps_cfie_apply; F from gyps_rhs_planewave_cfie),
  * or with GYPS_FORM_EFIE, A = -T (gyps_efie_apply; ne unknowns per column, F from
- * gyps_rhs_planewave_efie; FP32 / FP64 / double-float only).  Arnoldi with classical Gram-Schmidt
+ * gyps_rhs_planewave_efie; FP32 / FP64 / double-float only), or with
+ * GYPS_FORM_EM_CFIE, A = -beta T + (1 - beta)(Id/2 - nxK), beta = opts->eta
+ * (gyps_emcfie_apply; F from gyps_rhs_planewave_emcfie).  Arnoldi with classical Gram-Schmidt
  * applied twice, in FP64 on the device, Givens rotations on the host, one
  * Krylov space per column, the operator applied to all columns at once with
  * `opts->prec`.  After the

@@ -111,6 +111,12 @@ _SIGS = {
                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "gyps_rhs_planewave_efie": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
+    "gyps_mfie_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "gyps_emcfie_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "gyps_rhs_planewave_emcfie": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "gyps_bw_apply": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "gyps_sl_potential": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
@@ -414,6 +420,40 @@ def efie_apply(mesh: Mesh, k: float, X, prec: str = "fp32", stream=None):
     return y[:, 0] if one else y
 
 
+def _em_apply(mesh, fn, args, X, stream):
+    ne, _ = rwg_edges(mesh, stream)
+    one = (hasattr(X, "dim") and X.dim() == 1) or (not hasattr(X, "dim") and np.asarray(X).ndim == 1)
+    x, nrhs, ldx = _colmajor(X, ne, "X")
+    y = _empty_colmajor(ne, nrhs, x.device)
+    _check(fn(mesh.handle, *args[:-1], nrhs, x.data_ptr(), ldx, y.data_ptr(), max(y.stride(1), ne) if nrhs > 1 else ne,
+              args[-1], _stream(stream)))
+    return y[:, 0] if one else y
+
+
+def mfie_apply(mesh: Mesh, k: float, X, prec: str = "fp32", stream=None):
+    """Y = nxK X, the MFIE part of the electromagnetic listing (gyps_mfie_apply)."""
+    return _em_apply(mesh, load().gyps_mfie_apply, (float(k), PREC[prec]), X, stream)
+
+
+def emcfie_apply(mesh: Mesh, k: float, beta: float, X, prec: str = "fp32", stream=None):
+    """Y = (-beta T + (1 - beta)(Id/2 - nxK)) X, the listing's LHS (gyps_emcfie_apply)."""
+    return _em_apply(mesh, load().gyps_emcfie_apply, (float(k), float(beta), PREC[prec]), X, stream)
+
+
+def rhs_planewave_emcfie(mesh: Mesh, k: float, beta: float, dirs, pols, device=None, stream=None):
+    """F (ne, nrhs): beta int phi . E_inc - (1 - beta) int (n x phi) . H_inc (gyps_rhs_planewave_emcfie)."""
+    ne, _ = rwg_edges(mesh, stream)
+    dirs = np.ascontiguousarray(np.atleast_2d(np.asarray(dirs, dtype=np.float64)))
+    pols = np.ascontiguousarray(np.atleast_2d(np.asarray(pols, dtype=np.float64)))
+    if dirs.shape != pols.shape:
+        raise ValueError("one polarisation per direction")
+    dev = mesh.device if device is None else device
+    f = _empty_colmajor(ne, dirs.shape[0], dev)
+    _check(load().gyps_rhs_planewave_emcfie(mesh.handle, float(k), float(beta), dirs.shape[0], dirs.ctypes.data,
+                                            pols.ctypes.data, f.data_ptr(), ne, _stream(stream)))
+    return f
+
+
 def rhs_planewave_efie(mesh: Mesh, k: float, dirs, pols, device=None, stream=None):
     """F (ne, nrhs): F_ej = int phi_e . p_j exp(i k d_j . x) (gyps_rhs_planewave_efie)."""
     ne, _ = rwg_edges(mesh, stream)
@@ -565,7 +605,7 @@ class GmresReport:
     status: str
 
 
-FORMULATION = {"sl": 0, "bw": 1, "cfie": 2, "efie": 3}
+FORMULATION = {"sl": 0, "bw": 1, "cfie": 2, "efie": 3, "emcfie": 4}
 
 
 def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, maxit: int = 1000,
@@ -574,12 +614,13 @@ def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, 
                 timeout_ms: float = 0.0):
     """Solves A X = F (gyps_gmres_solve), A = V ("sl"), 1/2 M + K - i eta V ("bw"),
     1/2 M + K' - i eta V ("cfie"; F from rhs_planewave_cfie with the same eta) or -T
-    ("efie"; RWG coefficients, F from rhs_planewave_efie); eta defaults to k, or 1 at
+    ("efie"; RWG coefficients, F from rhs_planewave_efie), or -eta T + (1 - eta)(Id/2 - nxK)
+    ("emcfie", eta = beta; F from rhs_planewave_emcfie); eta defaults to k, or 1 at
     k = 0.  timeout_ms > 0 bounds the wall-clock time (status TIMEOUT, X = last iterate).
     Returns (X, GmresReport); NOT_CONVERGED and TIMEOUT raise only with raise_on_fail."""
     if eta is None:
-        eta = float(k) if k > 0 else 1.0
-    n = rwg_edges(mesh, stream)[0] if formulation == "efie" else mesh.nv
+        eta = 0.5 if formulation == "emcfie" else (float(k) if k > 0 else 1.0)
+    n = rwg_edges(mesh, stream)[0] if formulation in ("efie", "emcfie") else mesh.nv
     f, nrhs, ldf = _colmajor(F, n, "F")
     if x0 is not None:
         x, _, _ = _colmajor(x0.clone() if hasattr(x0, "clone") else x0, n, "x0")

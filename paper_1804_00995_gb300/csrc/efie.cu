@@ -22,9 +22,10 @@ namespace gyps {
 
 constexpr double kInv4PiE = 0.0795774715459476678844418816862571810;
 
-// local edge data of triangle t: P (3 vertices), area, s l / (2A) per local edge
+// local edge data of triangle t: P (3 vertices), unit normal, s l / (2A) per local edge
 struct RwgTri {
     double3 P[3];
+    double3 n;
     double c[3];
 };
 
@@ -35,6 +36,7 @@ __device__ inline RwgTri rwg_tri(const double *vtx, const int32_t *tri, const in
     for (int m = 0; m < 3; ++m) r.P[m] = ld3(vtx, tri[3 * t + m]);
     const double3 n = cross(r.P[1] - r.P[0], r.P[2] - r.P[0]);
     const double two_area = sqrt(dot(n, n));
+    r.n = (1.0 / two_area) * n;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const double3 e = r.P[(j + 2) % 3] - r.P[(j + 1) % 3];
@@ -223,16 +225,18 @@ __global__ void efie_project_kernel(const double *vtx, const int32_t *tri, const
     Y[e + (int64_t)c * ldy] = make_double2(-ca * ai + cb * bi, ca * ar - cb * br);
 }
 
-// F[e, j] = sum_k w_k phi_e(x_k) . p_j exp(i k d_j . x_k); dp: nrhs x 6 (d, p).
+// F[e, j] = sum_k w_k (beta phi_e(x_k) . p_j - (1 - beta) (n x phi_e(x_k)) . (d_j x p_j)) exp(i k d_j . x_k):
+// the listing's RHS (beta = 1: the EFIE's int phi . E_inc); dp: nrhs x 6 (d, p).
 __global__ void efie_rhs_kernel(const double *vtx, const int32_t *tri, const int32_t *tedge, const int32_t *etri,
-                                const double4_32a *pts64, int q, int64_t ne, double k, const double *dp, double2 *F,
-                                int64_t ldf)
+                                const double4_32a *pts64, int q, int64_t ne, double k, double beta, const double *dp,
+                                double2 *F, int64_t ldf)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (e >= ne) return;
     const double3 d = make_double3(dp[6 * j], dp[6 * j + 1], dp[6 * j + 2]);
     const double3 pol = make_double3(dp[6 * j + 3], dp[6 * j + 4], dp[6 * j + 5]);
+    const double3 hp = cross(d, pol);
     double fr = 0.0, fi = 0.0;
     for (int side = 0; side < 2; ++side) {
         const int32_t code = etri[2 * e + side];
@@ -242,7 +246,8 @@ __global__ void efie_rhs_kernel(const double *vtx, const int32_t *tri, const int
         for (int kq = 0; kq < q; ++kq) {
             const double4_32a x = pts64[t * q + kq];
             const double3 xx = make_double3(x.x, x.y, x.z);
-            const double fp = x.w * dot(g.c[i] * (xx - g.P[i]), pol);
+            const double3 f = g.c[i] * (xx - g.P[i]);
+            const double fp = x.w * (beta * dot(f, pol) - (1.0 - beta) * dot(cross(g.n, f), hp));
             double sn, cs;
             sincos(k * dot(d, xx), &sn, &cs);
             fr += fp * cs;
@@ -375,6 +380,375 @@ gyps_status efie_apply_device(Mesh *m, double k, double sign, int nrhs, const do
     return GYPS_OK;
 }
 
+// ---------------------------------------------------------------- MFIE (nxK)
+// nxK = (1/4pi) int int (n_x x phi_m(x)) . (grad_y G(x, y) x phi_n(y)) + 'grady[1/r]' correction,
+// grad_y exp(ikr)/r = F (x - y),  F = (1 - ikr) exp(ikr) / r^3.  The far sum per Gauss point,
+//   S_t = sum_l F(r_tl) (x_t - y_l) x u_l,   u_l = w_l J(y_l)  (3 complex components),
+// is taken pair by pair (the split x_t x sum F u - sum F y x u would cancel on close pairs),
+// without the pairs inside one triangle (their vector is normal to the triangle and meets
+// the in-plane test function n x phi).
+
+// FP32: one thread per target, 128-source shared tiles, coordinates scaled by k
+// (F (x - y) = k^2 F_s (x_s - y_s)), FP32 sums per tile into FP64.
+template <int R>
+__global__ void __launch_bounds__(128) far_mfie32_kernel(const double4_32a *pts, int q, const double2 *u64, int64_t ldu,
+                                                         int c0, int64_t nq, float ks, double2 *v, int64_t ldv)
+{
+    __shared__ float4 sp[128];
+    __shared__ float2 su[128][3 * R];
+    const int64_t tg = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    const int64_t tq0 = (min(tg, nq - 1) / q) * q;
+    const double4_32a x64 = pts[min(tg, nq - 1)];
+    const float tx = (float)x64.x * ks, ty = (float)x64.y * ks, tz = (float)x64.z * ks;
+    double acc[R][6];
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[j][c] = 0.0;
+    for (int64_t s0 = 0; s0 < nq; s0 += 128) {
+        const int64_t l = s0 + threadIdx.x;
+        if (l < nq) {
+            const double4_32a p = pts[l];
+            sp[threadIdx.x] = make_float4((float)p.x * ks, (float)p.y * ks, (float)p.z * ks, 0.0f);
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double2 uu = u64[l + (int64_t)(4 * (c0 + j) + c) * ldu];
+                    su[threadIdx.x][3 * j + c] = make_float2((float)uu.x, (float)uu.y);
+                }
+        }
+        __syncthreads();
+        const int n = (int)min((int64_t)128, nq - s0);
+        float b[R][6];
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) b[j][c] = 0.0f;
+        for (int ll = 0; ll < n; ++ll) {
+            if ((uint64_t)(s0 + ll - tq0) < (uint64_t)q) continue;  // same triangle
+            const float4 y = sp[ll];
+            const float dx = tx - y.x, dy = ty - y.y, dz = tz - y.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            float rs;
+            asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(r2));
+            const float kr = r2 * rs;
+            const float ang = fmaf(rintf(kr * 0.159154943091895335769f), -6.28318530717958647692f, kr);
+            float sn, cs;
+            asm("sin.approx.ftz.f32 %0, %1;" : "=f"(sn) : "f"(ang));
+            asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cs) : "f"(ang));
+            const float r3 = rs * rs * rs;
+            const float fr = (cs + kr * sn) * r3, fi = (sn - kr * cs) * r3;
+            // G = F d (complex 3-vector), S += G x u
+            const float gr[3] = {fr * dx, fr * dy, fr * dz}, gi[3] = {fi * dx, fi * dy, fi * dz};
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const float2 u0 = su[ll][3 * j], u1 = su[ll][3 * j + 1], u2 = su[ll][3 * j + 2];
+                const float ur[3] = {u0.x, u1.x, u2.x}, ui[3] = {u0.y, u1.y, u2.y};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+                    // (a x b)_c = a_c1 b_c2 - a_c2 b_c1
+                    b[j][2 * c] += (gr[c1] * ur[c2] - gr[c2] * ur[c1]) - (gi[c1] * ui[c2] - gi[c2] * ui[c1]);
+                    b[j][2 * c + 1] += (gr[c1] * ui[c2] - gr[c2] * ui[c1]) + (gi[c1] * ur[c2] - gi[c2] * ur[c1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[j][c] += (double)b[j][c];
+        __syncthreads();
+    }
+    if (tg < nq) {
+        const double k2 = (double)ks * (double)ks;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                v[tg + (int64_t)(3 * (c0 + j) + c) * ldv] = make_double2(k2 * acc[j][2 * c], k2 * acc[j][2 * c + 1]);
+    }
+}
+
+// The same in FP64 (one right-hand side per pass).
+__global__ void __launch_bounds__(128) far_mfie64_kernel(const double4_32a *pts, int q, const double2 *u64, int64_t ldu,
+                                                         int c0, int64_t nq, double k, double2 *v, int64_t ldv)
+{
+    __shared__ double4_32a sp[128];
+    __shared__ double2 su[128][3];
+    const int64_t tg = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    const int64_t tq0 = (min(tg, nq - 1) / q) * q;
+    const double4_32a x = pts[min(tg, nq - 1)];
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t s0 = 0; s0 < nq; s0 += 128) {
+        const int64_t l = s0 + threadIdx.x;
+        if (l < nq) {
+            sp[threadIdx.x] = pts[l];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) su[threadIdx.x][c] = u64[l + (int64_t)(4 * c0 + c) * ldu];
+        }
+        __syncthreads();
+        const int n = (int)min((int64_t)128, nq - s0);
+        for (int ll = 0; ll < n; ++ll) {
+            if ((uint64_t)(s0 + ll - tq0) < (uint64_t)q) continue;
+            const double4_32a y = sp[ll];
+            const double d[3] = {x.x - y.x, x.y - y.y, x.z - y.z};
+            const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            const double ri = rsqrt(r2);
+            const double kr = k * r2 * ri;
+            double sn, cs;
+            sincos(kr, &sn, &cs);
+            const double r3 = ri * ri * ri;
+            const double fr = (cs + kr * sn) * r3, fi = (sn - kr * cs) * r3;
+            const double ur[3] = {su[ll][0].x, su[ll][1].x, su[ll][2].x};
+            const double ui[3] = {su[ll][0].y, su[ll][1].y, su[ll][2].y};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+                const double xr = d[c1] * ur[c2] - d[c2] * ur[c1], xi = d[c1] * ui[c2] - d[c2] * ui[c1];
+                acc[2 * c] += fr * xr - fi * xi;
+                acc[2 * c + 1] += fr * xi + fi * xr;
+            }
+        }
+        __syncthreads();
+    }
+    if (tg < nq) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[tg + (int64_t)(3 * c0 + c) * ldv] = make_double2(acc[2 * c], acc[2 * c + 1]);
+    }
+}
+
+// MFIE correction blocks on the near pair (a, b), a != b (0 inside one triangle), with 1/(4pi):
+//   blk[i][j] = sum_{k in a} w_k (n_a x f_i(x_k)) . (int_b (x_k - y)/R^3 x f_j - Gauss sum over b),
+//   int_b (x - y)/R^3 x f_j = c_j sum_m (int_b lambda_m (x - y)/R^3) x (P_m - P_j).
+__global__ void mfie_blocks_kernel(const double *vtx, const int32_t *tri, const int32_t *tedge,
+                                   const double4_32a *pts64, int q, int64_t npairs, const int32_t *pair_a,
+                                   const int32_t *pair_b, double *blocks)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs) return;
+    const int64_t a = pair_a[p], b = pair_b[p];
+    double blk[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) blk[e] = 0.0;
+    if (a != b) {
+        const RwgTri ga = rwg_tri(vtx, tri, tedge, a), gb = rwg_tri(vtx, tri, tedge, b);
+        for (int kq = 0; kq < q; ++kq) {
+            const double4_32a xk4 = pts64[a * q + kq];
+            const double3 xk = make_double3(xk4.x, xk4.y, xk4.z);
+            double3 V[3];
+            p1_grad_over_r(xk, gb.P, V);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                double3 an = make_double3(0.0, 0.0, 0.0);
+#pragma unroll
+                for (int mm = 0; mm < 3; ++mm) an = an + gb.c[j] * cross(V[mm], gb.P[mm] - gb.P[j]);
+                for (int lq = 0; lq < q; ++lq) {
+                    const double4_32a y4 = pts64[b * q + lq];
+                    const double3 y = make_double3(y4.x, y4.y, y4.z);
+                    const double3 d = xk - y;
+                    const double r = sqrt(dot(d, d));
+                    an = an - (y4.w / (r * r * r)) * cross(d, gb.c[j] * (y - gb.P[j]));
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const double3 tf = cross(ga.n, ga.c[i] * (xk - ga.P[i]));
+                    blk[3 * i + j] += xk4.w * kInv4PiE * dot(tf, an);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) blocks[9 * p + e] = blk[e];
+}
+
+// Y[e, c] (+)= cm sum_k w_k phi_e(x_k) . J(x_k) + ck ((1/4pi) sum_k w_k (n x phi_e(x_k)) . S_k + (C x)_e):
+// the MFIE part of the listing's LHS (cm = 0, ck = 1: nxK x).
+__global__ void mfie_project_kernel(const double *vtx, const int32_t *tri, const int32_t *tedge, const int32_t *etri,
+                                    const double4_32a *pts64, int q, int64_t ne, const double2 *S, int64_t lds,
+                                    const int32_t *pair_ptr, const int32_t *pair_b, const double *blocks,
+                                    const double2 *X, int64_t ldx, double cm, double ck, int accumulate, double2 *Y,
+                                    int64_t ldy)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (e >= ne) return;
+    const double2 *xc = X + (int64_t)c * ldx;
+    const double2 *s0 = S + (int64_t)(3 * c) * lds;
+    double mr = 0.0, mi = 0.0, kr = 0.0, ki = 0.0;
+    for (int side = 0; side < 2; ++side) {
+        const int32_t code = etri[2 * e + side];
+        const int64_t t = code / 3;
+        const int i = code - 3 * (int)t;
+        const RwgTri g = rwg_tri(vtx, tri, tedge, t);
+        double2 xl[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) xl[j] = xc[tedge[3 * t + j] >> 1];
+        for (int kq = 0; kq < q; ++kq) {
+            const int64_t l = t * q + kq;
+            const double4_32a x = pts64[l];
+            const double3 xx = make_double3(x.x, x.y, x.z);
+            const double3 f = g.c[i] * (xx - g.P[i]);
+            if (cm != 0.0) {
+                double3 jr = make_double3(0.0, 0.0, 0.0), ji = jr;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const double3 fj = g.c[j] * (xx - g.P[j]);
+                    jr = jr + xl[j].x * fj;
+                    ji = ji + xl[j].y * fj;
+                }
+                mr += x.w * dot(f, jr);
+                mi += x.w * dot(f, ji);
+            }
+            const double3 tf = cross(g.n, f);
+            const double2 sx = s0[l], sy = s0[l + lds], sz = s0[l + 2 * lds];
+            kr += x.w * kInv4PiE * (tf.x * sx.x + tf.y * sy.x + tf.z * sz.x);
+            ki += x.w * kInv4PiE * (tf.x * sx.y + tf.y * sy.y + tf.z * sz.y);
+        }
+        for (int32_t p = pair_ptr[t]; p < pair_ptr[t + 1]; ++p) {
+            const int64_t b = pair_b[p];
+            const double *blk = blocks + 9 * (int64_t)p;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const double2 xf = xc[tedge[3 * b + j] >> 1];
+                kr += blk[3 * i + j] * xf.x;
+                ki += blk[3 * i + j] * xf.y;
+            }
+        }
+    }
+    double2 out = make_double2(cm * mr + ck * kr, cm * mi + ck * ki);
+    double2 &y = Y[e + (int64_t)c * ldy];
+    if (accumulate) {
+        out.x += y.x;
+        out.y += y.y;
+    }
+    y = out;
+}
+
+static gyps_status mfie_prepare(Mesh *m, cudaStream_t s)
+{
+    GYPS_TRY(efie_prepare(m, s));
+    if (m->d_mfie_blocks) return GYPS_OK;
+    double *blocks = nullptr;
+    GYPS_CUDA(cudaMalloc((void **)&blocks, (size_t)m->npairs * 9 * sizeof(double)));
+    mfie_blocks_kernel<<<(unsigned)((m->npairs + 127) / 128), 128, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_pts64,
+                                                                          m->q, m->npairs, m->d_pair_a, m->d_pair_b,
+                                                                          blocks);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(blocks);
+        return cuda_error(e, "MFIE correction");
+    }
+    m->d_mfie_blocks = blocks;
+    return GYPS_OK;
+}
+
+// Y (+)= cm Id X + ck nxK X (see mfie_project_kernel); prec FP32, or FP64 (also for double-float).
+static gyps_status mfie_apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t ldx, double2 *Y,
+                                     int64_t ldy, int prec, double cm, double ck, bool accumulate, cudaStream_t s)
+{
+    GYPS_TRY(mfie_prepare(m, s));
+    const int64_t ld = m->nq;
+    GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(ld * 4 * nrhs) * sizeof(double2)));
+    GYPS_TRY(grow(m, &m->ws_v, &m->ws_v_bytes, (size_t)(ld * 3 * nrhs) * sizeof(double2)));
+    double2 *u64 = reinterpret_cast<double2 *>(m->ws_den);
+    double2 *S = reinterpret_cast<double2 *>(m->ws_v);
+    dim3 gi((unsigned)((m->nq + 255) / 256), (unsigned)nrhs);
+    rwg_interp64_kernel<<<gi, 256, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_pts64, m->q, m->nq, ld, X, ldx, nrhs,
+                                           u64);
+    GYPS_CUDA(cudaGetLastError());
+    const unsigned grid = (unsigned)((m->nq + 127) / 128);
+    StageTimer tf(m, s, 1);
+    int launches = 0;
+    for (int c0 = 0; c0 < nrhs;) {
+        if (prec == GYPS_PREC_FP32) {
+            const int w = nrhs - c0 >= 2 ? 2 : 1;
+            if (w == 2)
+                far_mfie32_kernel<2><<<grid, 128, 0, s>>>(m->d_pts64, m->q, u64, ld, c0, m->nq, (float)k, S, ld);
+            else
+                far_mfie32_kernel<1><<<grid, 128, 0, s>>>(m->d_pts64, m->q, u64, ld, c0, m->nq, (float)k, S, ld);
+            c0 += w;
+        } else {
+            far_mfie64_kernel<<<grid, 128, 0, s>>>(m->d_pts64, m->q, u64, ld, c0, m->nq, k, S, ld);
+            c0 += 1;
+        }
+        GYPS_CUDA(cudaGetLastError());
+        ++launches;
+    }
+    tf.done(launches);
+    dim3 gp((unsigned)((m->ne + 127) / 128), (unsigned)nrhs);
+    mfie_project_kernel<<<gp, 128, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_etri, m->d_pts64, m->q, m->ne, S, ld,
+                                           m->d_pair_ptr, m->d_pair_b, m->d_mfie_blocks, X, ldx, cm, ck,
+                                           accumulate ? 1 : 0, Y, ldy);
+    GYPS_CUDA(cudaGetLastError());
+    return GYPS_OK;
+}
+
+// Y = sign (-beta T + (1 - beta)(Id/2 - nxK)) X, the listing's LHS.
+gyps_status emcfie_apply_device(Mesh *m, double k, double beta, double sign, int nrhs, const double2 *X, int64_t ldx,
+                                double2 *Y, int64_t ldy, int prec, cudaStream_t s)
+{
+    if (prec == GYPS_PREC_AUTO) prec = GYPS_PREC_FP32;
+    if (prec != GYPS_PREC_FP64 && prec != GYPS_PREC_FP32 && prec != GYPS_PREC_DF64)
+        return set_error(GYPS_ERR_UNSUPPORTED, "electromagnetic operators: FP64, FP32 or DF64");
+    if (beta != 0.0) GYPS_TRY(efie_apply_device(m, k, -beta * sign, nrhs, X, ldx, Y, ldy, prec, s));
+    if (beta == 1.0) return GYPS_OK;
+    return mfie_apply_device(m, k, nrhs, X, ldx, Y, ldy, prec == GYPS_PREC_FP32 ? GYPS_PREC_FP32 : GYPS_PREC_FP64,
+                             0.5 * sign * (1.0 - beta), -sign * (1.0 - beta), beta != 0.0, s);
+}
+
+// host / device staging shared by the electromagnetic applies (ne x nrhs)
+static gyps_status em_entry(gyps_mesh_t h, double k, double beta, bool mfie_only, int nrhs, const void *X,
+                            int64_t ldx, void *Y, int64_t ldy, int prec, void *stream)
+{
+    Mesh *m;
+    GYPS_TRY(check_mesh(h, &m));
+    if (nrhs < 1 || nrhs > 4096) return set_error(GYPS_ERR_INVALID, "nrhs must be in 1..4096");
+    if (!X || !Y) return set_error(GYPS_ERR_INVALID, "NULL argument");
+    if (!std::isfinite(k) || !(k > 0.0)) return set_error(GYPS_ERR_INVALID, "electromagnetic operators need a finite k > 0");
+    if (!std::isfinite(beta)) return set_error(GYPS_ERR_INVALID, "beta must be finite");
+    if (prec == GYPS_PREC_AUTO) prec = GYPS_PREC_FP32;
+    if (prec == GYPS_PREC_TC_BF16X3) return set_error(GYPS_ERR_UNSUPPORTED, "electromagnetic operators: FP64, FP32 or DF64");
+    if (prec != GYPS_PREC_FP64 && prec != GYPS_PREC_FP32 && prec != GYPS_PREC_DF64)
+        return set_error(GYPS_ERR_INVALID, "unknown precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    GYPS_TRY(efie_prepare(m, s));
+    const int64_t ne = m->ne;
+    if (ldx < ne || ldy < ne) return set_error(GYPS_ERR_INVALID, "leading dimension < number of edges");
+    const bool dx = is_device_pointer(X), dy = is_device_pointer(Y);
+    if (dx && dy && (const char *)X < (const char *)Y + ldy * nrhs * 16 &&
+        (const char *)Y < (const char *)X + ldx * nrhs * 16)
+        return set_error(GYPS_ERR_INVALID, "X and Y overlap");
+    const size_t blk = (size_t)ne * nrhs * sizeof(double2);
+    double2 *xs = nullptr, *ys = nullptr;
+    if (!dx || !dy) {
+        GYPS_TRY(grow(m, &m->ws_stage, &m->ws_stage_bytes, 2 * blk));
+        xs = reinterpret_cast<double2 *>(m->ws_stage);
+        ys = xs + (size_t)ne * nrhs;
+    }
+    const double2 *xin = (const double2 *)X;
+    int64_t lxin = ldx;
+    if (!dx) {
+        GYPS_CUDA(cudaMemcpy2DAsync(xs, ne * sizeof(double2), X, ldx * sizeof(double2), ne * sizeof(double2), nrhs,
+                                    cudaMemcpyHostToDevice, s));
+        xin = xs;
+        lxin = ne;
+    }
+    double2 *yout = dy ? (double2 *)Y : ys;
+    const int64_t lyout = dy ? ldy : ne;
+    if (mfie_only)
+        GYPS_TRY(mfie_apply_device(m, k, nrhs, xin, lxin, yout, lyout,
+                                   prec == GYPS_PREC_FP32 ? GYPS_PREC_FP32 : GYPS_PREC_FP64, 0.0, 1.0, false, s));
+    else
+        GYPS_TRY(emcfie_apply_device(m, k, beta, 1.0, nrhs, xin, lxin, yout, lyout, prec, s));
+    if (!dy)
+        GYPS_CUDA(cudaMemcpy2DAsync(Y, ldy * sizeof(double2), ys, ne * sizeof(double2), ne * sizeof(double2), nrhs,
+                                    cudaMemcpyDeviceToHost, s));
+    GYPS_CUDA(cudaStreamSynchronize(s));
+    return check_err_word(m, s);
+}
+
 }  // namespace gyps
 
 using namespace gyps;
@@ -435,8 +809,8 @@ extern "C" gyps_status gyps_efie_apply(gyps_mesh_t h, double k, int nrhs, const 
     return check_err_word(m, s);
 }
 
-extern "C" gyps_status gyps_rhs_planewave_efie(gyps_mesh_t h, double k, int nrhs, const double *dirs,
-                                               const double *pols, void *F, int64_t ldf, void *stream)
+static gyps_status rhs_em(gyps_mesh_t h, double k, double beta, int nrhs, const double *dirs, const double *pols,
+                          void *F, int64_t ldf, void *stream)
 {
     Mesh *m;
     GYPS_TRY(check_mesh(h, &m));
@@ -465,12 +839,37 @@ extern "C" gyps_status gyps_rhs_planewave_efie(gyps_mesh_t h, double k, int nrhs
     double2 *fout = df ? (double2 *)F : reinterpret_cast<double2 *>(st + bdp);
     const int64_t lf = df ? ldf : ne;
     dim3 g((unsigned)((ne + 127) / 128), (unsigned)nrhs);
-    efie_rhs_kernel<<<g, 128, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_etri, m->d_pts64, m->q, ne, k, d_dp, fout,
-                                      lf);
+    efie_rhs_kernel<<<g, 128, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_etri, m->d_pts64, m->q, ne, k, beta, d_dp,
+                                      fout, lf);
     GYPS_CUDA(cudaGetLastError());
     if (!df)
         GYPS_CUDA(cudaMemcpy2DAsync(F, ldf * sizeof(double2), fout, ne * sizeof(double2), ne * sizeof(double2), nrhs,
                                     cudaMemcpyDeviceToHost, s));
     GYPS_CUDA(cudaStreamSynchronize(s));
     return GYPS_OK;
+}
+
+extern "C" gyps_status gyps_rhs_planewave_efie(gyps_mesh_t h, double k, int nrhs, const double *dirs,
+                                               const double *pols, void *F, int64_t ldf, void *stream)
+{
+    return rhs_em(h, k, 1.0, nrhs, dirs, pols, F, ldf, stream);
+}
+
+extern "C" gyps_status gyps_rhs_planewave_emcfie(gyps_mesh_t h, double k, double beta, int nrhs, const double *dirs,
+                                                 const double *pols, void *F, int64_t ldf, void *stream)
+{
+    if (!std::isfinite(beta)) return set_error(GYPS_ERR_INVALID, "beta must be finite");
+    return rhs_em(h, k, beta, nrhs, dirs, pols, F, ldf, stream);
+}
+
+extern "C" gyps_status gyps_mfie_apply(gyps_mesh_t h, double k, int nrhs, const void *X, int64_t ldx, void *Y,
+                                       int64_t ldy, int prec, void *stream)
+{
+    return em_entry(h, k, 0.0, true, nrhs, X, ldx, Y, ldy, prec, stream);
+}
+
+extern "C" gyps_status gyps_emcfie_apply(gyps_mesh_t h, double k, double beta, int nrhs, const void *X, int64_t ldx,
+                                         void *Y, int64_t ldy, int prec, void *stream)
+{
+    return em_entry(h, k, beta, false, nrhs, X, ldx, Y, ldy, prec, stream);
 }

@@ -196,10 +196,12 @@ struct Solver {
 
     // Y = A X for the system's operator A: V (first kind), 1/2 M + K - i eta V
     // (Brakhage-Werner), 1/2 M + K' - i eta V (direct combined field), all
-    // nv x nrhs, or -T (the EFIE, ne x nrhs).
+    // nv x nrhs, or -T (the EFIE) and -eta T + (1 - eta)(Id/2 - nxK) (the
+    // electromagnetic combined field with beta = eta), ne x nrhs.
     gyps_status op(const double2 *X, int64_t ldx, double2 *Y, int prec)
     {
         if (form == GYPS_FORM_EFIE) return efie_apply_device(m, k, -1.0, nrhs, X, ldx, Y, nv, prec, s);
+        if (form == GYPS_FORM_EM_CFIE) return emcfie_apply_device(m, k, eta, 1.0, nrhs, X, ldx, Y, nv, prec, s);
         if (form == GYPS_FORM_BRAKHAGE_WERNER || form == GYPS_FORM_DIRECT_CFIE)
             return combined_apply_device(m, k, eta, form == GYPS_FORM_DIRECT_CFIE, nrhs, X, ldx, Y, nv, prec, s);
         return apply_device(m, k, nrhs, X, ldx, Y, nv, prec, 0, 0, m->nt, s);
@@ -432,7 +434,8 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
     S.nrhs = nrhs;
     S.restart = o.restart;
     S.s = s;
-    const int64_t n = o.formulation == GYPS_FORM_EFIE ? m->ne : m->nv;  // unknowns per column
+    const bool em = o.formulation == GYPS_FORM_EFIE || o.formulation == GYPS_FORM_EM_CFIE;
+    const int64_t n = em ? m->ne : m->nv;  // unknowns per column
     S.nv = n;
     S.form = o.formulation;
     S.eta = o.eta;
@@ -551,15 +554,17 @@ extern "C" gyps_status gyps_gmres_solve(gyps_mesh_t h, double k, int nrhs, const
         !(o.timeout_ms >= 0.0))
         return set_error(GYPS_ERR_INVALID, "bad GMRES options");
     if (o.formulation != GYPS_FORM_SINGLE_LAYER && o.formulation != GYPS_FORM_BRAKHAGE_WERNER &&
-        o.formulation != GYPS_FORM_DIRECT_CFIE && o.formulation != GYPS_FORM_EFIE)
+        o.formulation != GYPS_FORM_DIRECT_CFIE && o.formulation != GYPS_FORM_EFIE &&
+        o.formulation != GYPS_FORM_EM_CFIE)
         return set_error(GYPS_ERR_INVALID, "unknown formulation");
-    if (o.formulation == GYPS_FORM_EFIE) {
+    const bool em = o.formulation == GYPS_FORM_EFIE || o.formulation == GYPS_FORM_EM_CFIE;
+    if (em) {
         if (!(k > 0.0)) return set_error(GYPS_ERR_INVALID, "the EFIE needs k > 0");
         if (o.prec == GYPS_PREC_TC_BF16X3 || o.check_prec == GYPS_PREC_TC_BF16X3)
             return set_error(GYPS_ERR_UNSUPPORTED, "EFIE: FP64, FP32 or DF64");
         GYPS_TRY(efie_prepare(m, (cudaStream_t)stream));
     }
-    const int64_t n = o.formulation == GYPS_FORM_EFIE ? m->ne : m->nv;
+    const int64_t n = em ? m->ne : m->nv;
     if (ldf < n || ldx < n) return set_error(GYPS_ERR_INVALID, "leading dimension < number of unknowns");
     if (o.formulation != GYPS_FORM_SINGLE_LAYER) {
         if (!std::isfinite(o.eta)) return set_error(GYPS_ERR_INVALID, "eta must be finite");

@@ -103,6 +103,7 @@ struct Mesh {
     int32_t *d_tedge = nullptr;                           // nt x 3: (edge << 1) | (minus triangle)
     int32_t *d_etri = nullptr;                            // ne x 2: 3 t + j of the plus and the minus triangle
     double *d_efie_blocks = nullptr;                      // npairs x 18: the two 3 x 3 correction blocks
+    double *d_mfie_blocks = nullptr;                      // npairs x 9: the MFIE's 3 x 3 correction blocks
     std::vector<int32_t> h_edges;                         // ne x 2 vertex pairs (a < b)
     float pad = 0.0f;                                     // distance of padding points
     // mesh graph for the learned preconditioner (built on first use)
@@ -185,6 +186,9 @@ gyps_status far64_cols(Mesh *m, double k, const double2 *u64, int64_t ldu, int c
 gyps_status efie_prepare(Mesh *m, cudaStream_t s);
 gyps_status efie_apply_device(Mesh *m, double k, double sign, int nrhs, const double2 *X, int64_t ldx, double2 *Y,
                               int64_t ldy, int prec, cudaStream_t s);
+// Y = sign (-beta T + (1 - beta)(Id/2 - nxK)) X, the electromagnetic listing's LHS (ne x nrhs)
+gyps_status emcfie_apply_device(Mesh *m, double k, double beta, double sign, int nrhs, const double2 *X, int64_t ldx,
+                                double2 *Y, int64_t ldy, int prec, cudaStream_t s);
 
 // a2 in FP32: the density panel of columns c0 .. c0+w-1 (w = 1, 2, 4 or 8)
 cudaError_t launch_interp32(const Mesh *m, const double2 *X, int64_t ldx, int c0, int w, float *panel, cudaStream_t s);

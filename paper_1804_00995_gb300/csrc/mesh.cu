@@ -305,7 +305,7 @@ static void free_mesh(Mesh *m)
                     m->d_c_val, m->d_c_src_ptr, m->d_c_src, m->d_err, m->ws_den, m->ws_v, m->ws_stage, m->ws_tc,
                     m->d_adj_ptr, m->d_adj, m->d_vfeat, m->ws_pts, m->d_tri_cen, m->d_tri_cen32, m->d_tri_nrm,
                     m->d_cdl_val, m->ws_bw, m->d_nrm_panel, m->d_cdlT_val, m->d_tedge, m->d_etri,
-                    m->d_efie_blocks};
+                    m->d_efie_blocks, m->d_mfie_blocks};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;

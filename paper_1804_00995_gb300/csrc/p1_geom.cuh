@@ -112,4 +112,51 @@ static __device__ void p1_dn_over_r(double3 x, const double3 P[3], double out[3]
     }
 }
 
+// Closed-form y-integral over the flat triangle P of lambda_j(y) (x - y)/|x - y|^3
+// (the gradient in y of the single layer's 1/R, the MFIE's 'grady[1/r]' part).
+// With n, h, rho as above and s = y - rho in the plane:
+//   normal part    n h int lambda_j / R^3                    (p1_dn_over_r),
+//   in-plane part  int lambda_j (-s)/R^3
+//                = lambda_j(rho) sum_e m_e L_e - g_j I0 + sum_e (g_j . m_e) E_e,
+// g_j = grad lambda_j, I0 = int 1/R, E_e = int_e (y - rho)/R = (a - rho) L_e + t (R+ - R- - s- L_e)
+// (divergence theorem in the plane on 1/R and on s_i/R: grad (s_i/R) = e_i/R - s_i s/R^3).
+static __device__ void p1_grad_over_r(double3 x, const double3 P[3], double3 out[3])
+{
+    double3 nn = cross(P[1] - P[0], P[2] - P[0]);
+    double two_area = sqrt(dot(nn, nn));
+    double3 n = (1.0 / two_area) * nn;
+    double h = dot(x - P[0], n);
+    double3 rho = x - h * n;
+    double I[3], D[3];
+    p1_over_r(x, P, I);
+    p1_dn_over_r(x, P, D);
+    const double I0 = I[0] + I[1] + I[2];
+    double3 ML = make_double3(0.0, 0.0, 0.0), M[3], E[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        double3 a = P[e], b = P[(e + 1) % 3];
+        double3 tv = b - a;
+        double3 t = (1.0 / sqrt(dot(tv, tv))) * tv;
+        M[e] = cross(t, n);
+        double sm = dot(a - rho, t), sp = dot(b - rho, t);
+        double pe = dot(a - rho, M[e]);
+        double qe = pe * pe + h * h;
+        double3 xa = x - a, xb = x - b;
+        double Rm = sqrt(dot(xa, xa)), Rp = sqrt(dot(xb, xb));
+        double L = 0.0;
+        if (qe > 1e-30 * two_area) L = log(log_arg(Rp, sp, qe) / log_arg(Rm, sm, qe));
+        ML = ML + L * M[e];
+        E[e] = L * (a - rho) + (Rp - Rm - sm * L) * t;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        double3 g = (1.0 / two_area) * cross(n, P[(j + 2) % 3] - P[(j + 1) % 3]);  // grad lambda_j
+        double lam_rho = 1.0 + dot(g, rho - P[j]);
+        double3 w = lam_rho * ML - I0 * g;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) w = w + dot(g, M[e]) * E[e];
+        out[j] = D[j] * n + w;
+    }
+}
+
 }  // namespace gyps
