@@ -15,6 +15,7 @@
 #include <cmath>
 #include <vector>
 
+#include "far_tile.cuh"
 #include "internal.h"
 #include "p1_geom.cuh"
 
@@ -388,86 +389,214 @@ gyps_status efie_apply_device(Mesh *m, double k, double sign, int nrhs, const do
 // without the pairs inside one triangle (their vector is normal to the triangle and meets
 // the in-plane test function n x phi).
 
-// FP32: one thread per target, 128-source shared tiles, coordinates scaled by k
-// (F (x - y) = k^2 F_s (x_s - y_s)), FP32 sums per tile into FP64.
-template <int R>
-__global__ void __launch_bounds__(128) far_mfie32_kernel(const double4_32a *pts, int q, const double2 *u64, int64_t ldu,
-                                                         int c0, int64_t nq, float ks, double2 *v, int64_t ldv)
+// FP32, in the single layer's persistent tile form (coordinates scaled by k, so that
+// F (x - y) = k^2 F_s (x_s - y_s)): (target tile) x (source tile)
+// items over a persistent grid, position and density tiles (the RWG panel of one
+// right-hand side: columns x, y, z, div; div unused) by 1-D bulk copies into a 3-stage
+// ring, T targets per thread, source points in pairs with packed f32x2 arithmetic,
+// per-tile sums folded into TwoSum pairs, FP64 atomics per target-tile flush.
+struct MfieArgs {
+    const float *pos_panel, *den_panel;
+    const float4 *tgt;
+    double2 *v;  // nq x 3 (the components of S), added into
+    int64_t ldv, nq, n_src_tiles, n_tgt_tiles;
+    int q;
+    float ks;
+    int *err;
+};
+
+template <int T>
+struct MfieCfg {
+    static constexpr int NT = 128;
+    static constexpr int TT = NT * T;
+    static constexpr int STAGES = 3;
+    static constexpr int POS_BYTES = kPosTileFloats * 4;
+    static constexpr int DEN_BYTES = kSrcPairs * 6 * 4 * 4;  // R = 4 panel
+    static constexpr int STAGE_BYTES = POS_BYTES + DEN_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 64;
+};
+
+template <int T, bool CHECK>
+__device__ __forceinline__ void mfie_tile(const float *sp, const float2 (&tx)[T], const float2 (&ty)[T],
+                                          const float2 (&tz)[T], const int64_t (&tq0)[T], int64_t src0, int q,
+                                          float ks, float2 (&acc)[T][6])
 {
-    __shared__ float4 sp[128];
-    __shared__ float2 su[128][3 * R];
-    const int64_t tg = (int64_t)blockIdx.x * 128 + threadIdx.x;
-    const int64_t tq0 = (min(tg, nq - 1) / q) * q;
-    const double4_32a x64 = pts[min(tg, nq - 1)];
-    const float tx = (float)x64.x * ks, ty = (float)x64.y * ks, tz = (float)x64.z * ks;
-    double acc[R][6];
+    const float4 *XY = reinterpret_cast<const float4 *>(sp);
+    const float2 *Z = reinterpret_cast<const float2 *>(sp + 4 * kSrcPairs);
+    const float4 *U = reinterpret_cast<const float4 *>(sp + kPosTileFloats);
+    const float2 ks2 = make_float2(ks, ks);
+    const float2 magic = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23: round to integer
+    const float2 nmagic = make_float2(-12582912.0f, -12582912.0f);
+    const float2 inv2pi = make_float2(0.159154943091895335769f, 0.159154943091895335769f);
+    const float2 m2pi = make_float2(-6.28318530717958647692f, -6.28318530717958647692f);
+#pragma unroll 1
+    for (int p = 0; p < kSrcPairs; ++p) {
+        const float4 xy = XY[p];
+        const float2 sx = __fmul2_rn(make_float2(xy.x, xy.y), ks2), sy = __fmul2_rn(make_float2(xy.z, xy.w), ks2);
+        const float2 sz = __fmul2_rn(Z[p], ks2);
+        float2 ur[3], ui[3];
 #pragma unroll
-    for (int j = 0; j < R; ++j)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) acc[j][c] = 0.0;
-    for (int64_t s0 = 0; s0 < nq; s0 += 128) {
-        const int64_t l = s0 + threadIdx.x;
-        if (l < nq) {
-            const double4_32a p = pts[l];
-            sp[threadIdx.x] = make_float4((float)p.x * ks, (float)p.y * ks, (float)p.z * ks, 0.0f);
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double2 uu = u64[l + (int64_t)(4 * (c0 + j) + c) * ldu];
-                    su[threadIdx.x][3 * j + c] = make_float2((float)uu.x, (float)uu.y);
-                }
+        for (int c = 0; c < 3; ++c) {
+            const float4 u = U[4 * p + c];
+            ur[c] = make_float2(u.x, u.y);
+            ui[c] = make_float2(u.z, u.w);
         }
-        __syncthreads();
-        const int n = (int)min((int64_t)128, nq - s0);
-        float b[R][6];
 #pragma unroll
-        for (int j = 0; j < R; ++j)
+        for (int t = 0; t < T; ++t) {
+            const float2 d[3] = {__fadd2_rn(tx[t], sx), __fadd2_rn(ty[t], sy), __fadd2_rn(tz[t], sz)};
+            float2 r2 = __fmul2_rn(d[0], d[0]);
+            r2 = __ffma2_rn(d[1], d[1], r2);
+            r2 = __ffma2_rn(d[2], d[2], r2);
+            const float2 rs = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+            const float2 ph = __fmul2_rn(r2, rs);                                 // k r
+            const float2 nr = __fadd2_rn(__ffma2_rn(ph, inv2pi, magic), nmagic);  // nearest integer to k r / (2 pi)
+            const float2 ang = __ffma2_rn(nr, m2pi, ph);
+            const float2 sn = make_float2(sin_mufu(ang.x), sin_mufu(ang.y));
+            const float2 cs = make_float2(cos_mufu(ang.x), cos_mufu(ang.y));
+            const float2 r3 = __fmul2_rn(__fmul2_rn(rs, rs), rs);
+            // F = (1 - i k r) exp(i k r) / r^3 (scaled coordinates)
+            float2 fr = __fmul2_rn(__ffma2_rn(ph, sn, cs), r3);
+            float2 fi = __fmul2_rn(__ffma2_rn(make_float2(-ph.x, -ph.y), cs, sn), r3);
+            if (CHECK) {  // same triangle (and the point itself): 0
+                if ((uint64_t)(src0 + 2 * p - tq0[t]) < (uint64_t)q) fr.x = fi.x = 0.0f;
+                if ((uint64_t)(src0 + 2 * p + 1 - tq0[t]) < (uint64_t)q) fr.y = fi.y = 0.0f;
+            }
+            float2 gr[3], gi[3];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) b[j][c] = 0.0f;
-        for (int ll = 0; ll < n; ++ll) {
-            if ((uint64_t)(s0 + ll - tq0) < (uint64_t)q) continue;  // same triangle
-            const float4 y = sp[ll];
-            const float dx = tx - y.x, dy = ty - y.y, dz = tz - y.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            float rs;
-            asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(r2));
-            const float kr = r2 * rs;
-            const float ang = fmaf(rintf(kr * 0.159154943091895335769f), -6.28318530717958647692f, kr);
-            float sn, cs;
-            asm("sin.approx.ftz.f32 %0, %1;" : "=f"(sn) : "f"(ang));
-            asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cs) : "f"(ang));
-            const float r3 = rs * rs * rs;
-            const float fr = (cs + kr * sn) * r3, fi = (sn - kr * cs) * r3;
-            // G = F d (complex 3-vector), S += G x u
-            const float gr[3] = {fr * dx, fr * dy, fr * dz}, gi[3] = {fi * dx, fi * dy, fi * dz};
+            for (int c = 0; c < 3; ++c) {
+                gr[c] = __fmul2_rn(fr, d[c]);
+                gi[c] = __fmul2_rn(fi, d[c]);
+            }
+            // S += G x u:  (G x u)_c = G_c1 u_c2 - G_c2 u_c1 (complex)
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const float2 u0 = su[ll][3 * j], u1 = su[ll][3 * j + 1], u2 = su[ll][3 * j + 2];
-                const float ur[3] = {u0.x, u1.x, u2.x}, ui[3] = {u0.y, u1.y, u2.y};
+            for (int c = 0; c < 3; ++c) {
+                const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+                float2 re = acc[t][2 * c], im = acc[t][2 * c + 1];
+                re = __ffma2_rn(gr[c1], ur[c2], re);
+                re = __ffma2_rn(make_float2(-gi[c1].x, -gi[c1].y), ui[c2], re);
+                re = __ffma2_rn(make_float2(-gr[c2].x, -gr[c2].y), ur[c1], re);
+                re = __ffma2_rn(gi[c2], ui[c1], re);
+                im = __ffma2_rn(gr[c1], ui[c2], im);
+                im = __ffma2_rn(gi[c1], ur[c2], im);
+                im = __ffma2_rn(make_float2(-gr[c2].x, -gr[c2].y), ui[c1], im);
+                im = __ffma2_rn(make_float2(-gi[c2].x, -gi[c2].y), ur[c1], im);
+                acc[t][2 * c] = re;
+                acc[t][2 * c + 1] = im;
+            }
+        }
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(MfieCfg<T>::NT) far_mfie_tile_kernel(const MfieArgs a)
+{
+    using C = MfieCfg<T>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE_BYTES);
+    const int tid_x = threadIdx.x;
+    const int64_t items = a.n_tgt_tiles * a.n_src_tiles;
+    const int64_t beg = items * blockIdx.x / gridDim.x;
+    const int64_t end = items * (blockIdx.x + 1) / gridDim.x;
+    if (beg >= end) return;
+    if (tid_x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int64_t item) {
+        const int s = (int)((item - beg) % C::STAGES);
+        const int64_t st = item % a.n_src_tiles;
+        const uint32_t bar = smem_addr(&bars[s]);
+        const uint32_t dst = smem_addr(smem + s * C::STAGE_BYTES);
+        mbar_expect_tx(bar, C::STAGE_BYTES);
+        bulk_g2s(dst, a.pos_panel + st * kPosTileFloats, C::POS_BYTES, bar);
+        bulk_g2s(dst + C::POS_BYTES, a.den_panel + st * den_tile_floats(4), C::DEN_BYTES, bar);
+    };
+    int64_t issued = beg;
+    if (tid_x == 0)
+        for (; issued < end && issued < beg + C::STAGES - 1; ++issued) issue(issued);
+
+    float2 tx[T], ty[T], tz[T];
+    int64_t tid[T], tq0[T];
+    float2 acc[T][6];
+    float hi[T][6], lo[T][6];
+    int64_t cur_tt = -1;
+    const double scale = (double)a.ks * (double)a.ks;  // F (x - y) = k^2 F_s (x_s - y_s)
+    auto flush = [&]() {
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            if (tid[t] < a.nq) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-                    // (a x b)_c = a_c1 b_c2 - a_c2 b_c1
-                    b[j][2 * c] += (gr[c1] * ur[c2] - gr[c2] * ur[c1]) - (gi[c1] * ui[c2] - gi[c2] * ui[c1]);
-                    b[j][2 * c + 1] += (gr[c1] * ui[c2] - gr[c2] * ui[c1]) + (gi[c1] * ur[c2] - gi[c2] * ur[c1]);
+                    double *dst = reinterpret_cast<double *>(a.v + tid[t] + c * a.ldv);
+                    atomicAdd(dst, ((double)hi[t][2 * c] + (double)lo[t][2 * c]) * scale);
+                    atomicAdd(dst + 1, ((double)hi[t][2 * c + 1] + (double)lo[t][2 * c + 1]) * scale);
                 }
             }
         }
+    };
+    bool failed = false;
+    int64_t i = beg;
+    for (; i < end; ++i) {
+        if (tid_x == 0 && issued < end && issued == i + C::STAGES - 1) {
+            issue(issued);
+            ++issued;
+        }
+        const int64_t tt = i / a.n_src_tiles, st = i % a.n_src_tiles;
+        const int64_t tb = tt * C::TT;
+        const int64_t te = min(tb + (int64_t)C::TT, a.nq);
+        if (tt != cur_tt) {
+            if (cur_tt >= 0) flush();
 #pragma unroll
-        for (int j = 0; j < R; ++j)
+            for (int t = 0; t < T; ++t) {
+                const int64_t g = tb + tid_x + t * C::NT;
+                tid[t] = g;
+                tq0[t] = (g / a.q) * a.q;
+                const float4 p = a.tgt[min(g, a.nq - 1)];
+                tx[t] = make_float2(p.x * a.ks, p.x * a.ks);
+                ty[t] = make_float2(p.y * a.ks, p.y * a.ks);
+                tz[t] = make_float2(p.z * a.ks, p.z * a.ks);
 #pragma unroll
-            for (int c = 0; c < 6; ++c) acc[j][c] += (double)b[j][c];
+                for (int c = 0; c < 6; ++c) hi[t][c] = lo[t][c] = 0.0f;
+            }
+            cur_tt = tt;
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[t][c] = make_float2(0.0f, 0.0f);
+        const int s = (int)((i - beg) % C::STAGES);
+        const uint32_t parity = (uint32_t)(((i - beg) / C::STAGES) & 1);
+        const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), parity);
+        if (ok) {
+            const float *sp = reinterpret_cast<const float *>(smem + s * C::STAGE_BYTES);
+            const int64_t src0 = st * kSrcTile;
+            if (tb - 8 < src0 + kSrcTile && src0 < te + 8)
+                mfie_tile<T, true>(sp, tx, ty, tz, tq0, src0, a.q, a.ks, acc);
+            else
+                mfie_tile<T, false>(sp, tx, ty, tz, tq0, src0, a.q, a.ks, acc);
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) two_sum_acc(hi[t][c], lo[t][c], __fadd_rn(acc[t][c].x, acc[t][c].y));
+        }
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+    }
+    if (failed) {
+        if (tid_x == 0) {
+            atomicExch(a.err, 1);
+            for (int64_t j = i; j < issued; ++j) {
+                const int s = (int)((j - beg) % C::STAGES);
+                mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)(((j - beg) / C::STAGES) & 1));
+            }
+        }
         __syncthreads();
+        return;
     }
-    if (tg < nq) {
-        const double k2 = (double)ks * (double)ks;
-#pragma unroll
-        for (int j = 0; j < R; ++j)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                v[tg + (int64_t)(3 * (c0 + j) + c) * ldv] = make_double2(k2 * acc[j][2 * c], k2 * acc[j][2 * c + 1]);
-    }
+    flush();
 }
 
 // The same in FP64 (one right-hand side per pass).
@@ -654,21 +783,53 @@ static gyps_status mfie_apply_device(Mesh *m, double k, int nrhs, const double2 
     GYPS_TRY(grow(m, &m->ws_v, &m->ws_v_bytes, (size_t)(ld * 3 * nrhs) * sizeof(double2)));
     double2 *u64 = reinterpret_cast<double2 *>(m->ws_den);
     double2 *S = reinterpret_cast<double2 *>(m->ws_v);
-    dim3 gi((unsigned)((m->nq + 255) / 256), (unsigned)nrhs);
-    rwg_interp64_kernel<<<gi, 256, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_pts64, m->q, m->nq, ld, X, ldx, nrhs,
-                                           u64);
-    GYPS_CUDA(cudaGetLastError());
+    if (prec != GYPS_PREC_FP32) {
+        dim3 gi((unsigned)((m->nq + 255) / 256), (unsigned)nrhs);
+        rwg_interp64_kernel<<<gi, 256, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_pts64, m->q, m->nq, ld, X, ldx,
+                                               nrhs, u64);
+        GYPS_CUDA(cudaGetLastError());
+    }
     const unsigned grid = (unsigned)((m->nq + 127) / 128);
+    float *panel = nullptr;
+    MfieArgs ma{};
+    int tile_grid = 0;
+    constexpr int kT = 2;
+    if (prec == GYPS_PREC_FP32) {
+        // the RWG panel (one right-hand side, 4 columns) sits after the FP64 densities
+        const size_t b64 = ((size_t)(ld * 4 * nrhs) * sizeof(double2) + 255) / 256 * 256;
+        GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, b64 + (size_t)(m->n_src_tiles * den_tile_floats(4)) * sizeof(float)));
+        u64 = reinterpret_cast<double2 *>(m->ws_den);
+        panel = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(m->ws_den) + b64);
+        GYPS_CUDA(cudaMemsetAsync(S, 0, (size_t)(ld * 3 * nrhs) * sizeof(double2), s));
+        using C = MfieCfg<kT>;
+        GYPS_CUDA(cudaFuncSetAttribute(far_mfie_tile_kernel<kT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+        int occ = 0;
+        GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, far_mfie_tile_kernel<kT>, C::NT, C::SMEM));
+        occ = occ > 1 ? occ : 1;
+        ma.pos_panel = m->d_pos_panel;
+        ma.den_panel = panel;
+        ma.tgt = m->d_pts32;
+        ma.ldv = ld;
+        ma.nq = m->nq;
+        ma.n_src_tiles = m->n_src_tiles;
+        ma.n_tgt_tiles = (m->nq + C::TT - 1) / C::TT;
+        ma.q = m->q;
+        ma.ks = (float)k;
+        ma.err = m->d_err;
+        const int64_t items = ma.n_tgt_tiles * ma.n_src_tiles;
+        tile_grid = (int)(items < (int64_t)m->num_sms * occ ? items : (int64_t)m->num_sms * occ);
+    }
     StageTimer tf(m, s, 1);
     int launches = 0;
     for (int c0 = 0; c0 < nrhs;) {
         if (prec == GYPS_PREC_FP32) {
-            const int w = nrhs - c0 >= 2 ? 2 : 1;
-            if (w == 2)
-                far_mfie32_kernel<2><<<grid, 128, 0, s>>>(m->d_pts64, m->q, u64, ld, c0, m->nq, (float)k, S, ld);
-            else
-                far_mfie32_kernel<1><<<grid, 128, 0, s>>>(m->d_pts64, m->q, u64, ld, c0, m->nq, (float)k, S, ld);
-            c0 += w;
+            const unsigned gpan = (unsigned)((m->nq_pad + 255) / 256);
+            rwg_interp32_kernel<4><<<gpan, 256, 0, s>>>(m->d_vtx, m->d_tri, m->d_tedge, m->d_pts64, m->q, m->nq,
+                                                        m->nq_pad, X, ldx, c0, panel);
+            GYPS_CUDA(cudaGetLastError());
+            ma.v = S + (int64_t)(3 * c0) * ld;
+            far_mfie_tile_kernel<kT><<<(unsigned)tile_grid, MfieCfg<kT>::NT, MfieCfg<kT>::SMEM, s>>>(ma);
+            c0 += 1;
         } else {
             far_mfie64_kernel<<<grid, 128, 0, s>>>(m->d_pts64, m->q, u64, ld, c0, m->nq, k, S, ld);
             c0 += 1;
