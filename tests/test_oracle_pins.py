@@ -336,3 +336,48 @@ def test_icosphere_counts_and_orientation(level):
     e = np.sort(np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]]), axis=1)
     _, cnt = np.unique(e, axis=0, return_counts=True)
     assert (cnt == 2).all()
+
+
+def _octahedron():
+    v = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], dtype=float)
+    tri = []
+    for sx in (0, 1):
+        for sy in (2, 3):
+            for sz in (4, 5):
+                t = [sx, sy, sz]
+                P = v[t]
+                if np.cross(P[1] - P[0], P[2] - P[0]) @ P.mean(0) < 0:
+                    t = [sx, sz, sy]
+                tri.append(t)
+    return v, np.array(tri, dtype=np.int32)
+
+
+def test_tiny_mesh_approaches_the_exact_galerkin_matrix():
+    """Octahedron surface, k = 2: the exact Galerkin V_ij = (1/4pi) int int phi_i phi_j
+    exp(ikr)/r by brute force (outer: collapsed 10 x 10 Gauss-Legendre product rule per
+    triangle; inner: Duffy quadrature of order 30, which handles the coincident and
+    adjacent singularities).  The discrete V (Gauss points, far part with G_kk = ik, the
+    '[1/r]' correction) approaches it as the rule grows: about 26 % (q = 1), 7.7 % (q = 3),
+    1.1 % (q = 7); the brute force itself is converged to about 1e-3 at a coarser order."""
+    v, tri = _octahedron()
+    k = 2.0
+    g, w = np.polynomial.legendre.leggauss(10)
+    g, w = (g + 1) / 2, w / 2
+    U, W = np.meshgrid(g, g, indexing="ij")
+    WW = np.outer(w, w)
+    exact = np.zeros((6, 6), dtype=complex)
+    for a in range(len(tri)):
+        A, B, C = v[tri[a]]
+        X = (A + U[..., None] * (B - A) + (U * W)[..., None] * (C - B)).reshape(-1, 3)
+        wx = (np.linalg.norm(np.cross(B - A, C - A)) * U * WW).reshape(-1)
+        lam = np.stack([1 - U, U * (1 - W), U * W], -1).reshape(-1, 3)
+        for b in range(len(tri)):
+            Pb = [v[i] for i in tri[b]]
+            for xx, ww, la in zip(X, wx, lam):
+                inner = inner_integral(xx, Pb, lambda r: np.exp(1j * k * r) / r, ng=30)
+                exact[np.ix_(tri[a], tri[b])] += ww * np.outer(la, inner) / (4 * np.pi)
+    errs = []
+    for q in (1, 3, 7):
+        Vq = oracle.Mesh(v, tri, q).assemble(k)
+        errs.append(np.abs(Vq - exact).max() / np.abs(exact).max())
+    assert errs[2] < 2e-2 and errs[1] > 3 * errs[2] and errs[0] > 2 * errs[1], errs
