@@ -39,8 +39,8 @@ smooth limit ``i k`` and is left out of the correction's Gauss sum; the outer
 rule of the correction is the domain's own rule.
 
 Parity unpinned: the absolute accuracy of the paper's regularisation itself
-(the paper prints no values); it is bounded only by the sphere convergence
-checks in the tests.
+(the paper prints no values); it is bounded by the sphere convergence checks
+and by the comparison with brute-force exact Galerkin entries on a tiny mesh.
 """
 from __future__ import annotations
 
