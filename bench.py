@@ -40,6 +40,11 @@ FAR_SRC = os.path.join(ROOT, "paper_1804_00995_gb300", "csrc", "far.cu")
 FAR_TILE_SRC = os.path.join(ROOT, "paper_1804_00995_gb300", "csrc", "far_tile.cuh")
 
 
+def read_text(path):
+    with open(path) as f:
+        return f.read()
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -113,7 +118,7 @@ class ClockSampler:
         self.fh.close()
         sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in read_text(self.path).splitlines():
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -137,7 +142,7 @@ def far_traffic_per_launch():
     was taken on the current far-kernel source (else None)."""
     if not os.path.exists(PROFILE):
         return None
-    text = open(PROFILE).read()
+    text = read_text(PROFILE)
     m_sha = re.search(r"far_source_sha256:\s*([0-9a-f]{64})", text)
     m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_b:
@@ -151,8 +156,8 @@ def far_traffic_per_launch():
 def far_kernel_sha():
     """sha256 of the FP32 far-kernel code the counters describe: the tile body
     in far_tile.cuh and the FP32 section of far.cu."""
-    tile = open(FAR_TILE_SRC).read()
-    src = open(FAR_SRC).read()
+    tile = read_text(FAR_TILE_SRC)
+    src = read_text(FAR_SRC)
     a = src.index("// ---------------------------------------------------------------- a3: far, FP32")
     b = src.index("// ---------------------------------------------------------------- a3: far, FP64")
     return hashlib.sha256((tile + src[a:b]).encode()).hexdigest()
@@ -177,7 +182,7 @@ def far_roofline(achieved_gpairs, prec, nrhs, num_sms, mhz):
     r_pass = 64 if nrhs >= 64 else (32 if nrhs > 16 else 16)
     flop_per_pair = 24.0 * r_pass
     try:
-        tflops = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+        tflops = json.loads(read_text(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
         basis = "measured bf16 burst"
     except Exception:
         tflops, basis = 1900.0, "fallback bf16 burst"
@@ -331,7 +336,7 @@ def run_gyps(args, rank, world, local_rank):
     achieved = pairs / (far_ms * launches_per_apply * 1e-3) / 1e9
     peak_mhz = None
     try:
-        peak_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
+        peak_mhz = json.loads(read_text(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
     except Exception:
         peak_mhz = clk.get("sm_max_mhz") or 2070.0
     traffic = far_traffic_per_launch() if (prec == "fp32" and nrhs == 1) else None
@@ -692,7 +697,7 @@ def run_dl(args):
     achieved = pairs / (far_ms * 1e-3) / 1e9
     props = torch.cuda.get_device_properties(0)
     try:
-        peak_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
+        peak_mhz = json.loads(read_text(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
     except Exception:
         peak_mhz = clk.get("sm_max_mhz") or 2070.0
     roof = sm_peak_pairs(props.multi_processor_count, peak_mhz) / 1e9
@@ -849,7 +854,7 @@ def run_efie(args):
     achieved = pairs / (far_ms * 1e-3) / 1e9
     props = torch.cuda.get_device_properties(0)
     try:
-        peak_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
+        peak_mhz = json.loads(read_text(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
     except Exception:
         peak_mhz = clk.get("sm_max_mhz") or 2070.0
     roof = sm_peak_pairs(props.multi_processor_count, peak_mhz) / 1e9

@@ -39,3 +39,33 @@ def test_bench_pec_mie_matches_the_oracle():
         a1, a2 = bench.mie_pec_sphere(k, mu)
         b1, b2 = oracle.mie_pec_amplitudes(k, mu)
         assert np.abs(a1 - b1).max() < 1e-12 * np.abs(b1).max() and np.abs(a2 - b2).max() < 1e-12 * np.abs(b2).max()
+
+
+def test_clock_sampler_parses_nvidia_smi_lines(tmp_path):
+    """The clocks record of a bench line: median SM clock, maximum clock and power,
+    throttle reasons that were active, from nvidia-smi's CSV lines (a stand-in
+    process replaces nvidia-smi)."""
+    import os
+    cs = bench.ClockSampler("0")
+    cs.path = str(tmp_path / "clocks.csv")
+    with open(cs.path, "w") as f:
+        f.write("0, 2070 MHz, 2070 MHz, 500.12 W, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("0, 1980 MHz, 2070 MHz, 900.00 W, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n")
+        f.write("garbage line\n")
+
+    class Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+        def kill(self):
+            pass
+
+    cs.proc = Proc()
+    cs.fh = open(os.devnull, "w")
+    out = cs.stop()
+    assert out["samples"] == 2 and out["sm_mhz"] == 2025.0 and out["sm_max_mhz"] == 2070.0
+    assert out["power_w_max"] == 900.0 and out["reasons"] == ["sw_power_cap"]
+    assert not os.path.exists(cs.path)
