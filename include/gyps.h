@@ -25,7 +25,11 @@
  *    device staging and returns after `stream` has finished).
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
  *    stream).  The library owns mesh handles and the device memory inside them.
- *  - The wavenumber k must be finite and >= 0 (k = 0 is the Laplace kernel).
+ *  - A mesh's workspaces (accumulators, density panels, staging) serve every
+ *    call on that mesh: issue the calls on one mesh on one stream, or serialise
+ *    them; different meshes may run on different streams at the same time.
+ *  - The wavenumber k must be finite and >= 0 (k = 0 is the Laplace kernel);
+ *    the electromagnetic operators (RWG functions) need k > 0.
  */
 #ifndef GYPS_H
 #define GYPS_H
