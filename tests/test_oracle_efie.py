@@ -90,3 +90,59 @@ def test_efie_needs_positive_k():
     m = oracle.EfieMesh(v, t, 3)
     with pytest.raises(ValueError):
         m.efie_apply(0.0, np.ones(m.ne))
+
+
+def test_efie_near_blocks_vs_quadrature():
+    """For pairs of neighbouring triangles (and a triangle with itself), the Gauss-Gauss
+    far part (with G_kk = ik) plus the correction equals the Galerkin entry with the
+    same outer rule and the inner integrals int_b lambda_m exp(ikR)/R by Duffy
+    quadrature, to the Gauss error of the smooth remainder (below 1e-3); without the
+    correction the error is at least 20 times larger (0.71 for a triangle with itself)."""
+    from quadrature_ref import inner_integral
+    k = 2.0
+    v, t = synth.icosphere(3)
+    m = oracle.EfieMesh(v, t, 3)
+    q = m.q
+    pa, pb = oracle.near_pairs(m.tri, m.nv)
+    lib = oracle._load()
+    tsg = np.ascontiguousarray(m.tsign)
+    seen = {"self": 0, "other": 0}
+    for a, b in zip(pa, pb):
+        kind = "self" if a == b else "other"
+        if seen[kind] == 3:
+            continue
+        seen[kind] += 1
+        A, B = m.vtx[m.tri[a]], m.vtx[m.tri[b]]
+        two_b = np.linalg.norm(np.cross(B[1] - B[0], B[2] - B[0]))
+        yb, wb = m.x[b * q:(b + 1) * q], m.w[b * q:(b + 1) * q]
+        acc = np.zeros((3, 3), dtype=complex)
+        dis = np.zeros((3, 3), dtype=complex)
+        for kk in range(q):
+            x, wk = m.x[a * q + kk], m.w[a * q + kk]
+            J = inner_integral(x, B, lambda r: np.exp(1j * k * r) / r, ng=60)   # int_b lambda_m G
+            r = np.linalg.norm(yb - x, axis=1)
+            G = np.where(r > 0, np.exp(1j * k * r) / np.where(r > 0, r, 1.0), 1j * k)
+            for j in range(3):
+                cj = m.tsign[b, j] * np.linalg.norm(B[(j + 2) % 3] - B[(j + 1) % 3]) / two_b
+                vec = cj * sum(J[mm] * (B[mm] - B[j]) for mm in range(3))
+                div = 2 * cj * J.sum()
+                fjg, djg = oracle.rwg_eval(B, j, m.tsign[b, j], yb)
+                vec_g = ((wb * G)[:, None] * fjg).sum(0)
+                div_g = djg * (wb * G).sum()
+                for i in range(3):
+                    fi, di = oracle.rwg_eval(A, i, m.tsign[a, i], x)
+                    acc[i, j] += wk * (1j * k * fi[0] @ vec - 1j / k * di * div) / (4 * np.pi)
+                    dis[i, j] += wk * (1j * k * fi[0] @ vec_g - 1j / k * di * div_g) / (4 * np.pi)
+        ba, bb = np.zeros((3, 3)), np.zeros((3, 3))
+        lib.or_efie_near_blocks(oracle._dp(np.ascontiguousarray(m.vtx)),
+                                oracle._i32p(np.ascontiguousarray(m.tri, dtype=np.int32)), oracle._dp(tsg), q, 1,
+                                oracle._i64p(np.array([a], dtype=np.int64)), oracle._i64p(np.array([b], dtype=np.int64)),
+                                oracle._dp(ba), oracle._dp(bb))
+        corr = (1j * k * ba - 1j / k * bb) / (4 * np.pi)
+        scale = np.abs(acc).max()
+        e_corr = np.abs(dis + corr - acc).max() / scale
+        e_none = np.abs(dis - acc).max() / scale
+        # measured: 3e-4 with / 0.71 without for a triangle with itself, 7e-6 .. 2e-5 with /
+        # 1e-3 .. 4e-3 without for neighbours
+        assert e_corr < 1e-3 and e_none > 20 * e_corr, (kind, e_corr, e_none)
+    assert seen == {"self": 3, "other": 3}
