@@ -124,7 +124,7 @@ def loss_and_grad(params, vtx, tri, k, R, E, hidden=64, layers=4):
     per = (d.real ** 2 + d.imag ** 2).sum(dim=0) / (Et.real ** 2 + Et.imag ** 2).sum(dim=0)
     loss = per.mean()
     loss.backward()
-    return float(loss), p.grad.numpy().copy()
+    return float(loss.detach()), p.grad.numpy().copy()
 
 
 def adam_step(p, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
