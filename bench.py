@@ -554,7 +554,7 @@ def mie_scattered_sphere(k, d, pts):
 
 def run_field(args):
     """Workload field_sphere10242_k16: the total field of the sound-soft sphere
-    (the listing of Sec. 6.4: Pdom = PW - Sdom lambda) on a 300 x 300 grid of the
+    (the listing of Sec. 5.4: Pdom = PW - Sdom lambda) on a 300 x 300 grid of the
     plane y = 0, x, z in [-2.5, 2.5], from the GMRES density of
     sphere10242_k16_q7 (icosphere 20480 triangles, q = 7, k = 16, d = (1, 0, 0)).
     One step = one potential evaluation (FP32 far sum, FP64 [1/r]
@@ -759,7 +759,7 @@ def rwg_current_at_points(g, mesh, v, t, x):
 
 def run_efie(args):
     """Workload efie_sphere10242_k8_q3: the EFIE of the electromagnetic listing
-    after Sec. 6.4 with RWG functions on the icosphere of 20480 triangles (30720
+    of Sec. 5.5 with RWG functions on the icosphere of 20480 triangles (30720
     edges), q = 3 (61440 Gauss points), k = 8.  One step = one FP32 apply of T to
     one random current (four density columns through the FP32 far kernel, FP64
     correction); once each: the FP64 and double-float applies; then GMRES to 1e-6

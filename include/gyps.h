@@ -8,7 +8,7 @@
  * with Gauss points on each triangle, the dense kernel G_kl = exp(ik r_kl)/r_kl
  * between point clouds, the sparse P1 matrix Phi and the sparse singular
  * correction C of Sec. 5.2 (analytic y-integral of 1/r minus its Gauss sum, for
- * triangles sharing a vertex).  The sound-soft sphere example of Sec. 6.4 is the
+ * triangles sharing a vertex).  The sound-soft sphere example of Sec. 5.4 is the
  * intended use: V lambda = F with F_i = int phi_i exp(ik d.x).
  *
  * Conventions for every call:
@@ -66,13 +66,13 @@ typedef enum {
 
 /* Boundary integral equation that gyps_gmres_solve solves for sound-soft scattering. */
 typedef enum {
-    GYPS_FORM_SINGLE_LAYER = 0,   /* V X = F (first kind, Sec. 6.4); resonant where k^2 is an
+    GYPS_FORM_SINGLE_LAYER = 0,   /* V X = F (first kind, Sec. 5.4); resonant where k^2 is an
                                      interior Dirichlet eigenvalue */
     GYPS_FORM_BRAKHAGE_WERNER = 1, /* (1/2 M + K - i eta V) X = F: the density of u = (D - i eta S) phi,
                                      uniquely solvable for every k when eta > 0 */
     GYPS_FORM_DIRECT_CFIE = 2,     /* (1/2 M + K' - i eta V) X = F: X = du/dn of the total field, the same
                                      density as the first-kind system; F from gyps_rhs_planewave_cfie */
-    GYPS_FORM_EFIE = 3,            /* -T J = F (the electromagnetic listing after Sec. 6.4 with beta = 1):
+    GYPS_FORM_EFIE = 3,            /* -T J = F (the electromagnetic listing of Sec. 5.5 with beta = 1):
                                      J the RWG coefficients (ne unknowns), F from gyps_rhs_planewave_efie */
     GYPS_FORM_EM_CFIE = 4          /* (-beta T + (1 - beta)(Id/2 - nxK)) J = F, the listing's LHS with
                                      beta = opts->eta in [0, 1]; F from gyps_rhs_planewave_emcfie */
@@ -137,7 +137,7 @@ gyps_status gyps_quad_points(gyps_mesh_t mesh, double *xw, void *stream);
 
 /*
  * The correction matrix C of Sec. 5.2 (already multiplied by 1/(4 pi), as the
- * listing of Sec. 6.4 adds it), CSR with sorted columns.  All HOST buffers:
+ * listing of Sec. 5.4 adds it), CSR with sorted columns.  All HOST buffers:
  * rowptr nv+1, col near_nnz, val near_nnz.  Synchronous.
  */
 gyps_status gyps_near_export(gyps_mesh_t mesh, int64_t *rowptr, int32_t *col, double *val);
@@ -171,7 +171,7 @@ gyps_status gyps_near_correct(gyps_mesh_t mesh, int nrhs, const void *X, int64_t
                               void *Y, int64_t ldy, void *stream);
 
 /*
- * Dense assembly of the whole operator (the listing of Sec. 6.4:
+ * Dense assembly of the whole operator (the listing of Sec. 5.4:
  * LHS = integral(...)/(4 pi) + regularize(...)/(4 pi)):
  *     V = (1/4pi) Phi^T W G W Phi + C,   nv x nv complex double2,
  * column-major with ldv >= nv; V_ij pairs test function i with trial
@@ -239,14 +239,14 @@ gyps_status gyps_adl_apply(gyps_mesh_t mesh, double k, int nrhs, const void *X, 
  *     Y = (1/2 M + K' - i eta V) X,   M = Phi^T W Phi (Eq. A=BWB),
  * is invertible at every k > 0 for eta > 0, and its solution for the right-hand
  * side of gyps_rhs_planewave_cfie is du/dn, the density of the first-kind
- * system V lambda = F of Sec. 6.4.  Arguments, precisions and errors as
+ * system V lambda = F of Sec. 5.4.  Arguments, precisions and errors as
  * gyps_bw_apply (K' takes the precision K would).
  */
 gyps_status gyps_cfie_apply(gyps_mesh_t mesh, double k, double eta, int nrhs, const void *X, int64_t ldx,
                             void *Y, int64_t ldy, int prec, void *stream);
 
 /*
- * RWG functions (the EFIE of the electromagnetic listing after Sec. 6.4), one per
+ * RWG functions (the EFIE of the electromagnetic listing of Sec. 5.5), one per
  * edge of a closed, consistently oriented mesh.  Edges are the vertex pairs
  * (a < b) in lexicographic order; local edge j of a triangle joins its vertices
  * j+1 and j+2 (opposite P_j); the triangle where the edge runs a -> b is its plus
@@ -308,7 +308,7 @@ gyps_status gyps_rhs_planewave_emcfie(gyps_mesh_t mesh, double k, double beta, i
 
 /*
  * Single-layer potential at points (the radiation operator of the listing in
- * Sec. 6.4: Sdom = integral(points, S2, Gxy, Vh)/(4 pi)
+ * Sec. 5.4: Sdom = integral(points, S2, Gxy, Vh)/(4 pi)
  * + regularize(points, S2, '[1/r]', Vh)/(4 pi)):
  *     P[i, c] = (1/4pi) sum_l G(x_i, y_l) eta_l sum_j phi_j(y_l) X[j, c] + R[i, c],
  * G = exp(ik r)/r at the mesh's Gauss points y_l (weights eta_l); R: for every
@@ -331,7 +331,7 @@ gyps_status gyps_sl_potential(gyps_mesh_t mesh, double k, int64_t npts, const do
                               const void *X, int64_t ldx, void *P, int64_t ldp, int prec, void *stream);
 
 /*
- * Right-hand sides of the sound-soft example (Sec. 6.4, RHS = integral(S2, Vh,
+ * Right-hand sides of the sound-soft example (Sec. 5.4, RHS = integral(S2, Vh,
  * PW)): F_ij = sum_k w_k phi_i(x_k) exp(i k d_j . x_k) by the mesh's rule.
  *   dirs  HOST, nrhs x 3 doubles (propagation directions d_j, used as given).
  *   F     nv x nrhs complex double2, leading dimension ldf.
@@ -381,7 +381,7 @@ typedef struct {
 
 /*
  * Solves A X = F for nrhs columns by restarted
- * GMRES, A = V (Sec. 6.4, Eq. Singlelayerwf) or, with opts->formulation =
+ * GMRES, A = V (Sec. 5.4, Eq. Singlelayerwf) or, with opts->formulation =
  * GYPS_FORM_BRAKHAGE_WERNER, A = 1/2 M + K - i opts->eta V (gyps_bw_apply;
  * pass -F for the sound-soft problem), or with GYPS_FORM_DIRECT_CFIE,
  * A = 1/2 M + K' - i opts->eta V (gyps_cfie_apply; F from gyps_rhs_planewave_cfie),

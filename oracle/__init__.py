@@ -13,9 +13,9 @@ It follows the paper's formulation step by step:
   ``G_kl = exp(ik|x_k - y_l|)/|x_k - y_l|`` evaluated on point clouds.
 * Sec. 5.2 (regularize ... '[1/r]'): a sparse correction on pairs of triangles
   sharing a vertex, analytic integral in y minus the Gauss sum, outer Gauss in x.
-* Sec. 6.4, Eqs. (Singlelayer), (Singlelayerwf): right-hand side
+* Sec. 5.4, Eqs. (Singlelayer), (Singlelayerwf): right-hand side
   ``F_i = int phi_i exp(ik d.x)`` and the solve ``V lambda = F``.
-* Sec. 6.4 (radiation operator): the single-layer potential at points, with the
+* Sec. 5.4 (radiation operator): the single-layer potential at points, with the
   same '[1/r]' regularisation for triangles near a point.
 * Sec. 5.2 with the grady[exp(ikr)/r] kernel: the double layer ``K``, its
   'grady[1/r]' correction in closed form (solid angle and edge logarithms).
@@ -24,7 +24,7 @@ It follows the paper's formulation step by step:
 * The adjoint double layer ``K'`` (normal at the test point) and the direct
   combined-field operator ``1/2 M + K' - i eta V`` whose solution is the density of
   the paper's sound-soft problem.
-* The EFIE of the electromagnetic listing after Sec. 6.4 with RWG functions:
+* The EFIE of the electromagnetic listing of Sec. 5.5 with RWG functions:
   the vector and divergence parts of ``T`` through the same kernel, their
   '[1/r]' corrections from the P1 closed form, and the Mie amplitudes of the
   perfectly conducting sphere.
@@ -438,7 +438,7 @@ class Mesh:
     def cfie_apply(self, k, eta, x):
         """Direct combined-field operator (1/2 M + K' - i eta V) x for the sound-soft
         problem: its solution is the normal derivative of the total field, the density
-        of the paper's first-kind system V lambda = F (Sec. 6.4)."""
+        of the paper's first-kind system V lambda = F (Sec. 5.4)."""
         x = np.asarray(x, dtype=np.complex128)
         return 0.5 * (self.mass() @ x) + self.adl_apply(k, x) - 1j * eta * self.apply(k, x)
 
@@ -457,7 +457,7 @@ class Mesh:
         return 0.5 * (self.mass() @ x) + self.dl_apply(k, x) - 1j * eta * self.apply(k, x)
 
     def apply(self, k, x, rows=None):
-        """V x = far part + C x (Sec. 5.2, listing of Sec. 6.4: LHS = integral + regularize)."""
+        """V x = far part + C x (Sec. 5.2, listing of Sec. 5.4: LHS = integral + regularize)."""
         y = self.far_apply(k, x, rows)
         cx = self.near @ np.asarray(x, dtype=np.complex128)
         if rows is not None:
@@ -477,7 +477,7 @@ class Mesh:
 
     def potential(self, k, pts, x):
         """Single-layer potential of the density x (nv, nrhs) at points pts (npts, 3):
-        the radiation operator of the listing in Sec. 6.4,
+        the radiation operator of the listing in Sec. 5.4,
         integral(points, S2, Gxy, Vh)/(4 pi) + regularize(points, S2, '[1/r]', Vh)/(4 pi).
         The Gauss-point sum of exp(ikr)/r; then, for each triangle whose centroid
         lies within twice its largest centroid-vertex distance of the point (the
@@ -507,14 +507,14 @@ class Mesh:
         return v[:, 0] if one else v
 
     def rhs_planewave(self, k, dirs):
-        """F_i = int phi_i exp(ik d.x) by the domain's rule, one column per direction (Sec. 6.4)."""
+        """F_i = int phi_i exp(ik d.x) by the domain's rule, one column per direction (Sec. 5.4)."""
         dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
         p = np.exp(1j * k * (self.x @ dirs.T))               # (Nq, nd)
         return np.asarray(self.phi.T @ (self.w[:, None] * p))
 
 
 # --------------------------------------------------------------------------
-# EFIE with RWG functions (the electromagnetic listing after Sec. 6.4):
+# EFIE with RWG functions (the electromagnetic listing of Sec. 5.5):
 #   T = ik/(4pi) int int phi_m . phi_n G - i/(4pi k) int int div phi_m div phi_n G
 #     + the same two terms with the '[1/r]' regularisation (Sec. 5.2)
 # --------------------------------------------------------------------------
@@ -818,7 +818,7 @@ def mie_pec_amplitudes(k, cos_theta):
 # --------------------------------------------------------------------------
 
 def solve_lu(a, f):
-    """Direct solve (the paper's LHS \\ RHS, Sec. 6.4)."""
+    """Direct solve (the paper's LHS \\ RHS, Sec. 5.4)."""
     return np.linalg.solve(a, f)
 
 

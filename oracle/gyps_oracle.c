@@ -231,7 +231,7 @@ void or_p1_inv_r(const double *x, const double *P0, const double *P1, const doub
 
 /* ------------------------------------------------------------------------ */
 /* Singular correction of Sec. 5.2 (regularize(S, S, Vh, '[1/r]', Vh)),      */
-/* scaled by 1/(4 pi) as in the paper's listing of Sec. 6.4.  For each       */
+/* scaled by 1/(4 pi) as in the paper's listing of Sec. 5.4.  For each       */
 /* ordered pair (a, b) of triangles that share at least one vertex, each     */
 /* quadrature point x_k of a and each local vertex j of b:                   */
 /*   exact_j = int_b lambda_j(y)/|x_k - y| dy          (closed form above)   */

@@ -1,4 +1,4 @@
-// Dense assembly of the single layer (listing of Sec. 6.4: LHS = integral/(4pi) +
+// Dense assembly of the single layer (listing of Sec. 5.4: LHS = integral/(4pi) +
 // regularize/(4pi)) and the plane-wave right-hand side (RHS = integral(S2, Vh, PW)).
 #include <cmath>
 

@@ -1,4 +1,4 @@
-// EFIE with RWG functions (the electromagnetic listing after Sec. 6.4):
+// EFIE with RWG functions (the electromagnetic listing of Sec. 5.5):
 //   T = ik/(4pi) int int phi_m . phi_n G - i/(4pi k) int int div phi_m div phi_n G
 //     + ik/(4pi) regularize(phi, '[1/r]', phi) - i/(4pi k) regularize(div phi, '[1/r]', div phi),
 // in the single layer's factorisation: per right-hand side four density columns

@@ -548,7 +548,7 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
 
 // Host staging of an nv x nrhs complex block with leading dimension ld.
 // Far part of the potential at arbitrary points (the radiation operator of the
-// listing in Sec. 6.4: integral(points, S2, Gxy, Vh)).  The FP32 kernel takes
+// listing in Sec. 5.4: integral(points, S2, Gxy, Vh)).  The FP32 kernel takes
 // the points as targets numbered from nq_pad on, past every source index, so
 // its self-pair test never fires: the target and accumulator pointers are
 // shifted back by that offset (every access stays inside the point arrays).

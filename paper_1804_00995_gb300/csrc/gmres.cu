@@ -1,4 +1,4 @@
-// Restarted GMRES for V X = F (Sec. 6.4, Eq. Singlelayerwf), one Krylov space
+// Restarted GMRES for V X = F (Sec. 5.4, Eq. Singlelayerwf), one Krylov space
 // per right-hand side, the operator applied to all columns at once.  Arnoldi
 // uses classical Gram-Schmidt applied twice, in FP64 on the device; the small
 // Hessenberg least-squares problems are solved on the host with Givens

@@ -1,7 +1,7 @@
 // Learned preconditioner: a message-passing network on the P1 mesh graph that
 // maps a residual r to an approximate correction z ~ V^{-1} r, for flexible
 // GMRES.  Not in the paper; the operator it approximates is the single layer of
-// Sec. 5 / Sec. 6.4.
+// Sec. 5 / Sec. 5.4.
 //
 // Network (H hidden features, L layers, bf16 weights, FP32 activations and sums):
 //   f_i   = [Re r_i / s, Im r_i / s, x^_i, y^_i, z^_i, n_i, k h]   (s = rms(r))

@@ -1,5 +1,5 @@
 // Single-layer potential at arbitrary points: the radiation operator of the
-// listing in Sec. 6.4,
+// listing in Sec. 5.4,
 //   Sdom = integral(points, S2, Gxy, Vh)/(4 pi) + regularize(points, S2, '[1/r]', Vh)/(4 pi),
 //   P[i, c] = (1/4pi) sum_l G(x_i, y_l) eta_l sum_j phi_j(y_l) X[j, c]
 //           + (1/4pi) sum_{b near x_i} sum_j (int_b lambda_j / |x_i - y| - sum_{l in b} eta_l lambda_j(y_l) / |x_i - y_l|) X[v_j(b), c],

@@ -3,7 +3,7 @@
 This module holds only input generation: meshes, plane-wave directions and
 wavenumbers.  It holds none of the single-layer operator's arithmetic
 (quadrature, kernel, correction, solve).  The paper's sound-soft sphere test
-case (Sec. 6.4) meshes the unit sphere with ``mshSphere``, whose construction
+case (Sec. 5.4) meshes the unit sphere with ``mshSphere``, whose construction
 is not given; an icosphere stands in for it, and random-axis ellipsoids made by
 mapping icosphere vertices stand in for the uneven batch of meshes.
 """
@@ -135,12 +135,12 @@ def random_complex(rng: np.random.Generator, n: int, nrhs: int = 1):
 
 # The five workloads of the operator: mesh, quadrature points per triangle,
 # wavenumber and right-hand sides.  Sizes follow the sound-soft sphere example
-# and the scaling study of the paper (Sec. 6.4, Table 4) on icospheres.
+# and the scaling study of the paper (Sec. 6.2, Table 4) on icospheres.
 WORKLOADS = {
     "sphere642_k5_q3_dense": dict(level=3, q=3, k=5.0, dirs=[(0.0, 0.0, 1.0)], tol=1e-8),
     "sphere10242_k16_q7": dict(level=5, q=7, k=16.0, dirs=[(1.0, 0.0, 0.0)], tol=1e-6),
     "sphere163842_k64_q3_r16": dict(level=7, q=3, k=64.0, ndirs=16, seed=7, tol=1e-6),
-    # EFIE (electromagnetic listing after Sec. 6.4): RWG on the 20480-triangle sphere,
+    # EFIE (electromagnetic listing of Sec. 5.5): RWG on the 20480-triangle sphere,
     # x-polarised plane wave along z
     "efie_sphere10242_k8_q3": dict(level=5, q=3, k=8.0, dirs=[(0.0, 0.0, 1.0)], pols=[(1.0, 0.0, 0.0)], tol=1e-6),
 }

@@ -1,5 +1,5 @@
 """Single-layer potential at points (gyps_sl_potential, the radiation operator
-of the listing in Sec. 6.4) against the oracle: FP64 and double-float 1e-10,
+of the listing in Sec. 5.4) against the oracle: FP64 and double-float 1e-10,
 FP32 1e-5, with points inside, outside and within 1e-3 of the surface."""
 import numpy as np
 import pytest

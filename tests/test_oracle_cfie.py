@@ -1,7 +1,7 @@
 """Pins of the oracle's adjoint double layer K' (normal derivative at the test
 point) and of the direct combined-field system (1/2 M + K' - i eta V) lambda =
 int phi (d/dn - i eta) u_inc, whose solution is the density of the paper's
-sound-soft problem (Sec. 6.4), on the unit sphere at the resonant k = pi."""
+sound-soft problem (Sec. 5.4), on the unit sphere at the resonant k = pi."""
 import numpy as np
 import pytest
 

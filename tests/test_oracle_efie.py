@@ -1,5 +1,5 @@
 """Pins of the oracle's EFIE with RWG functions (the electromagnetic listing
-after Sec. 6.4): T = ik/(4pi) <phi, G phi> - i/(4pi k) <div phi, G div phi> with
+of Sec. 5.5): T = ik/(4pi) <phi, G phi> - i/(4pi k) <div phi, G div phi> with
 the '[1/r]' regularisation, on closed meshes."""
 import numpy as np
 import pytest

@@ -1,5 +1,5 @@
-"""Pins of the oracle's MFIE part nxK of the electromagnetic listing after
-Sec. 6.4 (kernel grad_y exp(ikr)/r tested with n x phi, 'grady[1/r]'
+"""Pins of the oracle's MFIE part nxK of the electromagnetic listing of
+Sec. 5.5 (kernel grad_y exp(ikr)/r tested with n x phi, 'grady[1/r]'
 regularisation) and of the listing's combined system
 -beta T + (1 - beta)(Id/2 - nxK)."""
 import numpy as np

@@ -264,7 +264,7 @@ def test_sphere_eigenvalues_converge(k, n):
 
 
 def test_rhs_constant_wave_is_mass_row_sum():
-    """Sec. 6.4 right-hand side with k = 0: F_i = int phi_i = sum of area/3 over
+    """Sec. 5.4 right-hand side with k = 0: F_i = int phi_i = sum of area/3 over
     the triangles at vertex i."""
     v, t = synth.icosphere(2)
     m = oracle.Mesh(v, t, 3)
@@ -293,7 +293,7 @@ def test_gmres_matches_lu_sphere642():
 
 
 def test_mie_series_convergence():
-    """Sound-soft sphere (Sec. 6.4): the discrete density of V lambda = F
+    """Sound-soft sphere (Sec. 5.4): the discrete density of V lambda = F
     converges to the Mie series lambda = sum (2n+1) i^n P_n(d.x)/(i k h_n(k))
     (mass-weighted relative L2 error), halving at least per refinement."""
     k = 3.0

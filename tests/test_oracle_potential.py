@@ -1,5 +1,5 @@
 """Pins of the oracle's single-layer potential at points (the radiation
-operator of the listing in Sec. 6.4: integral(points, S2, Gxy, Vh) +
+operator of the listing in Sec. 5.4: integral(points, S2, Gxy, Vh) +
 regularize(points, S2, '[1/r]', Vh), divided by 4 pi) against closed forms:
 the Laplace potential of a constant density on the unit sphere, the Mie field
 of the sound-soft sphere, and brute-force quadrature near one triangle."""
