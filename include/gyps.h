@@ -130,6 +130,31 @@ gyps_status gyps_mesh_destroy(gyps_mesh_t mesh);
 gyps_status gyps_mesh_info(gyps_mesh_t mesh, gyps_mesh_info_t *info);
 
 /*
+ * Error word of a mesh's bounded device waits (library service; no counterpart
+ * in the paper).  Every pipeline wait inside the far kernels gives up after a
+ * poll limit instead of spinning forever; a wait that gives up records it in
+ * the mesh's error word and its kernel returns early, so the result of that
+ * launch is incomplete.  Synchronous calls (host buffers, GMRES, the double
+ * layer, EFIE and potential entry points) clear the word when they start and
+ * return TIMEOUT if one of their own launches set it.  Asynchronous calls
+ * (device X and Y for gyps_sl_apply, gyps_sl_apply_noalloc) cannot report it:
+ * gyps_mesh_check synchronises `stream`, then reads and clears the word.
+ * Returns TIMEOUT if a wait gave up since the word was last cleared, else OK.
+ */
+gyps_status gyps_mesh_check(gyps_mesh_t mesh, void *stream);
+
+/*
+ * Poll limit of the pipeline waits in the far kernels (FP32 CUDA-core and
+ * tensor-core forms of gyps_sl_apply and gyps_sl_apply_noalloc) launched after
+ * this call, process-wide.  polls < 0 restores each kernel's default (about a
+ * second of polling); polls = 0 makes every such wait give up at once, which
+ * exercises the TIMEOUT path deterministically (tests).  The wait that drains a
+ * failed launch's copies and products in flight always keeps the default.
+ * Errors: INVALID for polls > 2^30.
+ */
+gyps_status gyps_set_wait_polls(int64_t polls);
+
+/*
  * Quadrature points and weights (x_k, w_k) of Eq. (approxA), k = t*q + j,
  * written as nq x 4 doubles (x, y, z, w) into xw (device or host).
  */
@@ -158,6 +183,10 @@ gyps_status gyps_near_export(gyps_mesh_t mesh, int64_t *rowptr, int32_t *col, do
  *        applies over a partition of the triangles add up to the full apply.
  * Errors: INVALID (nrhs, ld, k, range), UNSUPPORTED (tensor-core precision
  * with fewer than 16 right-hand sides), OOM, CUDA, TIMEOUT.
+ * TIMEOUT (a bounded device wait gave up, Y incomplete) is returned only when
+ * X or Y is a host buffer: that call is synchronous and reports the waits of
+ * its own launches.  With device X and Y the call returns after launching;
+ * call gyps_mesh_check after the stream's work to learn whether a wait gave up.
  */
 gyps_status gyps_sl_apply(gyps_mesh_t mesh, double k, int nrhs, const void *X, int64_t ldx,
                           void *Y, int64_t ldy, int prec, uint32_t flags,
@@ -438,6 +467,7 @@ typedef struct {
 
 #define GYPS_BATCH_NO_GRAPH 0x1u /* launch the kernels on each apply instead of a captured graph */
 #define GYPS_BATCH_AUTOTUNE 0x2u /* time the candidate shapes now when the cache has no entry */
+#define GYPS_BATCH_CUDA_CORES 0x4u /* form (a) only: FP32 CUDA-core kernel products, no tensor cores */
 
 typedef struct {
     int32_t nmesh, nrhs;
@@ -458,7 +488,7 @@ typedef struct {
  * accumulators), the work list, the shape choice and the graph.  X and Y must
  * stay valid until gyps_batch_destroy; refill X and call gyps_batch_apply.
  *   items  HOST array of nitems (1..4096).  nrhs 1..4096, shared by all items.
- *   flags  GYPS_BATCH_NO_GRAPH | GYPS_BATCH_AUTOTUNE.
+ *   flags  GYPS_BATCH_NO_GRAPH | GYPS_BATCH_AUTOTUNE | GYPS_BATCH_CUDA_CORES.
  * Errors: INVALID (argument, host buffers, meshes on different devices), OOM, CUDA.
  */
 gyps_status gyps_batch_create(const gyps_batch_item *items, int nitems, int nrhs, uint32_t flags,
@@ -495,6 +525,8 @@ gyps_status gyps_batch_destroy(gyps_batch_t batch);
  * keeps the previous call's contents: calls whose work overlaps on the GPU
  * (other streams, other threads) race and corrupt each other's results;
  * order them on one stream.
+ * The call returns after launching, so it cannot return TIMEOUT: a bounded
+ * device wait that gave up is reported by gyps_mesh_check.
  */
 gyps_status gyps_sl_apply_noalloc(gyps_mesh_t mesh, double k, int nrhs, const void *X, int64_t ldx,
                                   void *Y, int64_t ldy, void *stream);

@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "PREC", "GypsError", "Mesh", "load", "sl_apply", "near_correct", "sl_assemble", "rhs_planewave",
-    "gmres_solve", "version",
+    "gmres_solve", "version", "set_wait_polls",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -132,6 +132,8 @@ _SIGS = {
     "gyps_batch_apply": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "gyps_batch_info": ([ctypes.c_void_p, ctypes.POINTER(_BatchInfo)], ctypes.c_int),
     "gyps_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "gyps_mesh_check": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "gyps_set_wait_polls": ([ctypes.c_int64], ctypes.c_int),
     "gyps_sl_apply_noalloc": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "gyps_precond_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)],
@@ -287,6 +289,12 @@ class Mesh:
         _check(load().gyps_profile_read(self.handle, ctypes.byref(p)))
         return {f: getattr(p, f) for f, _ in _Profile._fields_}
 
+    def check(self, stream=None):
+        """Synchronises the stream, then reads and clears the error word of the
+        mesh's bounded device waits (gyps_mesh_check); raises GypsError
+        (TIMEOUT) if a wait of an asynchronous call gave up."""
+        _check(load().gyps_mesh_check(self.handle, _stream(stream)))
+
     def near_csr(self):
         """Correction matrix C (CSR: rowptr int64, col int32, val float64), host numpy."""
         rowptr = np.zeros(self.nv + 1, dtype=np.int64)
@@ -294,6 +302,13 @@ class Mesh:
         val = np.zeros(self.info.near_nnz, dtype=np.float64)
         _check(load().gyps_near_export(self.handle, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data))
         return rowptr, col, val
+
+
+def set_wait_polls(polls: int) -> None:
+    """Poll limit of the far kernels' pipeline waits, process-wide
+    (gyps_set_wait_polls): negative restores the defaults, 0 makes every such
+    wait give up at once (tests of the TIMEOUT path)."""
+    _check(load().gyps_set_wait_polls(int(polls)))
 
 
 def sl_apply(mesh: Mesh, k: float, X, prec: str = "fp32", near: bool = True, tri_range=None, out=None, stream=None):
@@ -486,7 +501,8 @@ class Batch:
     bound to the batch: fill ``X[i]`` in place, call ``apply()``.
     """
 
-    def __init__(self, items, nrhs: int, graph: bool = True, autotune: bool = False, stream=None):
+    def __init__(self, items, nrhs: int, graph: bool = True, autotune: bool = False, cuda_cores: bool = False,
+                 stream=None):
         torch = _torch()
         self.meshes = [m for m, _ in items]
         self.ks = [float(k) for _, k in items]
@@ -497,7 +513,7 @@ class Batch:
         arr = (_BatchItem * len(items))()
         for i, m in enumerate(self.meshes):
             arr[i] = _BatchItem(m.handle.value, self.ks[i], self.X[i].data_ptr(), m.nv, self.Y[i].data_ptr(), m.nv)
-        flags = (0 if graph else 0x1) | (0x2 if autotune else 0)
+        flags = (0 if graph else 0x1) | (0x2 if autotune else 0) | (0x4 if cuda_cores else 0)
         h = ctypes.c_void_p()
         _check(load().gyps_batch_create(arr, len(items), int(nrhs), flags, _stream(stream), ctypes.byref(h)))
         self._h = h

@@ -646,7 +646,8 @@ extern "C" gyps_status gyps_batch_create(const gyps_batch_item *items, int nitem
     *out = nullptr;
     if (!items || nitems < 1 || nitems > 4096) return set_error(GYPS_ERR_INVALID, "nitems must be in 1..4096");
     if (nrhs < 1 || nrhs > 4096) return set_error(GYPS_ERR_INVALID, "nrhs must be in 1..4096");
-    if (flags & ~(GYPS_BATCH_NO_GRAPH | GYPS_BATCH_AUTOTUNE)) return set_error(GYPS_ERR_INVALID, "unknown flag");
+    if (flags & ~(GYPS_BATCH_NO_GRAPH | GYPS_BATCH_AUTOTUNE | GYPS_BATCH_CUDA_CORES))
+        return set_error(GYPS_ERR_INVALID, "unknown flag");
     std::vector<gyps_batch_item> its(items, items + nitems);
     Batch *b = new Batch();
     b->nrhs = nrhs;
@@ -677,10 +678,11 @@ extern "C" gyps_status gyps_batch_create(const gyps_batch_item *items, int nitem
     gyps_status st = GYPS_OK;
     if (cudaMalloc((void **)&b->d_err, sizeof(int)) != cudaSuccess) st = set_error(GYPS_ERR_OOM, "error word");
     if (st == GYPS_OK) cudaMemset(b->d_err, 0, sizeof(int));
-    bool tc_ok = true;
+    bool tc_ok = !(flags & GYPS_BATCH_CUDA_CORES);
     for (const auto &it : its) tc_ok = tc_ok && it.k > 0.0;
     int R = -1, T = -1;
-    const std::string key = (st == GYPS_OK) ? tune_key(b) : std::string();
+    const std::string key =
+        (st == GYPS_OK) ? tune_key(b) + ((flags & GYPS_BATCH_CUDA_CORES) ? "|cuda_cores" : "") : std::string();
     if (st == GYPS_OK && tune_lookup(key, &R, &T) && ((R == 0 && tc_ok && nrhs >= 16) || (R > 0 && nrhs % R == 0))) {
         b->tuned = 2;
     } else if (st == GYPS_OK && (flags & GYPS_BATCH_AUTOTUNE)) {

@@ -666,6 +666,7 @@ static gyps_status dl_entry(gyps_mesh_t h, double k, int nrhs, const void *X, in
     }
     double2 *yout = dy ? (double2 *)Y : ys;
     const int64_t lyout = dy ? ldy : m->nv;
+    GYPS_TRY(clear_err_word(m, s));  // report only the waits of this call's launches
     GYPS_TRY(dl_apply_device(m, k, nrhs, xin, lxin, yout, lyout, prec, adj, s));
     if (!dy)
         GYPS_CUDA(cudaMemcpy2DAsync(Y, ldy * sizeof(double2), ys, m->nv * sizeof(double2), m->nv * sizeof(double2), nrhs,
@@ -711,6 +712,7 @@ static gyps_status combined_entry(gyps_mesh_t h, double k, double eta, int nrhs,
     }
     double2 *yout = dy ? (double2 *)Y : ys;
     const int64_t lyout = dy ? ldy : m->nv;
+    GYPS_TRY(clear_err_word(m, s));  // report only the waits of this call's launches
     GYPS_TRY(combined_apply_device(m, k, eta, adj, nrhs, xin, lxin, yout, lyout, prec, s));
     if (!dy)
         GYPS_CUDA(cudaMemcpy2DAsync(Y, ldy * sizeof(double2), ys, m->nv * sizeof(double2), m->nv * sizeof(double2), nrhs,

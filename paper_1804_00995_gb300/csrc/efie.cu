@@ -898,6 +898,7 @@ static gyps_status em_entry(gyps_mesh_t h, double k, double beta, bool mfie_only
     }
     double2 *yout = dy ? (double2 *)Y : ys;
     const int64_t lyout = dy ? ldy : ne;
+    GYPS_TRY(clear_err_word(m, s));  // report only the waits of this call's launches
     if (mfie_only)
         GYPS_TRY(mfie_apply_device(m, k, nrhs, xin, lxin, yout, lyout,
                                    prec == GYPS_PREC_FP32 ? GYPS_PREC_FP32 : GYPS_PREC_FP64, 0.0, 1.0, false, s));
@@ -962,6 +963,7 @@ extern "C" gyps_status gyps_efie_apply(gyps_mesh_t h, double k, int nrhs, const 
     }
     double2 *yout = dy ? (double2 *)Y : ys;
     const int64_t lyout = dy ? ldy : ne;
+    GYPS_TRY(clear_err_word(m, s));  // report only the waits of this call's launches
     GYPS_TRY(efie_apply_device(m, k, 1.0, nrhs, xin, lxin, yout, lyout, prec, s));
     if (!dy)
         GYPS_CUDA(cudaMemcpy2DAsync(Y, ldy * sizeof(double2), ys, ne * sizeof(double2), ne * sizeof(double2), nrhs,

@@ -3,6 +3,7 @@
 // Steps: interp (u = W_y Phi X, a2), far (v = G u, a3), project
 // (Y = Phi^T W_x v / 4pi, a4) fused with the CSR correction (a5).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(FarCfg<R, T>::NT) far32_kernel(const FarArgs a
 
         const int s = (int)((i - beg) % C::STAGES);
         const uint32_t parity = (uint32_t)(((i - beg) / C::STAGES) & 1);
-        bool ok = mbar_wait_bounded(smem_addr(&bars[s]), parity);
+        bool ok = mbar_wait_polls(smem_addr(&bars[s]), parity, a.wait_polls);
         if (ok) {
             const float *sp = reinterpret_cast<const float *>(smem + s * C::STAGE_BYTES);
             const int64_t src0 = st * kSrcTile;
@@ -394,6 +395,8 @@ static FarArgs far_args(const Mesh *m, const float *panel, double2 *v, int64_t l
     a.n_tgt_tiles = (t_end - t_begin + tt_size - 1) / tt_size;
     a.ks = k > 0.0 ? (float)k : 1.0f;
     a.err = m->d_err;
+    const int wp = wait_polls_setting();
+    a.wait_polls = wp >= 0 ? wp : kDefaultWaitPolls;
     return a;
 }
 
@@ -634,6 +637,15 @@ static gyps_status stage_out(Mesh *m, const double2 *src, void *dst, int64_t ld,
     return GYPS_OK;
 }
 
+static std::atomic<int> g_wait_polls{-1};
+int wait_polls_setting() { return g_wait_polls.load(std::memory_order_relaxed); }
+
+gyps_status clear_err_word(Mesh *m, cudaStream_t s)
+{
+    GYPS_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(int), s));
+    return GYPS_OK;
+}
+
 gyps_status check_err_word(Mesh *m, cudaStream_t s)
 {
     int h = 0;
@@ -693,6 +705,7 @@ extern "C" gyps_status gyps_sl_apply(gyps_mesh_t h, double k, int nrhs, const vo
     double2 *xs = reinterpret_cast<double2 *>(m->ws_stage), *ys = xs + (size_t)m->nv * nrhs;
     const double2 *xin = (const double2 *)X;
     int64_t lxin = ldx;
+    GYPS_TRY(clear_err_word(m, s));
     if (!dx) {
         GYPS_TRY(stage_in(m, X, ldx, nrhs, xs, s));
         xin = xs;
@@ -739,6 +752,22 @@ extern "C" gyps_status gyps_near_correct(gyps_mesh_t h, int nrhs, const void *X,
     GYPS_CUDA(launch_near_spmv(*m, nrhs, xin, lxin, yio, lyio, s));
     if (!dy) GYPS_TRY(stage_out(m, ys, Y, ldy, nrhs, s));
     GYPS_CUDA(cudaStreamSynchronize(s));
+    return GYPS_OK;
+}
+
+extern "C" gyps_status gyps_mesh_check(gyps_mesh_t h, void *stream)
+{
+    Mesh *m;
+    GYPS_TRY(check_mesh(h, &m));
+    cudaStream_t s = (cudaStream_t)stream;
+    GYPS_CUDA(cudaStreamSynchronize(s));
+    return check_err_word(m, s);
+}
+
+extern "C" gyps_status gyps_set_wait_polls(int64_t polls)
+{
+    if (polls > ((int64_t)1 << 30)) return set_error(GYPS_ERR_INVALID, "polls must be <= 2^30");
+    g_wait_polls.store(polls < 0 ? -1 : (int)polls, std::memory_order_relaxed);
     return GYPS_OK;
 }
 

@@ -153,9 +153,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 }
 
 // Bounded wait that also gives up as soon as another thread reported a failure.
-__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort)
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort, int polls)
 {
-    for (int n = 0; n < (1 << 22); ++n) {
+    for (int n = 0; n < polls; ++n) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((n & 255) == 255 && *abort) return false;
     }
@@ -181,9 +181,9 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity
 
 // Bounded (about a second at most) suspending wait; gives up when another
 // thread reported a failure.
-__device__ __forceinline__ bool wait_sleep_or_abort(uint32_t bar, uint32_t parity, volatile int *abort)
+__device__ __forceinline__ bool wait_sleep_or_abort(uint32_t bar, uint32_t parity, volatile int *abort, int polls)
 {
-    for (int n = 0; n < (1 << 21); ++n) {
+    for (int n = 0; n < polls; ++n) {
         if (mbar_try_wait_hint(bar, parity, 500u)) return true;
         if ((n & 15) == 15 && *abort) return false;
     }
@@ -268,6 +268,8 @@ struct TcArgs {
     int ncols;        // valid right-hand sides in this pass (<= R)
     float ks;
     int *err;
+    int polls_spin;   // poll limits of the pipeline waits (spinning / suspending); the
+    int polls_sleep;  // drain after a failure keeps the default limit
 };
 
 // Kernel values of one generator thread (its row = its tensor-memory lane) for
@@ -420,10 +422,10 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
         for (int64_t it = 0; it < icount && ok; ++it) {
             const int nc = chunks_of(seg_of(ifirst + it * istep));
             if (it > 0)
-                ok = __all_sync(0xffffffffu, wait_sleep_or_abort(smem_addr(acc_empty), (uint32_t)((it - 1) & 1), abort));
+                ok = __all_sync(0xffffffffu, wait_sleep_or_abort(smem_addr(acc_empty), (uint32_t)((it - 1) & 1), abort, a.polls_sleep));
             for (int c = 0; c < nc && ok; ++c) {
-                ok = wait_sleep_or_abort(smem_addr(&a_full[sa]), pa, abort) &&
-                     wait_sleep_or_abort(smem_addr(&src_full[ss]), ps, abort);
+                ok = wait_sleep_or_abort(smem_addr(&a_full[sa]), pa, abort, a.polls_sleep) &&
+                     wait_sleep_or_abort(smem_addr(&src_full[ss]), ps, abort, a.polls_sleep);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 tc_fence_after();
@@ -477,7 +479,7 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
                 const int s = j % SS;
                 if (j >= SS) {  // the products of chunk j - SS, the stage's last user, finished
                     ok = __all_sync(0xffffffffu,
-                                    wait_sleep_or_abort(smem_addr(&src_empty[s]), (uint32_t)((j / SS - 1) & 1), abort));
+                                    wait_sleep_or_abort(smem_addr(&src_empty[s]), (uint32_t)((j / SS - 1) & 1), abort, a.polls_sleep));
                     if (!ok) break;
                 }
                 if (leader) {
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
                 // work: the panel chunk before the first group, the tile stage (free
                 // once the products of chunk n - A_STAGES finished) after it, and a
                 // non-blocking test of the next chunk's panel after the last group.
-                if (!src_ready) ok = wait_or_abort(smem_addr(&src_full[ss]), ps, abort);
+                if (!src_ready) ok = wait_or_abort(smem_addr(&src_full[ss]), ps, abort, a.polls_spin);
                 ok = __all_sync(0xffffffffu, ok);  // tcgen05.st is warp-collective
                 if (!ok) break;
                 const unsigned char *src = smem + ss * C::CHUNK_BYTES;
@@ -538,7 +540,7 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
                     else
                         gen_group<false>(src, q, tx, ty, tz, tgt, src0, slice, g);
                     if (q == 0) {
-                        if (n >= AS) ok = wait_or_abort(smem_addr(&mma_done[sa]), pa ^ 1u, abort);
+                        if (n >= AS) ok = wait_or_abort(smem_addr(&mma_done[sa]), pa ^ 1u, abort, a.polls_spin);
                         ok = __all_sync(0xffffffffu, ok);
                         if (!ok) break;
                         tc_fence_after();
@@ -562,7 +564,7 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
             }
             if (!ok) break;
             // epilogue: this item's accumulator, [hi*hi + lo*hi | hi*lo]
-            ok = __all_sync(0xffffffffu, wait_or_abort(smem_addr(acc_full), (uint32_t)(it & 1), abort));
+            ok = __all_sync(0xffffffffu, wait_or_abort(smem_addr(acc_full), (uint32_t)(it & 1), abort, a.polls_spin));
             if (!ok) break;
             tc_fence_after();
             constexpr int GROUPS = NGEN / 32 / 4;  // warps sharing one lane quadrant
@@ -630,6 +632,9 @@ gyps_status run(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, doub
     a.ncols = 0;
     a.ks = (float)k;
     a.err = m->d_err;
+    const int wp = wait_polls_setting();
+    a.polls_spin = wp >= 0 ? wp : (1 << 22);
+    a.polls_sleep = wp >= 0 ? wp : (1 << 21);
     GYPS_CUDA(cudaFuncSetAttribute(far_tc_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     // one CTA per SM: each takes the whole tensor memory
     const int64_t grid = std::min<int64_t>((int64_t)m->num_sms, a.n_tiles * a.n_segs);

@@ -35,13 +35,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: gives up after a fixed number of polls (each poll may suspend
-// the thread for a short, hardware-defined time) instead of spinning forever.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+// Bounded wait: gives up after `polls` polls (each poll may suspend the thread
+// for a short, hardware-defined time) instead of spinning forever.
+constexpr int kDefaultWaitPolls = 1 << 22;
+__device__ __forceinline__ bool mbar_wait_polls(uint32_t bar, uint32_t parity, int polls)
 {
-    for (int n = 0; n < (1 << 22); ++n)
+    for (int n = 0; n < polls; ++n)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    return mbar_wait_polls(bar, parity, kDefaultWaitPolls);
 }
 
 // 1-D bulk copy global -> shared (TMA engine), completion counted on `bar`.
@@ -107,6 +112,7 @@ struct FarArgs {
     int64_t n_src_tiles, n_tgt_tiles;
     float ks;  // coordinate scale: k (1 for the Laplace kernel)
     int *err;
+    int wait_polls;  // poll limit of the pipeline waits (the drain after a failure keeps the default)
 };
 
 template <int R, int T>

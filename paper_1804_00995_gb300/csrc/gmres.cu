@@ -444,6 +444,7 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
         S.deadline = std::chrono::steady_clock::now() +
                      std::chrono::microseconds((int64_t)std::min(o.timeout_ms * 1e3, 9.0e15));
     }
+    GYPS_TRY(clear_err_word(m, s));  // report only the waits of this solve's launches
     S.grid_v = dim3((unsigned)((n + 255) / 256), (unsigned)nrhs);
     S.grid_r = dim3((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)nrhs);
     const size_t blk = (size_t)n * nrhs * sizeof(double2);

@@ -153,6 +153,12 @@ gyps_status enter_device(const Mesh *m);
 bool is_device_pointer(const void *p);
 // Reads (and clears) the error word of bounded device waits; TIMEOUT if set.
 gyps_status check_err_word(Mesh *m, cudaStream_t s);
+// Clears the error word on the stream, so that a synchronous call reports only
+// the waits of its own launches.
+gyps_status clear_err_word(Mesh *m, cudaStream_t s);
+// Poll limit of the pipeline waits in the far kernels launched from now on
+// (gyps_set_wait_polls; negative = each kernel's default).
+int wait_polls_setting();
 
 // ---------------------------------------------------------------- launchers
 // a1: quadrature points and the FP32 position panel

@@ -179,6 +179,7 @@ extern "C" gyps_status gyps_sl_potential(gyps_mesh_t h, double k, int64_t npts, 
     }
     double2 *pout = dP ? (double2 *)P : reinterpret_cast<double2 *>(st + bp + bx);
     const int64_t lpo = dP ? ldp : npts;
+    GYPS_TRY(clear_err_word(m, s));  // report only the waits of this call's launches
     GYPS_TRY(potential_device(m, k, npts, pd, nrhs, xd, lxd, pout, lpo, prec, s));
     if (!dP)
         GYPS_CUDA(cudaMemcpy2DAsync(P, ldp * sizeof(double2), pout, npts * sizeof(double2), npts * sizeof(double2), nrhs,

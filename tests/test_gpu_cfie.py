@@ -7,15 +7,12 @@ import pytest
 
 import oracle
 import synth
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 D = np.array([0.0, 0.0, 1.0])
-
-
-def rel(a, b):
-    return max(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c]) for c in range(b.shape[1]))
 
 
 @pytest.fixture(scope="module")

@@ -6,13 +6,10 @@ import pytest
 
 import synth
 from oracle import mpnn as omp
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-
-
-def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
 
 
 @pytest.fixture(scope="module")

@@ -6,13 +6,10 @@ import pytest
 
 import oracle
 import synth
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-
-
-def rel(a, b):
-    return max(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c]) for c in range(b.shape[1]))
 
 
 def _points(n, seed):

@@ -6,15 +6,12 @@ import pytest
 
 import oracle
 import synth
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 TC_TOL = 1e-4
-
-
-def rel(a, b):
-    return max(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c]) for c in range(a.shape[1]))
 
 
 @pytest.mark.parametrize("level,q,k,nrhs", [(1, 3, 5.0, 16), (2, 3, 16.0, 16), (2, 7, 9.0, 20), (3, 3, 30.0, 32), (3, 3, 12.0, 64), (2, 7, 7.0, 70)])
@@ -61,7 +58,8 @@ def test_tc_rejects_laplace_and_partial_ranges():
 @pytest.mark.slow
 def test_sphere163842_k64_q3_r16_sampled_rows():
     """Workload sphere163842_k64_q3_r16 at full size (983040 points, 16 plane
-    waves, seed 7): tensor-core apply vs the oracle on 48 sampled rows."""
+    waves, seed 7): tensor-core apply (16 columns) and the FP32 CUDA-core apply
+    (2 columns) vs the oracle on 48 sampled rows."""
     import paper_1804_00995_gb300 as g
     v, t = synth.icosphere(7)
     gm = g.Mesh(v, t, 3)
@@ -73,3 +71,6 @@ def test_sphere163842_k64_q3_r16_sampled_rows():
     rows = np.sort(np.random.default_rng(64).choice(om.nv, 48, replace=False))
     ref = om.apply(64.0, fh, rows=rows)[rows]
     assert rel(y[rows], ref) < TC_TOL
+    # the FP32 CUDA-core form at the same k (phases up to about 130 rad), two columns
+    y32 = g.sl_apply(gm, 64.0, f[:, :2], prec="fp32").cpu().numpy()
+    assert rel(y32[rows], ref[:, :2]) < 1e-5

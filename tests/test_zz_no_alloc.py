@@ -4,26 +4,25 @@ cudaMalloc and the synchronisation it can cause is not acceptable in their
 loop).  Its scratch is a fixed array inside the library, shared by all calls.
 
 Checked through the C ABI against gyps_sl_apply (FP32 far part, FP64
-correction) on two calls in a row with different inputs, so that a stale
-accumulator from the first call would show up in the second.  This file is
-collected last.
+correction) and against the FP64 oracle on two calls in a row with different
+inputs, so that a stale accumulator from the first call would show up in the
+second; device memory in use does not change over repeated calls.  This file
+is collected last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
+from parity import rel
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
 FP32_TOL = 1e-5  # relative, per column: the tolerance of the FP32 parity tests
-
-
-def _rel(a, b):
-    return max(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c]) for c in range(a.shape[1]))
 
 
 def _colmajor(x):
@@ -40,6 +39,7 @@ def test_noalloc_matches_apply_two_calls(level, q, k, nrhs):
     lib = g.load()
     v, t = synth.icosphere(level)
     mesh = g.Mesh(v, t, q)
+    om = oracle.Mesh(v, t, q)
     nv = mesh.nv
     for call in range(2):
         x = _colmajor(synth.random_complex(np.random.default_rng(100 * level + call), nv, nrhs))
@@ -53,7 +53,31 @@ def test_noalloc_matches_apply_two_calls(level, q, k, nrhs):
         torch.cuda.synchronize()
         a, b = y_new.cpu().numpy(), y_ref.cpu().numpy()
         assert np.isfinite(a).all()
-        assert _rel(a, b) < FP32_TOL, (call, _rel(a, b))
+        assert rel(a, b) < FP32_TOL, (call, rel(a, b))
+        # and against the FP64 oracle on the same input
+        assert rel(a, om.apply(k, x.cpu().numpy())) < FP32_TOL, call
+        assert lib.gyps_mesh_check(mesh.handle, _stream()) == 0
+    mesh.close()
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After a first call (which looks up the scratch array's address), further
+    calls leave the device's free memory unchanged."""
+    import paper_1804_00995_gb300 as g
+    lib = g.load()
+    v, t = synth.icosphere(3)
+    mesh = g.Mesh(v, t, 3)
+    nv = mesh.nv
+    x = _colmajor(synth.random_complex(np.random.default_rng(5), nv, 3))
+    y = torch.empty((3, nv), dtype=torch.complex128, device="cuda").t()
+    assert lib.gyps_sl_apply_noalloc(mesh.handle, 7.0, 3, x.data_ptr(), nv, y.data_ptr(), nv, _stream()) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        assert lib.gyps_sl_apply_noalloc(mesh.handle, 7.0, 3, x.data_ptr(), nv, y.data_ptr(), nv, _stream()) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
     mesh.close()
 
 
