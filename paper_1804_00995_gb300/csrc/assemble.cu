@@ -7,29 +7,8 @@
 namespace gyps {
 
 constexpr double kInv4PiA = 0.0795774715459476678844418816862571810;
-constexpr double kTwoPiA = 6.283185307179586476925286766559;
 
-__device__ __forceinline__ float mufu_rsqrt(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float mufu_sin(float x)
-{
-    float y;
-    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float mufu_cos(float x)
-{
-    float y;
-    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Kernel value exp(ik r)/r between two points, FP64 or FP32 arithmetic.
-template <bool FP64>
+// Kernel value exp(ik r)/r between two points in FP64.
 __device__ __forceinline__ void kernel_value(double4_32a x, double4_32a y, double k, double &gr, double &gi)
 {
     double dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
@@ -39,18 +18,6 @@ __device__ __forceinline__ void kernel_value(double4_32a x, double4_32a y, doubl
     sincos(k * (r2 * ri), &sn, &cs);
     gr = cs * ri;
     gi = sn * ri;
-}
-
-__device__ __forceinline__ void kernel_value(float4 x, float4 y, float kt, float &gr, float &gi)
-{
-    float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
-    float r2 = dx * dx + dy * dy + dz * dz;
-    float rs = mufu_rsqrt(r2);
-    float t = r2 * rs * kt;  // k r / (2 pi)
-    float f = t - rintf(t);
-    float ang = f * 6.28318530717958647692f;
-    gr = mufu_cos(ang) * rs;
-    gi = mufu_sin(ang) * rs;
 }
 
 // a6, FP64: one thread per (test triangle a, trial triangle b); the 3x3 block
@@ -79,7 +46,7 @@ __global__ void assemble_far64_kernel(const double4_32a *pts64, const int32_t *t
                 gr = 0.0;
                 gi = k;
             } else {
-                kernel_value<true>(x, y, k, gr, gi);
+                kernel_value(x, y, k, gr, gi);
             }
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
@@ -110,72 +77,6 @@ __global__ void assemble_far64_kernel(const double4_32a *pts64, const int32_t *t
     }
 }
 
-// a6, FP32 kernel values: one thread per (test vertex i, trial triangle b):
-//   V[i, v_j(b)] += (1/4pi) sum_{a ni i} sum_{k in a, l in b} w_k lambda_i(x_k) G(x_k, y_l) eta_l lambda_j(y_l).
-// The thread walks the quadrature points of the triangles around i (vertex
-// incidence CSR); consecutive threads hold consecutive vertices, so a warp's
-// atomics for one entry column hit consecutive addresses.  Each Gauss-pair
-// value is computed once per vertex of its test triangle (three times), which
-// the MUFU unit absorbs: against one thread per triangle pair (nine scattered
-// atomics per pair) this takes 47 ms instead of 83 on the 10242-vertex sphere,
-// and against one thread per entry (no atomics, nine evaluations per value)
-// 47 ms instead of 110.  Sums in FP32 over the about 6 q^2 terms of an entry's
-// share, added into V in FP64.
-template <int Q>
-__global__ void assemble_vt32_kernel(const int32_t *v2t_ptr, const int32_t *v2t, const double4_32a *pts64,
-                                     const int32_t *tri, const Rule rule, int64_t nv, double k, double2 *V,
-                                     int64_t ldv)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t b = blockIdx.y;
-    if (i >= nv) return;
-    const float kt = (float)(k / kTwoPiA);
-    float4 y[Q];
-    float d[Q][3];  // eta_l lambda_j(y_l)
-#pragma unroll
-    for (int lq = 0; lq < Q; ++lq) {
-        const double4_32a p = pts64[b * Q + lq];
-        y[lq] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) d[lq][j] = (float)p.w * (float)rule.bary[3 * lq + j];
-    }
-    float sr[3] = {0.0f, 0.0f, 0.0f}, si[3] = {0.0f, 0.0f, 0.0f};
-    for (int32_t e = v2t_ptr[i]; e < v2t_ptr[i + 1]; ++e) {
-        const int32_t te = v2t[e];
-        const int64_t a = te / 3;
-        const int m = te - 3 * (int)a;
-#pragma unroll
-        for (int kq = 0; kq < Q; ++kq) {
-            const double4_32a x = pts64[a * Q + kq];
-            const float4 xf = make_float4((float)x.x, (float)x.y, (float)x.z, 0.0f);
-            const float c = (float)x.w * (float)rule.bary[3 * kq + m];
-#pragma unroll
-            for (int lq = 0; lq < Q; ++lq) {
-                float gr, gi;
-                if (a == b && kq == lq) {
-                    gr = 0.0f;
-                    gi = (float)k;
-                } else {
-                    kernel_value(xf, y[lq], kt, gr, gi);
-                }
-                gr *= c;
-                gi *= c;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    sr[j] += gr * d[lq][j];
-                    si[j] += gi * d[lq][j];
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        double *dst = reinterpret_cast<double *>(V + i + (int64_t)tri[3 * b + j] * ldv);
-        atomicAdd(dst, (double)sr[j] * kInv4PiA);
-        atomicAdd(dst + 1, (double)si[j] * kInv4PiA);
-    }
-}
-
 // V[i, c] += C_ic (each nonzero once: no atomics needed).
 __global__ void assemble_near_kernel(const int32_t *rowptr, const int32_t *col, const double *val, int64_t nv,
                                      double2 *V, int64_t ldv)
@@ -187,14 +88,12 @@ __global__ void assemble_near_kernel(const int32_t *rowptr, const int32_t *col, 
 
 gyps_status assemble_device(Mesh *m, double k, int prec, double2 *V, int64_t ldv, cudaStream_t s)
 {
-    GYPS_CUDA(cudaMemset2DAsync(V, ldv * sizeof(double2), 0, m->nv * sizeof(double2), m->nv, s));
-    if (prec == GYPS_PREC_FP64) {
+    if (prec == GYPS_PREC_FP32) {
+        GYPS_TRY(assemble_tiles(m, k, V, ldv, s));  // writes every entry of V once
+    } else {
+        GYPS_CUDA(cudaMemset2DAsync(V, ldv * sizeof(double2), 0, m->nv * sizeof(double2), m->nv, s));
         dim3 g((unsigned)((m->nt + 127) / 128), (unsigned)m->nt);  // x: test triangles, y: trial triangle
         assemble_far64_kernel<<<g, 128, 0, s>>>(m->d_pts64, m->d_tri, m->rule, m->nt, k, V, ldv);
-    } else {
-        dim3 g((unsigned)((m->nv + 127) / 128), (unsigned)m->nt);  // x: test vertices, y: trial triangle
-        auto kern = m->q == 1 ? assemble_vt32_kernel<1> : m->q == 3 ? assemble_vt32_kernel<3> : assemble_vt32_kernel<7>;
-        kern<<<g, 128, 0, s>>>(m->d_v2t_ptr, m->d_v2t, m->d_pts64, m->d_tri, m->rule, m->nv, k, V, ldv);
     }
     GYPS_CUDA(cudaGetLastError());
     assemble_near_kernel<<<(unsigned)((m->nv + 127) / 128), 128, 0, s>>>(m->d_c_rowptr, m->d_c_col, m->d_c_val, m->nv,
@@ -273,7 +172,8 @@ extern "C" gyps_status gyps_sl_assemble(gyps_mesh_t h, double k, int prec, void 
     if (!std::isfinite(k) || k < 0.0) return set_error(GYPS_ERR_INVALID, "k must be finite and >= 0");
     if (prec != GYPS_PREC_FP64 && prec != GYPS_PREC_FP32)
         return set_error(GYPS_ERR_UNSUPPORTED, "dense assembly supports FP64 and FP32");
-    if (m->nt > 65535) return set_error(GYPS_ERR_UNSUPPORTED, "dense assembly limited to 65535 triangles");
+    if (prec == GYPS_PREC_FP64 && m->nt > 65535)
+        return set_error(GYPS_ERR_UNSUPPORTED, "FP64 dense assembly limited to 65535 triangles");
     cudaStream_t s = (cudaStream_t)stream;
     if (is_device_pointer(V)) return assemble_device(m, k, prec, (double2 *)V, ldv, s);
     const size_t bytes = (size_t)m->nv * m->nv * sizeof(double2);

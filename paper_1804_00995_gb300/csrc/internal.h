@@ -49,6 +49,9 @@ struct Rule {
 };
 
 // ---------------------------------------------------------------- mesh
+struct VertexTiles;  // vtiles.h
+void free_vertex_tiles(VertexTiles *T);
+
 struct Mesh {
     int device = 0;
     int64_t nv = 0, nt = 0, nq = 0;
@@ -110,6 +113,7 @@ struct Mesh {
     int32_t *d_adj_ptr = nullptr, *d_adj = nullptr;       // vertex neighbours over mesh edges
     float *d_vfeat = nullptr;                             // nv x 6: centred coordinates, unit normal
     double h_mean = 0.0;                                  // mean edge length
+    VertexTiles *vt = nullptr;                            // vertex tiles of the dense blocks (built on first use)
     int64_t device_bytes = 0;
     int num_sms = 0;
 
@@ -208,6 +212,8 @@ gyps_status combined_apply_device(Mesh *m, double k, double eta, bool adj, int n
 
 // a6, a7
 gyps_status assemble_device(Mesh *m, double k, int prec, double2 *V, int64_t ldv, cudaStream_t s);
+// a6 with FP32 kernel values by vertex-tile blocks (the Gauss-Gauss part only; C is added by the caller)
+gyps_status assemble_tiles(Mesh *m, double k, double2 *V, int64_t ldv, cudaStream_t s);
 // F = int phi (exp(ik d.x)), or with cfie: int phi (d/dn - i eta) exp(ik d.x)
 gyps_status rhs_device(Mesh *m, double k, int nrhs, const double *dirs_host, double2 *F, int64_t ldf,
                        cudaStream_t s, bool cfie = false, double eta = 0.0);

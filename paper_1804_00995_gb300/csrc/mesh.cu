@@ -308,6 +308,7 @@ static void free_mesh(Mesh *m)
                     m->d_efie_blocks, m->d_mfie_blocks};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    free_vertex_tiles(m->vt);
     delete m;
 }
 
