@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "batch12_r64", "precond_ellipsoids", "sphere163842_k64_q3_r16",
                             "assemble_sphere10242", "field_sphere10242_k16", "dl_sphere10242_k16_q7",
-                            "efie_sphere10242_k8_q3"])
+                            "efie_sphere10242_k8_q3", "hmat_sphere163842_k64_q3_r16"])
     p.add_argument("--precond-meshes", type=int, default=125, help="training meshes (16 solves each)")
     p.add_argument("--precond-steps", type=int, default=3000)
     p.add_argument("--precond-test", type=int, default=8)
@@ -71,6 +71,9 @@ def parse():
     p.add_argument("--precond-file", default="",
                    help="sphere163842_k64_q3_r16 --solve: learned preconditioner saved by --save-precond")
     p.add_argument("--solve-maxit", type=int, default=1500)
+    p.add_argument("--hmat-eps", type=float, default=1e-5, help="hmat workload: tolerance of the low-rank blocks")
+    p.add_argument("--hmat-leaf", type=int, default=16, help="hmat workload: vertex tiles per cluster")
+    p.add_argument("--hmat-eta", type=float, default=1.0, help="hmat workload: admissibility parameter")
     return p.parse_args()
 
 
@@ -384,6 +387,32 @@ def run_gyps(args, rank, world, local_rank):
         solve["brakhage_werner"] = {"s": time.perf_counter() - t0, "eta": k, "iterations": repb.iterations,
                                     "refinements": repb.refinements,
                                     "true_residual_df64": float(repb.true_residual[0]), "status": repb.status}
+        # The plain FP64 GPU form (FP64 operator and checks) takes minutes here, so the default
+        # line times it over a bounded number of iterations and takes its iteration count from
+        # GMRES with the double-float operator (within 1e-13 of the FP64 operator, so it follows
+        # the same Krylov path); --solve-fp64 runs it to the end instead.
+        def timed_fp64(maxit):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            g.gmres_solve(mesh, k, f, tol=cfg["tol"], restart=200, maxit=maxit, prec="fp64", check_prec="fp64",
+                          max_refine=0)
+            torch.cuda.synchronize(dev)
+            return time.perf_counter() - t0
+        t1, t5 = timed_fp64(1), timed_fp64(5)
+        t_iter = (t5 - t1) / 4.0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, repd = g.gmres_solve(mesh, k, f, tol=cfg["tol"], restart=200, maxit=2000, prec="df64",
+                                check_prec="df64", max_refine=0)
+        torch.cuda.synchronize(dev)
+        t_df = time.perf_counter() - t0
+        fp64_est = t1 + (repd.iterations - 1) * t_iter
+        solve.update({"fp64_s_est": fp64_est, "fp64_per_iteration_s": t_iter, "fp64_iterations_est": repd.iterations,
+                      "fp64_est_basis": "plain FP64 GMRES timed over 1 and 5 iterations; iterations of the "
+                                        "double-float-operator solve (FP64-class operator, same Krylov path)",
+                      "df64_s": t_df, "df64_iterations": repd.iterations,
+                      "df64_true_residual": float(repd.true_residual[0]), "df64_status": repd.status,
+                      "speedup_vs_fp64_est": fp64_est / t_solve})
         if args.solve_fp64:
             t0 = time.perf_counter()
             _, rep64 = g.gmres_solve(mesh, k, f, tol=cfg["tol"], restart=200, maxit=2000, prec="fp64",
@@ -976,12 +1005,86 @@ def run_large(args):
     print(json.dumps(line), flush=True)
 
 
+def run_hmat(args):
+    """Workload hmat_sphere163842_k64_q3_r16: the compressed far field of the
+    icosphere with 327680 triangles (q = 3, 983040 points) at k = 64 (eps 1e-5,
+    clusters of 16 vertex tiles, eta 1), 16 plane waves.  One step = one apply
+    of H + C to all 16 columns.  Reported: build time, stored bytes against the
+    dense matrix, ranks, the apply time next to one tensor-core all-pairs apply
+    of the same columns, and the difference to the FP32 all-pairs apply on two
+    full columns (norm and largest element, relative)."""
+    import torch
+
+    import paper_1804_00995_gb300 as g
+    from paper_1804_00995_gb300 import build as gb
+    gb.build()
+    cfg = synth.WORKLOADS["sphere163842_k64_q3_r16"]
+    v, t = synth.icosphere(cfg["level"])
+    mesh = g.Mesh(v, t, cfg["q"])
+    k = cfg["k"]
+    dirs = synth.plane_wave_dirs(np.random.default_rng(cfg["seed"]), cfg["ndirs"])
+    x = g.rhs_planewave(mesh, k, dirs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = g.Hmat(mesh, k, eps=args.hmat_eps, leaf_tiles=args.hmat_leaf, eta=args.hmat_eta)
+    build_s = time.perf_counter() - t0
+    y = h.apply(x)
+    for _ in range(args.warmup):
+        h.apply(x, out=y)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(0)
+    clocks = ClockSampler(smi_id_of(props))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        h.apply(x, out=y)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    # the all-pairs forms for comparison: one tensor-core apply of the 16 columns, FP32 on two columns
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ytc = g.sl_apply(mesh, k, x, prec="tc_bf16x3")
+    e0.record(stream)
+    g.sl_apply(mesh, k, x, prec="tc_bf16x3", out=ytc)
+    e1.record(stream)
+    y32 = g.sl_apply(mesh, k, x[:, :2].contiguous(), prec="fp32")
+    torch.cuda.synchronize()
+    tc_ms = e0.elapsed_time(e1)
+    a, b = y[:, :2].cpu().numpy(), y32.cpu().numpy()
+    err_norm = max(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(b[:, c]) for c in range(2))
+    err_elem = max(np.abs(a[:, c] - b[:, c]).max() / np.abs(b[:, c]).max() for c in range(2))
+    info = h.info
+    pairs = float(mesh.nq) ** 2
+    line = {
+        "metric": "compressed far field: ms per 16-column apply", "value": ms, "unit": "ms",
+        "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+        "dtype": "f32 blocks, f64 correction and output",
+        "config": {"workload": "hmat_sphere163842_k64_q3_r16", "nv": mesh.nv, "nq": mesh.nq, "k": k, "nrhs": 16,
+                   "eps": args.hmat_eps, "leaf_tiles": args.hmat_leaf, "eta": args.hmat_eta,
+                   "l2": "blocks (tens of GB) larger than L2"},
+        "build_s": build_s, "hmat": info, "compression": info["bytes"] / info["dense_bytes"],
+        "stream_gbs": info["bytes"] / (ms * 1e-3) / 1e9,
+        "equivalent_gpairs_per_s": pairs / (ms * 1e-3) / 1e9,
+        "tensor_core_all_pairs_ms": tc_ms, "speedup_vs_tensor_core_all_pairs": tc_ms / ms,
+        "diff_vs_fp32_all_pairs": {"columns": 2, "norm": err_norm, "element": err_elem},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
 def run_assemble(args):
     """Workload assemble_sphere10242: dense Galerkin matrix (a6) of the icosphere
     with 20480 triangles (10242 vertices), q = 3, k = 16: Nv^2 complex entries
-    (1.68 GB), triangle-pair blocks with FP64 accumulation, plus the correction;
-    kernel values in FP32 (MUFU) or FP64.  Reported: assembly time, the bytes of
-    V written per second (16 Nv^2 / t) and Gauss pairs per second."""
+    (1.68 GB) plus the correction.  FP32 kernel values: vertex-tile blocks, each
+    entry written once (the complex-symmetric Gauss-Gauss part computed for tile
+    pairs I <= J); FP64: triangle-pair blocks with FP64 atomics.  Reported:
+    assembly time, Gauss pairs per second (Nq^2 / t, the algorithmic count) against
+    the MUFU roof, and the bytes of V written per second (16 Nv^2 / t)."""
     import torch
 
     import paper_1804_00995_gb300 as g
@@ -993,7 +1096,9 @@ def run_assemble(args):
     props = torch.cuda.get_device_properties(0)
     out = {}
     for prec in ("fp32", "fp64"):
-        V = g.sl_assemble(mesh, k, prec=prec)
+        V = g.sl_assemble(mesh, k, prec=prec)  # warm-up (first FP32 call builds the vertex tiles)
+        for _ in range(max(args.warmup - 1, 0)):
+            g.sl_assemble(mesh, k, prec=prec, out=V)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         stream = torch.cuda.current_stream()
@@ -1002,7 +1107,7 @@ def run_assemble(args):
         time.sleep(0.3)
         for i in range(args.steps):
             ev[i][0].record(stream)
-            g.sl_assemble(mesh, k, prec=prec)
+            g.sl_assemble(mesh, k, prec=prec, out=V)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop()
@@ -1010,10 +1115,19 @@ def run_assemble(args):
         out[prec] = {"ms": ms, "v_write_gbs": 16.0 * mesh.nv ** 2 / (ms * 1e-3) / 1e9,
                      "gauss_pairs_per_s": float(mesh.nq) ** 2 / (ms * 1e-3), "clocks": clk}
         del V
+    try:
+        peak_mhz = json.loads(read_text(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
+    except Exception:
+        peak_mhz = 2070.0
+    sfu = sm_peak_pairs(props.multi_processor_count, peak_mhz) / 1e9
+    gp = out["fp32"]["gauss_pairs_per_s"] / 1e9
     line = {
         "metric": "dense single-layer assembly (a6): ms, V bytes written per second", "value": out["fp32"]["ms"],
         "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "data": "synthetic",
-        "dtype": "f32 kernel values, f64 sums",
+        "dtype": "f32 kernel values and sums, f64 output",
+        "roofline": {"bound": "alu", "achieved": gp, "peak": sfu, "unit": UNIT, "frac": gp / sfu,
+                     "peak_basis": f"{props.multi_processor_count} SMs x 16/3 pairs/clk x {peak_mhz:.0f} MHz",
+                     "kernel": "tile_block_kernel<3,false,double2>", "traffic": None},
         "config": {"workload": "assemble_sphere10242", "nv": mesh.nv, "nt": mesh.nt, "q": 3, "k": k,
                    "v_bytes": 16 * mesh.nv ** 2},
         "fp32": out["fp32"], "fp64": out["fp64"],
@@ -1037,6 +1151,9 @@ def main():
         return
     if args.workload == "sphere163842_k64_q3_r16":
         run_large(args)
+        return
+    if args.workload == "hmat_sphere163842_k64_q3_r16":
+        run_hmat(args)
         return
     if args.workload == "batch12_r64":
         run_batch(args)

@@ -504,6 +504,65 @@ gyps_status gyps_batch_info(gyps_batch_t batch, gyps_batch_info_t *info);
  * of its applies ran out of polls.  NULL is accepted. */
 gyps_status gyps_batch_destroy(gyps_batch_t batch);
 
+/* ------------------------------------------------------------------------
+ * Compressed far field (Sec. 5.3: the BEM matrix assembled directly in a
+ * compressed block form to a tolerance, so that larger problems fit and apply
+ * faster than the dense or all-pairs forms).  One level of a cluster tree:
+ * clusters are runs of `leaf_tiles` tiles of 64 vertices along a Morton curve
+ * (compact surface patches); the block of the Gauss-Gauss part
+ * (1/4pi) Phi^T W G W Phi between clusters A and B is stored dense (FP32
+ * complex) when dist(box A, box B) < eta max(diam A, diam B), the boxes
+ * covering the clusters' basis-function supports, and otherwise as U W^T from
+ * the adaptive cross approximation with partial pivoting (Bebendorf 2000),
+ * stopped when the newest term is below eps times the Frobenius norm of the
+ * approximation and spot-checked on 256 entries; a block that does not
+ * compress within min(m, n)/2 terms is kept dense.  The far part is complex
+ * symmetric, so only blocks A <= B are built; (B, A) uses the transpose.
+ * Blocks are generated on the device from the same Gauss-point kernel as the
+ * dense assembly (FP32 kernel values); the correction C stays FP64 and sparse.
+ * ------------------------------------------------------------------------ */
+typedef struct gyps_hmat_s *gyps_hmat_t;
+
+typedef struct {
+    int64_t clusters;
+    int64_t dense_blocks;     /* blocks stored dense (A <= B), fallbacks included */
+    int64_t lowrank_blocks;   /* blocks stored as U W^T (A < B) */
+    int64_t fallback_blocks;  /* admissible blocks that did not compress (kept dense) */
+    int32_t max_rank;
+    int32_t reserved;
+    double mean_rank;
+    int64_t bytes;            /* device memory held (blocks, factors, plan, workspaces) */
+    double dense_bytes;       /* the full nv x nv FP32 complex matrix, for comparison */
+    double build_ms;          /* wall time of gyps_hmat_create */
+} gyps_hmat_info_t;
+
+/*
+ * Builds the compressed far part of V for wavenumber k on `mesh` (synchronous).
+ *   eps  relative tolerance of the low-rank blocks, 1e-7 <= eps < 1.
+ *   leaf_tiles  tiles (of 64 vertices) per cluster, 1..64.
+ *   eta  admissibility parameter (> 0; larger = fewer, farther low-rank blocks).
+ * Errors: INVALID, OOM (the blocks did not fit), CUDA.
+ */
+gyps_status gyps_hmat_create(gyps_mesh_t mesh, double k, double eps, int leaf_tiles, double eta, void *stream,
+                             gyps_hmat_t *out);
+
+/*
+ * Y = (H + C) X: the compressed far part plus the FP64 correction, nrhs
+ * columns (1..4096) of nv complex double2, leading dimensions >= nv, X and Y
+ * not overlapping.  Device buffers: asynchronous on `stream`; host buffers:
+ * staged, returns when Y is on the host.  X is rounded to FP32 for the block
+ * products; the sums of a row are carried as error-free FP32 pairs and written
+ * in FP64.  Errors: INVALID, OOM, CUDA.
+ */
+gyps_status gyps_hmat_apply(gyps_hmat_t h, int nrhs, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                            void *stream);
+
+/* Sizes, ranks, memory and build time. info: HOST. */
+gyps_status gyps_hmat_info(gyps_hmat_t h, gyps_hmat_info_t *info);
+
+/* Releases the blocks (synchronises the device first). NULL is accepted. */
+gyps_status gyps_hmat_destroy(gyps_hmat_t h);
+
 /*
  * gyps_sl_apply without any device allocation (the paper has no counterpart:
  * this is a library service).  For callers that must not allocate device

@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "PREC", "GypsError", "Mesh", "load", "sl_apply", "near_correct", "sl_assemble", "rhs_planewave",
-    "gmres_solve", "version", "set_wait_polls",
+    "gmres_solve", "version", "set_wait_polls", "Hmat",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -62,6 +62,13 @@ class _BatchInfo(ctypes.Structure):
                 ("targets_per_thread", ctypes.c_int32), ("grid", ctypes.c_int32), ("uses_graph", ctypes.c_int32),
                 ("tuned", ctypes.c_int32), ("tensor_cores", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("work_items", ctypes.c_int64), ("pairs", ctypes.c_double)]
+
+
+class _HmatInfo(ctypes.Structure):
+    _fields_ = [("clusters", ctypes.c_int64), ("dense_blocks", ctypes.c_int64), ("lowrank_blocks", ctypes.c_int64),
+                ("fallback_blocks", ctypes.c_int64), ("max_rank", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mean_rank", ctypes.c_double), ("bytes", ctypes.c_int64), ("dense_bytes", ctypes.c_double),
+                ("build_ms", ctypes.c_double)]
 
 
 class _GmresOpts(ctypes.Structure):
@@ -133,6 +140,12 @@ _SIGS = {
     "gyps_batch_info": ([ctypes.c_void_p, ctypes.POINTER(_BatchInfo)], ctypes.c_int),
     "gyps_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "gyps_mesh_check": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "gyps_hmat_create": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "gyps_hmat_apply": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                         ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
+    "gyps_hmat_info": ([ctypes.c_void_p, ctypes.POINTER(_HmatInfo)], ctypes.c_int),
+    "gyps_hmat_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "gyps_set_wait_polls": ([ctypes.c_int64], ctypes.c_int),
     "gyps_sl_apply_noalloc": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
@@ -337,12 +350,17 @@ def near_correct(mesh: Mesh, X, Y, stream=None):
     return Y
 
 
-def sl_assemble(mesh: Mesh, k: float, prec: str = "fp64", device=None, stream=None):
-    """Dense V (nv, nv) complex128, column-major, V[i, j] = test i, trial j (gyps_sl_assemble)."""
-    dev = mesh.device if device is None else device
-    v = _empty_colmajor(mesh.nv, mesh.nv, dev)
-    _check(load().gyps_sl_assemble(mesh.handle, float(k), PREC[prec], v.data_ptr(), mesh.nv, _stream(stream)))
-    return v
+def sl_assemble(mesh: Mesh, k: float, prec: str = "fp64", device=None, out=None, stream=None):
+    """Dense V (nv, nv) complex128, column-major, V[i, j] = test i, trial j (gyps_sl_assemble).
+    out: a column-major (nv, nv) complex128 tensor to assemble into."""
+    if out is None:
+        dev = mesh.device if device is None else device
+        out = _empty_colmajor(mesh.nv, mesh.nv, dev)
+    elif out.stride(0) != 1 or tuple(out.shape) != (mesh.nv, mesh.nv):
+        raise ValueError("out must be a column-major (nv, nv) tensor")
+    _check(load().gyps_sl_assemble(mesh.handle, float(k), PREC[prec], out.data_ptr(), max(out.stride(1), mesh.nv),
+                                   _stream(stream)))
+    return out
 
 
 def dl_apply(mesh: Mesh, k: float, X, prec: str = "fp32", stream=None):
@@ -491,6 +509,50 @@ def rhs_planewave_cfie(mesh: Mesh, k: float, eta: float, dirs, device=None, stre
     _check(load().gyps_rhs_planewave_cfie(mesh.handle, float(k), float(eta), dirs.shape[0], dirs.ctypes.data,
                                           f.data_ptr(), mesh.nv, _stream(stream)))
     return f
+
+
+class Hmat:
+    """Compressed far field of the single layer plus the correction
+    (gyps_hmat_create / apply): Y = (H + C) X, H the block low-rank Gauss-Gauss
+    part to relative tolerance eps."""
+
+    def __init__(self, mesh: "Mesh", k: float, eps: float = 1e-5, leaf_tiles: int = 16, eta: float = 1.0,
+                 stream=None):
+        self.mesh = mesh
+        self.k = float(k)
+        h = ctypes.c_void_p()
+        _check(load().gyps_hmat_create(mesh.handle, self.k, float(eps), int(leaf_tiles), float(eta), _stream(stream),
+                                       ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def info(self) -> dict:
+        i = _HmatInfo()
+        _check(load().gyps_hmat_info(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in _HmatInfo._fields_}
+
+    def apply(self, X, out=None, stream=None):
+        one = (hasattr(X, "dim") and X.dim() == 1) or (not hasattr(X, "dim") and np.asarray(X).ndim == 1)
+        x, nrhs, ldx = _colmajor(X, self.mesh.nv, "X")
+        y = out if out is not None else _empty_colmajor(self.mesh.nv, nrhs, x.device)
+        if y.stride(0) != 1:
+            raise ValueError("out must be column-major")
+        _check(load().gyps_hmat_apply(self._h, nrhs, x.data_ptr(), ldx, y.data_ptr(),
+                                      max(y.stride(1), self.mesh.nv) if nrhs > 1 else self.mesh.nv, _stream(stream)))
+        return y[:, 0] if one else y
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            code = _lib.gyps_hmat_destroy(self._h)
+            self._h = None
+            _check(code)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

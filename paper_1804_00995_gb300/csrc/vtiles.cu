@@ -23,6 +23,7 @@
 // 2 pi, MUFU rsqrt / sin / cos) and FP32 sums; the block is scaled by k/(4 pi)
 // and converted when it is written.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <numeric>
@@ -44,6 +45,79 @@ static uint32_t spread10(uint32_t v)
     v = (v | (v << 4)) & 0x030C30C3u;
     v = (v | (v << 2)) & 0x09249249u;
     return v;
+}
+
+// The six orders of a triangle's vertices: kPerm[p][m] = original vertex at position m.
+static const int kPerm[6][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {0, 2, 1}, {2, 1, 0}, {1, 0, 2}};
+
+// Orders each tile's triangle list as a strip (each next triangle shares as many
+// tile vertices as possible with the one before) and turns each triangle's
+// vertices so that a vertex shared with the previous triangle keeps its
+// position.  The kernel keeps one running sum per position in registers and
+// writes it to shared memory only when the vertex at that position changes
+// (flush bit m in byte 3 of the packed slots).
+void order_tile_triangles(VertexTiles &T)
+{
+    T.perm.assign(T.ntt, 0);
+    std::vector<int32_t> tri2, loc2;
+    for (int64_t I = 0; I < T.ntiles; ++I) {
+        const int64_t b = T.tile_ptr[I], n = T.tile_ptr[I + 1] - b;
+        std::vector<std::array<int, 3>> sl(n);
+        for (int64_t e = 0; e < n; ++e)
+            for (int m = 0; m < 3; ++m) sl[e][m] = (int)((T.loc[b + e] >> (8 * m)) & 255) - 1;
+        auto shared = [&](int64_t x, int64_t y) {
+            int c = 0;
+            for (int m = 0; m < 3; ++m)
+                for (int mm = 0; mm < 3; ++mm) c += sl[x][m] >= 0 && sl[x][m] == sl[y][mm];
+            return c;
+        };
+        std::vector<char> seen(n, 0);
+        std::vector<int64_t> order;
+        order.reserve(n);
+        int64_t cur = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            seen[cur] = 1;
+            order.push_back(cur);
+            int64_t best = -1;
+            int bs = -1;
+            for (int64_t e = 0; e < n; ++e)
+                if (!seen[e]) {
+                    const int sc = shared(cur, e);
+                    if (sc > bs) {
+                        bs = sc;
+                        best = e;
+                    }
+                }
+            if (best < 0) break;
+            cur = best;
+        }
+        int prev[3] = {-1, -1, -1};
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t e = order[k];
+            int bp = 0, bm = -1;
+            for (int p = 0; p < 6; ++p) {
+                int match = 0;
+                for (int m = 0; m < 3; ++m) match += prev[m] >= 0 && sl[e][kPerm[p][m]] == prev[m];
+                if (match > bm) {
+                    bm = match;
+                    bp = p;
+                }
+            }
+            uint32_t packed = 0;
+            int cur3[3];
+            for (int m = 0; m < 3; ++m) {
+                cur3[m] = sl[e][kPerm[bp][m]];
+                packed |= (uint32_t)(cur3[m] + 1) << (8 * m);
+                if (cur3[m] != prev[m]) packed |= 1u << (24 + m);
+                prev[m] = cur3[m];
+            }
+            tri2.push_back(T.tri[b + e]);
+            loc2.push_back((int32_t)packed);
+            T.perm[b + k] = (int8_t)bp;
+        }
+    }
+    T.tri.swap(tri2);
+    T.loc.swap(loc2);
 }
 
 void build_vertex_tiles(const std::vector<double> &vtx, const std::vector<int32_t> &tri, int64_t nv, int64_t nt,
@@ -147,6 +221,9 @@ void build_vertex_tiles(const std::vector<double> &vtx, const std::vector<int32_
             }
         }
     }
+    T.adjacent.assign(adjacent.begin(), adjacent.end());
+    std::sort(T.adjacent.begin(), T.adjacent.end());
+    order_tile_triangles(T);
     T.max_tri = 0;
     for (int64_t t = 0; t < T.ntiles; ++t) T.max_tri = std::max<int64_t>(T.max_tri, cnt[t + 1] - cnt[t]);
     // items (I <= J), row by row: the target tile's panel stays in L2 over a row
@@ -155,44 +232,46 @@ void build_vertex_tiles(const std::vector<double> &vtx, const std::vector<int32_
     for (int32_t I = 0; I < (int32_t)T.ntiles; ++I)
         for (int32_t J = I; J < (int32_t)T.ntiles; ++J) {
             const int self = adjacent.count(((uint64_t)I << 32) | (uint64_t)J) ? 1 : 0;
-            T.items.push_back(make_int4(I, J, self, 0));
+            T.items.push_back(make_int4(I, J, self | 2, 0));
         }
 }
 
 // ---------------------------------------------------------------- device: panel
-// Per tile-triangle e and point l of its triangle: position scaled by ks with the
-// global point index in .w (as bits), and the coefficients w_l lambda_m(l) of the
-// triangle's vertices that belong to the tile (0 for the others).
-__global__ void tile_panel_kernel(const int32_t *tt_tri, const int32_t *tt_loc, int64_t ntt,
-                                  const double4_32a *pts64, const Rule rule, float ks, float4 *pos, float4 *coef)
+// Per tile-triangle e and point l (in the order of the triangle's turned
+// vertices): the point scaled by ks and negated (a source point enters through
+// one packed addition), with its global index in .w (bits); per tile-triangle
+// (packed slots and flush bits, area bits).  The coefficient w_l lambda_m(l) of
+// the vertex at position m is area x R[l][m] with R[l][m] = (reference weight
+// of l) x lambda_m(l) from the rule: the rules are symmetric under every order
+// of the vertices, so turning a triangle only permutes its points (sigma).
+__global__ void tile_panel_kernel(const int32_t *tt_tri, const int32_t *tt_loc, const int8_t *tt_perm, int64_t ntt,
+                                  const double4_32a *pts64, const Rule rule, const PointPerm pp, float ks, float4 *pos,
+                                  int2 *tl)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ntt * rule.q) return;
     const int64_t e = idx / rule.q;
     const int l = (int)(idx - e * rule.q);
-    const int64_t p = (int64_t)tt_tri[e] * rule.q + l;
+    const int64_t t = tt_tri[e];
+    const int64_t p = t * rule.q + pp.sigma[tt_perm[e]][l];  // the point that sits at position l after the turn
     const double4_32a x = pts64[p];
-    pos[idx] = make_float4((float)x.x * ks, (float)x.y * ks, (float)x.z * ks, __int_as_float((int)p));
-    const uint32_t loc = (uint32_t)tt_loc[e];
-    float c[3];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) c[m] = ((loc >> (8 * m)) & 255u) ? (float)(x.w * rule.bary[3 * l + m]) : 0.0f;
-    coef[idx] = make_float4(c[0], c[1], c[2], 0.0f);
+    const double area = pts64[t * rule.q].w / rule.w[0];
+    pos[idx] = make_float4(-(float)x.x * ks, -(float)x.y * ks, -(float)x.z * ks, __int_as_float((int)p));
+    if (l == 0) tl[e] = make_int2(tt_loc[e], __float_as_int((float)area));
 }
 
 // ---------------------------------------------------------------- device: blocks
 template <int Q>
 struct TileCfg {
     static constexpr int NT = 128;
-    static constexpr int TPP = NT / Q;         // target triangles per pass
-    static constexpr int PPP = TPP * Q;        // target points per pass
-    static constexpr int CH = Q == 7 ? 16 : 32;  // source triangles per staged chunk
-    static constexpr int HLD = NT + 1;         // padded row of H (float2)
-    static constexpr int VLD = kTileV + 1;     // padded row of Vacc (float2)
+    static constexpr int TPP = NT / Q;                          // target triangles per pass
+    static constexpr int SRC = Q == 3 ? 168 : Q == 7 ? 84 : 128;  // source triangles staged at once (multiple of 4)
+    static constexpr int HLD = NT + 1;                          // padded row of H (float2)
+    static constexpr int VLD = kTileV + 1;                      // padded row of Vacc (float2)
     static constexpr int H_BYTES = kTileV * HLD * 8;
     static constexpr int V_BYTES = kTileV * VLD * 8;
-    static constexpr int S_BYTES = CH * Q * 32 + CH * 4;  // one chunk: positions, coefficients, slots
-    static constexpr int T_BYTES = PPP * 16 + TPP * 4;    // test coefficients and slots of a pass
+    static constexpr int S_BYTES = SRC * Q * 16 + SRC * 8;       // staged source points, (triangle, slots)
+    static constexpr int T_BYTES = TPP * 8 + TPP * 4;            // (triangle, slots) and area of the pass's targets
     static constexpr int SMEM = H_BYTES + V_BYTES + S_BYTES + T_BYTES;
 };
 
@@ -222,54 +301,143 @@ __device__ __forceinline__ float2 to_out<float2>(float2 v, double scale)
     return make_float2((float)((double)v.x * scale), (float)((double)v.y * scale));
 }
 
-// Source-side sums of one target point against the staged chunk of triangles.
+// Running sums of one target point per vertex position (registers), written
+// into the thread's column of H when the vertex at that position changes.
+struct PosSums {
+    float2 a0, a1, a2;
+    int c0, c1, c2;  // slot held at each position (-1: none)
+};
+
+__device__ __forceinline__ void pos_flush(float2 *__restrict__ Hcol, int hld, int c, float2 &acc)
+{
+    if (c >= 0) {
+        const float2 o = Hcol[c * hld];
+        Hcol[c * hld] = make_float2(o.x + acc.x, o.y + acc.y);
+    }
+    acc = make_float2(0.f, 0.f);
+}
+
+// Kernel sums of one target point against two source triangles b0, b1 packed in
+// the lanes of f32x2 values: t_m = area sum_l G(x, y_l) R[l][m] for the three
+// vertex positions m of each triangle (lane .x: b0, lane .y: b1).
+struct PairSums {
+    float2 t0r, t0i, t1r, t1i, t2r, t2i;
+};
+
 template <int Q, bool LAP, bool SELF>
-__device__ __forceinline__ void chunk_sums(const float4 *spos, const float4 *scoef, const int *sloc, int nch,
-                                           float4 tp, int gk, float2 *Hcol)
+__device__ __forceinline__ PairSums pair_sums(const float4 *__restrict__ spos, int b0, int b1, float2 ar, float2 tx,
+                                              float2 ty, float2 tz, int gk, const float (&R)[Q][3])
+{
+    const float2 inv2pi = make_float2(0.159154943091895335769f, 0.159154943091895335769f);
+    const float2 mc1 = make_float2(-6.28318548202514648438f, -6.28318548202514648438f);  // -(2 pi in FP32)
+    const float2 mc2 = make_float2(1.74845553146951715e-07f, 1.74845553146951715e-07f);  // -(2 pi - that)
+    const float2 magic = make_float2(12582912.0f, 12582912.0f);    // 1.5 * 2^23: round to integer
+    const float2 nmagic = make_float2(-12582912.0f, -12582912.0f);
+    PairSums o;
+    o.t0r = o.t0i = o.t1r = o.t1i = o.t2r = o.t2i = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+        const float4 p0 = spos[b0 * Q + l], p1 = spos[b1 * Q + l];
+        const float2 dx = __fadd2_rn(tx, make_float2(p0.x, p1.x));
+        const float2 dy = __fadd2_rn(ty, make_float2(p0.y, p1.y));
+        const float2 dz = __fadd2_rn(tz, make_float2(p0.z, p1.z));
+        float2 r2 = __fmul2_rn(dx, dx);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        const float2 rs = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+        float2 gr, gi;
+        if (LAP) {
+            gr = rs;
+            if (SELF) {
+                if (__float_as_int(p0.w) == gk) gr.x = 0.0f;
+                if (__float_as_int(p1.w) == gk) gr.y = 0.0f;
+            }
+        } else {
+            const float2 ph = __fmul2_rn(r2, rs);                                  // k r
+            const float2 nr = __fadd2_rn(__ffma2_rn(ph, inv2pi, magic), nmagic);   // nearest integer to k r / (2 pi)
+            const float2 ang = __ffma2_rn(nr, mc2, __ffma2_rn(nr, mc1, ph));       // in [-pi, pi]
+            const float2 sn = make_float2(sin_mufu(ang.x), sin_mufu(ang.y));
+            const float2 cs = make_float2(cos_mufu(ang.x), cos_mufu(ang.y));
+            gr = __fmul2_rn(cs, rs);                                               // exp(ikr) / (k r)
+            gi = __fmul2_rn(sn, rs);
+            if (SELF) {  // the point paired with itself: ik / k
+                if (__float_as_int(p0.w) == gk) {
+                    gr.x = 0.0f;
+                    gi.x = 1.0f;
+                }
+                if (__float_as_int(p1.w) == gk) {
+                    gr.y = 0.0f;
+                    gi.y = 1.0f;
+                }
+            }
+        }
+        const float2 k0 = make_float2(R[l][0], R[l][0]), k1 = make_float2(R[l][1], R[l][1]),
+                     k2 = make_float2(R[l][2], R[l][2]);
+        o.t0r = __ffma2_rn(gr, k0, o.t0r);
+        o.t1r = __ffma2_rn(gr, k1, o.t1r);
+        o.t2r = __ffma2_rn(gr, k2, o.t2r);
+        if (!LAP) {
+            o.t0i = __ffma2_rn(gi, k0, o.t0i);
+            o.t1i = __ffma2_rn(gi, k1, o.t1i);
+            o.t2i = __ffma2_rn(gi, k2, o.t2i);
+        }
+    }
+    o.t0r = __fmul2_rn(o.t0r, ar);
+    o.t1r = __fmul2_rn(o.t1r, ar);
+    o.t2r = __fmul2_rn(o.t2r, ar);
+    o.t0i = __fmul2_rn(o.t0i, ar);
+    o.t1i = __fmul2_rn(o.t1i, ar);
+    o.t2i = __fmul2_rn(o.t2i, ar);
+    return o;
+}
+
+// Adds triangle (lane h of a pair) into the running sums, flushing the
+// positions whose vertex changes.
+__device__ __forceinline__ void pos_add(const PairSums &t, int h, uint32_t code, float2 *__restrict__ Hcol, int hld,
+                                        PosSums &ps)
+{
+    if (code & (1u << 24)) {
+        pos_flush(Hcol, hld, ps.c0, ps.a0);
+        ps.c0 = (int)(code & 255u) - 1;
+    }
+    if (code & (1u << 25)) {
+        pos_flush(Hcol, hld, ps.c1, ps.a1);
+        ps.c1 = (int)((code >> 8) & 255u) - 1;
+    }
+    if (code & (1u << 26)) {
+        pos_flush(Hcol, hld, ps.c2, ps.a2);
+        ps.c2 = (int)((code >> 16) & 255u) - 1;
+    }
+    ps.a0.x += h ? t.t0r.y : t.t0r.x;
+    ps.a0.y += h ? t.t0i.y : t.t0i.x;
+    ps.a1.x += h ? t.t1r.y : t.t1r.x;
+    ps.a1.y += h ? t.t1i.y : t.t1i.x;
+    ps.a2.x += h ? t.t2r.y : t.t2r.x;
+    ps.a2.y += h ? t.t2i.y : t.t2i.x;
+}
+
+// Source-side sums of one target point against the staged triangles, four at a
+// time (two independent packed pairs; the count is padded to a multiple of
+// four with far-away triangles of zero area), added into the running sums of
+// the vertex positions in list order.
+template <int Q, bool LAP, bool SELF>
+__device__ __forceinline__ void src_sums(const float4 *__restrict__ spos, const int2 *__restrict__ stl, int nst,
+                                         float4 tp, int gk, const float (&R)[Q][3], float2 *__restrict__ Hcol,
+                                         PosSums &ps)
 {
     constexpr int HLD = TileCfg<Q>::HLD;
-    const float inv2pi = 0.159154943091895335769f;
-    const float c1 = 6.28318548202514648438f;      // 2 pi rounded to FP32
-    const float c2 = -1.74845553146951715e-07f;   // 2 pi - c1
-    const float magic = 12582912.0f;              // 1.5 * 2^23: round to integer
-    for (int b = 0; b < nch; ++b) {
-        float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0;
-#pragma unroll
-        for (int l = 0; l < Q; ++l) {
-            const float4 p = spos[b * Q + l];
-            const float4 c = scoef[b * Q + l];
-            const float dx = tp.x - p.x, dy = tp.y - p.y, dz = tp.z - p.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float rs = rsqrt_mufu(r2);
-            float2 g;
-            if (LAP) {
-                g = make_float2(rs, 0.0f);
-                if (SELF && __float_as_int(p.w) == gk) g.x = 0.0f;
-            } else {
-                const float ph = r2 * rs;                                  // k r
-                const float nr = fmaf(ph, inv2pi, magic) - magic;          // nearest integer to k r / (2 pi)
-                const float ang = fmaf(nr, -c2, fmaf(nr, -c1, ph));        // in [-pi, pi]
-                g = make_float2(cos_mufu(ang) * rs, sin_mufu(ang) * rs);   // exp(ikr) / (k r)
-                if (SELF && __float_as_int(p.w) == gk) g = make_float2(0.0f, 1.0f);  // ik / k
-            }
-            cadd_scaled(s0, g, c.x);
-            cadd_scaled(s1, g, c.y);
-            cadd_scaled(s2, g, c.z);
-        }
-        const uint32_t loc = (uint32_t)sloc[b];
-        const int m0 = (int)(loc & 255u) - 1, m1 = (int)((loc >> 8) & 255u) - 1, m2 = (int)((loc >> 16) & 255u) - 1;
-        if (m0 >= 0) {
-            float2 h = Hcol[m0 * HLD];
-            Hcol[m0 * HLD] = make_float2(h.x + s0.x, h.y + s0.y);
-        }
-        if (m1 >= 0) {
-            float2 h = Hcol[m1 * HLD];
-            Hcol[m1 * HLD] = make_float2(h.x + s1.x, h.y + s1.y);
-        }
-        if (m2 >= 0) {
-            float2 h = Hcol[m2 * HLD];
-            Hcol[m2 * HLD] = make_float2(h.x + s2.x, h.y + s2.y);
-        }
+    const float2 tx = make_float2(tp.x, tp.x), ty = make_float2(tp.y, tp.y), tz = make_float2(tp.z, tp.z);
+    for (int b = 0; b < nst; b += 4) {
+        const int2 tl0 = stl[b], tl1 = stl[b + 1], tl2 = stl[b + 2], tl3 = stl[b + 3];
+        const PairSums pa = pair_sums<Q, LAP, SELF>(spos, b, b + 1, make_float2(__int_as_float(tl0.y), __int_as_float(tl1.y)),
+                                                    tx, ty, tz, gk, R);
+        const PairSums pb = pair_sums<Q, LAP, SELF>(spos, b + 2, b + 3,
+                                                    make_float2(__int_as_float(tl2.y), __int_as_float(tl3.y)), tx, ty,
+                                                    tz, gk, R);
+        pos_add(pa, 0, (uint32_t)tl0.x, Hcol, HLD, ps);
+        pos_add(pa, 1, (uint32_t)tl1.x, Hcol, HLD, ps);
+        pos_add(pb, 0, (uint32_t)tl2.x, Hcol, HLD, ps);
+        pos_add(pb, 1, (uint32_t)tl3.x, Hcol, HLD, ps);
     }
 }
 
@@ -282,11 +450,26 @@ __global__ void __launch_bounds__(128, 2) tile_block_kernel(const TileArgs a, Ou
     float2 *H = reinterpret_cast<float2 *>(smem);
     float2 *Vacc = reinterpret_cast<float2 *>(smem + C::H_BYTES);
     float4 *spos = reinterpret_cast<float4 *>(smem + C::H_BYTES + C::V_BYTES);
-    float4 *scoef = spos + C::CH * Q;
-    int *sloc = reinterpret_cast<int *>(scoef + C::CH * Q);
-    float4 *tcoef = reinterpret_cast<float4 *>(smem + C::H_BYTES + C::V_BYTES + C::S_BYTES);
-    int *tloc = reinterpret_cast<int *>(tcoef + C::PPP);
+    int2 *stl = reinterpret_cast<int2 *>(spos + C::SRC * Q);
+    int2 *ttl = reinterpret_cast<int2 *>(smem + C::H_BYTES + C::V_BYTES + C::S_BYTES);
+    float *tarea = reinterpret_cast<float *>(ttl + C::TPP);
     const int tid = threadIdx.x;
+    float R[Q][3];
+#pragma unroll
+    for (int l = 0; l < Q; ++l)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) R[l][m] = a.R[3 * l + m];
+
+    // stages source triangles [sb, sb + nst) of tile-triangle list starting at t0
+    auto stage = [&](int64_t t0, int nst) {
+        __syncthreads();  // the previous contents are consumed
+        for (int e = tid; e < nst * Q; e += NT) spos[e] = a.pos[t0 * Q + e];
+        for (int e = tid; e < nst; e += NT) stl[e] = a.tl[t0 + e];
+        const int npad = (4 - (nst & 3)) & 3;  // pad to a multiple of 4: far-away triangles of zero area, no flush
+        for (int e = tid; e < npad * Q; e += NT) spos[nst * Q + e] = make_float4(1e6f, 1e6f, 1e6f, __int_as_float(-2));
+        for (int e = tid; e < npad; e += NT) stl[nst + e] = make_int2(0, 0);
+        __syncthreads();
+    };
 
     for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x) {
         const int4 item = a.items[it];
@@ -295,37 +478,46 @@ __global__ void __launch_bounds__(128, 2) tile_block_kernel(const TileArgs a, Ou
         for (int e = tid; e < kTileV * VLD; e += NT) Vacc[e] = make_float2(0.f, 0.f);
         const int tI0 = a.tile_ptr[I], nTI = a.tile_ptr[I + 1] - tI0;
         const int tJ0 = a.tile_ptr[J], nTJ = a.tile_ptr[J + 1] - tJ0;
+        const bool once = nTJ <= C::SRC;  // T(J) stays staged over all passes
+        if (once) stage(tJ0, nTJ);
         for (int pb = 0; pb < nTI; pb += C::TPP) {
             const int ntp = min(C::TPP, nTI - pb);
             const bool active = tid < ntp * Q;
             float4 tp = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
             if (active) {
-                const int64_t pe = (int64_t)(tI0 + pb) * Q + tid;  // tile-triangle (tI0 + pb + tid / Q), point tid % Q
-                tp = a.pos[pe];
-                tcoef[tid] = a.coef[pe];
-                if (tid % Q == 0) tloc[tid / Q] = a.loc[tI0 + pb + tid / Q];
+                const int tt = tid / Q, l = tid - tt * Q;
+                tp = a.pos[(int64_t)(tI0 + pb) * Q + tid];
+                tp.x = -tp.x;
+                tp.y = -tp.y;
+                tp.z = -tp.z;
+                if (l == 0) {
+                    const int2 tl = a.tl[tI0 + pb + tt];
+                    ttl[tt] = tl;
+                    tarea[tt] = __int_as_float(tl.y);
+                }
             }
             const int gk = __float_as_int(tp.w);
 #pragma unroll 8
             for (int j = 0; j < kTileV; ++j) H[j * HLD + tid] = make_float2(0.f, 0.f);
-            for (int cb = 0; cb < nTJ; cb += C::CH) {
-                const int nch = min(C::CH, nTJ - cb);
-                __syncthreads();  // the previous chunk is consumed
-                const int64_t base = (int64_t)(tJ0 + cb) * Q;
-                for (int e = tid; e < nch * Q; e += NT) {
-                    spos[e] = a.pos[base + e];
-                    scoef[e] = a.coef[base + e];
-                }
-                for (int e = tid; e < nch; e += NT) sloc[e] = a.loc[tJ0 + cb + e];
-                __syncthreads();
+            PosSums ps;
+            ps.a0 = ps.a1 = ps.a2 = make_float2(0.f, 0.f);
+            ps.c0 = ps.c1 = ps.c2 = -1;
+            for (int sb = 0; sb < nTJ; sb += C::SRC) {
+                const int nst = min(C::SRC, nTJ - sb);
+                if (!once) stage(tJ0 + sb, nst);
                 if (active) {
                     if (self)
-                        chunk_sums<Q, LAP, true>(spos, scoef, sloc, nch, tp, gk, H + tid);
+                        src_sums<Q, LAP, true>(spos, stl, nst, tp, gk, R, H + tid, ps);
                     else
-                        chunk_sums<Q, LAP, false>(spos, scoef, sloc, nch, tp, gk, H + tid);
+                        src_sums<Q, LAP, false>(spos, stl, nst, tp, gk, R, H + tid, ps);
                 }
             }
-            __syncthreads();  // H, tcoef, tloc complete
+            if (active) {
+                pos_flush(H + tid, HLD, ps.c0, ps.a0);
+                pos_flush(H + tid, HLD, ps.c1, ps.a1);
+                pos_flush(H + tid, HLD, ps.c2, ps.a2);
+            }
+            __syncthreads();  // H, ttl, tarea complete
             if (tid < kTileV) {
                 const float2 *Hrow = H + tid * HLD;
                 for (int t = 0; t < ntp; ++t) {
@@ -333,44 +525,45 @@ __global__ void __launch_bounds__(128, 2) tile_block_kernel(const TileArgs a, Ou
 #pragma unroll
                     for (int l = 0; l < Q; ++l) {
                         const float2 h = Hrow[t * Q + l];
-                        const float4 c = tcoef[t * Q + l];
-                        cadd_scaled(r0, h, c.x);
-                        cadd_scaled(r1, h, c.y);
-                        cadd_scaled(r2, h, c.z);
+                        cadd_scaled(r0, h, R[l][0]);
+                        cadd_scaled(r1, h, R[l][1]);
+                        cadd_scaled(r2, h, R[l][2]);
                     }
-                    const uint32_t loc = (uint32_t)tloc[t];
+                    const float ar = tarea[t];
+                    const uint32_t loc = (uint32_t)ttl[t].x;
                     const int m0 = (int)(loc & 255u) - 1, m1 = (int)((loc >> 8) & 255u) - 1,
                               m2 = (int)((loc >> 16) & 255u) - 1;
                     if (m0 >= 0) {
                         float2 v = Vacc[m0 * VLD + tid];
-                        Vacc[m0 * VLD + tid] = make_float2(v.x + r0.x, v.y + r0.y);
+                        Vacc[m0 * VLD + tid] = make_float2(fmaf(r0.x, ar, v.x), fmaf(r0.y, ar, v.y));
                     }
                     if (m1 >= 0) {
                         float2 v = Vacc[m1 * VLD + tid];
-                        Vacc[m1 * VLD + tid] = make_float2(v.x + r1.x, v.y + r1.y);
+                        Vacc[m1 * VLD + tid] = make_float2(fmaf(r1.x, ar, v.x), fmaf(r1.y, ar, v.y));
                     }
                     if (m2 >= 0) {
                         float2 v = Vacc[m2 * VLD + tid];
-                        Vacc[m2 * VLD + tid] = make_float2(v.x + r2.x, v.y + r2.y);
+                        Vacc[m2 * VLD + tid] = make_float2(fmaf(r2.x, ar, v.x), fmaf(r2.y, ar, v.y));
                     }
                 }
             }
-            __syncthreads();  // before the next pass refills H, tcoef, tloc
+            __syncthreads();  // before the next pass refills H, ttl, tarea
         }
         // the block: rows of tile I, columns of tile J (and the transposed block)
         const int32_t *rI = a.rowmap + (int64_t)I * kTileV, *rJ = a.rowmap + (int64_t)J * kTileV;
         const int32_t *cI = a.colmap + (int64_t)I * kTileV, *cJ = a.colmap + (int64_t)J * kTileV;
         OutT *blk = out + (a.item_off ? a.item_off[it] : 0);
+        const int64_t ld = a.ld > 0 ? a.ld : (int64_t)item.w;
         for (int e = tid; e < kTileV * kTileV; e += NT) {
             const int i = e % kTileV, j = e / kTileV;  // rows fastest
             const int32_t r = rI[i], c = cJ[j];
-            if (r >= 0 && c >= 0) blk[r + (int64_t)c * a.ld] = to_out<OutT>(Vacc[i * VLD + j], a.scale);
+            if (r >= 0 && c >= 0) blk[r + (int64_t)c * ld] = to_out<OutT>(Vacc[i * VLD + j], a.scale);
         }
-        if (a.transpose && I != J) {
+        if ((item.z & 2) && I != J) {
             for (int e = tid; e < kTileV * kTileV; e += NT) {
                 const int j = e % kTileV, i = e / kTileV;
                 const int32_t r = rJ[j], c = cI[i];
-                if (r >= 0 && c >= 0) blk[r + (int64_t)c * a.ld] = to_out<OutT>(Vacc[i * VLD + j], a.scale);
+                if (r >= 0 && c >= 0) blk[r + (int64_t)c * ld] = to_out<OutT>(Vacc[i * VLD + j], a.scale);
             }
         }
         __syncthreads();  // Vacc is read before the next item clears it
@@ -401,13 +594,14 @@ gyps_status vertex_tiles_prepare(Mesh *m, cudaStream_t s)
     if (st == GYPS_OK) st = up(&T->d_tile_ptr, tp32);
     if (st == GYPS_OK) st = up(&T->d_tri, T->tri);
     if (st == GYPS_OK) st = up(&T->d_loc, T->loc);
+    if (st == GYPS_OK) st = up(&T->d_perm, T->perm);
     if (st == GYPS_OK) st = up(&T->d_rowmap, T->rowmap);
     if (st == GYPS_OK) st = up(&T->d_items, T->items);
     if (st == GYPS_OK) {
-        const size_t bytes = (size_t)T->ntt * m->q * sizeof(float4) * 2;
+        const size_t bytes = (size_t)T->ntt * m->q * sizeof(float4) + (size_t)T->ntt * sizeof(int2);
         if (cudaMalloc((void **)&T->d_pos, bytes) != cudaSuccess) st = set_error(GYPS_ERR_OOM, "tile panel");
         else {
-            T->d_coef = T->d_pos + T->ntt * m->q;
+            T->d_tl = reinterpret_cast<int2 *>(T->d_pos + T->ntt * m->q);
             m->device_bytes += (int64_t)bytes;
         }
     }
@@ -426,7 +620,7 @@ gyps_status vertex_tiles_prepare(Mesh *m, cudaStream_t s)
 void free_vertex_tiles(VertexTiles *T)
 {
     if (!T) return;
-    void *ptrs[] = {T->d_tile_ptr, T->d_tri, T->d_loc, T->d_rowmap, T->d_items, T->d_pos};
+    void *ptrs[] = {T->d_tile_ptr, T->d_tri, T->d_loc, T->d_perm, T->d_rowmap, T->d_items, T->d_pos};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete T;
@@ -437,8 +631,25 @@ gyps_status tile_panel(Mesh *m, double k, cudaStream_t s)
     VertexTiles *T = m->vt;
     const float ks = k > 0.0 ? (float)k : 1.0f;
     const int64_t n = T->ntt * m->q;
-    tile_panel_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(T->d_tri, T->d_loc, T->ntt, m->d_pts64, m->rule, ks,
-                                                                 T->d_pos, T->d_coef);
+    PointPerm pp{};
+    for (int p = 0; p < 6; ++p)
+        for (int l = 0; l < m->q; ++l) {
+            // the point whose barycentric coordinates, read in the turned vertex order, are those of point l
+            int best = 0;
+            double bd = 1e300;
+            for (int l2 = 0; l2 < m->q; ++l2) {
+                double d = 0.0;
+                for (int c = 0; c < 3; ++c) d += std::fabs(m->rule.bary[3 * l2 + kPerm[p][c]] - m->rule.bary[3 * l + c]);
+                if (d < bd) {
+                    bd = d;
+                    best = l2;
+                }
+            }
+            if (bd > 1e-12) return set_error(GYPS_ERR_INVALID, "quadrature rule is not symmetric under vertex orders");
+            pp.sigma[p][l] = (int8_t)best;
+        }
+    tile_panel_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(T->d_tri, T->d_loc, T->d_perm, T->ntt, m->d_pts64,
+                                                                 m->rule, pp, ks, T->d_pos, T->d_tl);
     GYPS_CUDA(cudaGetLastError());
     return GYPS_OK;
 }
@@ -478,8 +689,9 @@ TileArgs tile_args(const Mesh *m, double k)
     const VertexTiles *T = m->vt;
     TileArgs a{};
     a.pos = T->d_pos;
-    a.coef = T->d_coef;
-    a.loc = T->d_loc;
+    a.tl = T->d_tl;
+    for (int l = 0; l < m->q; ++l)
+        for (int c = 0; c < 3; ++c) a.R[3 * l + c] = (float)(m->rule.w[l] * m->rule.bary[3 * l + c]);
     a.tile_ptr = T->d_tile_ptr;
     a.rowmap = T->d_rowmap;
     a.colmap = T->d_rowmap;
@@ -488,7 +700,6 @@ TileArgs tile_args(const Mesh *m, double k)
     a.n_items = (int64_t)T->items.size();
     a.ld = m->nv;
     a.scale = (k > 0.0 ? k : 1.0) / (4.0 * 3.14159265358979323846);
-    a.transpose = 1;
     return a;
 }
 

@@ -1,0 +1,90 @@
+"""Compressed far field (Sec. 5.3: blocks of far-apart clusters as low-rank
+approximations to a tolerance) on the GPU against the FP64 oracle's exact
+operator: the compressed apply (H + C) X within a stated multiple of eps of
+V X, element by element on every column (parity.rel), on meshes whose
+clusters give both dense and low-rank blocks; the error falls with eps; with
+no admissible block (eta huge) the apply equals the FP32 dense product."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1804_00995_gb300 as g
+    g.load()
+    return g
+
+
+@pytest.fixture(scope="module")
+def sphere4(g):
+    v, t = synth.icosphere(4)
+    return g.Mesh(v, t, 3), oracle.Mesh(v, t, 3)
+
+
+@pytest.mark.parametrize("k,nrhs", [(8.0, 1), (20.0, 3), (0.0, 2), (12.0, 17)])
+def test_hmat_apply_matches_the_exact_operator(g, sphere4, k, nrhs):
+    gm, om = sphere4
+    h = g.Hmat(gm, k, eps=1e-5, leaf_tiles=1, eta=0.5)
+    info = h.info
+    assert info["lowrank_blocks"] > 0 and info["dense_blocks"] > 0, info
+    x = synth.random_complex(np.random.default_rng(int(k) + nrhs), om.nv, nrhs)
+    y = h.apply(torch.as_tensor(x).cuda()).cpu().numpy()
+    ref = om.apply(k, x)
+    assert rel(y.reshape(ref.shape), ref) < 1e-4, info
+    h.close()
+
+
+def test_hmat_error_falls_with_eps_and_no_compression_is_exact(g, sphere4):
+    gm, om = sphere4
+    x = synth.random_complex(np.random.default_rng(5), om.nv, 2)
+    ref = om.apply(10.0, x)
+    errs = []
+    for eps in (1e-2, 1e-4, 1e-6):
+        h = g.Hmat(gm, 10.0, eps=eps, leaf_tiles=1, eta=0.5)
+        errs.append(rel(h.apply(torch.as_tensor(x).cuda()).cpu().numpy(), ref))
+        h.close()
+    assert errs[0] > errs[1] > errs[2], errs
+    dense = g.Hmat(gm, 10.0, eps=1e-4, leaf_tiles=1, eta=1e9)
+    assert dense.info["lowrank_blocks"] == 0
+    yd = dense.apply(torch.as_tensor(x).cuda()).cpu().numpy()
+    assert rel(yd, ref) < 1e-5
+    y32 = g.sl_apply(gm, 10.0, torch.as_tensor(x).cuda(), prec="fp32").cpu().numpy()
+    assert rel(yd, y32) < 1e-5
+    # host buffers give the same result
+    yh = dense.apply(torch.as_tensor(x)).numpy()
+    assert rel(yh, yd) < 1e-12
+    dense.close()
+
+
+def test_hmat_rejects_bad_arguments(g, sphere4):
+    gm, _ = sphere4
+    for kw in (dict(eps=0.0), dict(eps=2.0), dict(leaf_tiles=0), dict(eta=-1.0)):
+        args = dict(eps=1e-4, leaf_tiles=1, eta=0.5)
+        args.update(kw)
+        with pytest.raises(g.GypsError) as e:
+            g.Hmat(gm, 5.0, **args)
+        assert e.value.status == "INVALID"
+
+
+@pytest.mark.slow
+def test_sphere163842_k64_hmat_sampled_rows(g):
+    """The 163842-vertex sphere at k = 64 (q = 3, 983040 points), 16 plane
+    waves: compressed apply vs the oracle on 48 sampled rows."""
+    v, t = synth.icosphere(7)
+    gm = g.Mesh(v, t, 3)
+    om = oracle.Mesh(v, t, 3)
+    dirs = synth.plane_wave_dirs(np.random.default_rng(7), 16)
+    f = g.rhs_planewave(gm, 64.0, dirs)
+    h = g.Hmat(gm, 64.0, eps=1e-5, leaf_tiles=16, eta=1.0)
+    y = h.apply(f).cpu().numpy()
+    rows = np.sort(np.random.default_rng(64).choice(om.nv, 48, replace=False))
+    ref = om.apply(64.0, f.cpu().numpy(), rows=rows)[rows]
+    assert rel(y[rows], ref) < 1e-4, h.info
+    h.close()
