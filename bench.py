@@ -271,6 +271,11 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU arm
+def triangle_range(rank, world, nt):
+    """Contiguous test-triangle range of a rank: the ranges of all ranks partition [0, nt)."""
+    return (rank * nt // world, (rank + 1) * nt // world)
+
+
 def run_gyps(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -290,16 +295,24 @@ def run_gyps(args, rank, world, local_rank):
     mesh = g.Mesh(v, t, cfg["q"])
     nq, nv = mesh.nq, mesh.nv
     pairs = float(nq) * nq
-    # each rank applies the operator to its own seeded right-hand side (independent problems)
+    # one operator apply per step, sharded over the ranks by contiguous ranges of test
+    # triangles (their target points), then one all-reduce (sum) of Y: the row blocks of
+    # Phi^T W G W Phi are independent, so the partial applies add up to the full apply
     nrhs, prec = args.nrhs, args.prec
-    x = torch.as_tensor(synth.random_complex(np.random.default_rng(1000 + rank), nv, nrhs)).to(dev)
-    y = g.sl_apply(mesh, k, x, prec=prec)
+    tr = triangle_range(rank, world, mesh.nt)
+    x = torch.as_tensor(synth.random_complex(np.random.default_rng(1000), nv, nrhs)).to(dev)
+    y = g.sl_apply(mesh, k, x, prec=prec, tri_range=tr)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
+    def step(xin, yout):
+        g.sl_apply(mesh, k, xin, prec=prec, out=yout, tri_range=tr)
+        if world > 1:
+            dist.all_reduce(torch.view_as_real(yout.t()))  # (nrhs, nv) is contiguous
+
     for _ in range(args.warmup):
         flush.zero_()
-        g.sl_apply(mesh, k, x, prec=prec, out=y)
+        step(x, y)
     torch.cuda.synchronize(dev)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -314,7 +327,7 @@ def run_gyps(args, rank, world, local_rank):
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        g.sl_apply(mesh, k, x, prec=prec, out=y)
+        step(x, y)
         ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
@@ -330,41 +343,54 @@ def run_gyps(args, rank, world, local_rank):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = float(tt.item())
     ms_per_step = t_max / args.steps
-    value = world * pairs / (ms_per_step * 1e-3) / 1e9
+    value = pairs / (ms_per_step * 1e-3) / 1e9  # the whole operator per step, over all ranks
 
     # roofline of the dominant kernel (dense G u), from its own events
     far_ms = prof["far_ms"] / max(prof["far_launches"], 1)
     # one launch covers all right-hand sides of a pass: pairs per launch = Nq^2 x (passes per apply)^-1
     launches_per_apply = prof["far_launches"] / max(prof["applies"], 1)
-    achieved = pairs / (far_ms * launches_per_apply * 1e-3) / 1e9
+    rank_pairs = pairs * (tr[1] - tr[0]) / mesh.nt  # this rank's target points x all sources
+    achieved = rank_pairs / (far_ms * launches_per_apply * 1e-3) / 1e9
     peak_mhz = None
     try:
         peak_mhz = json.loads(read_text(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
     except Exception:
         peak_mhz = clk.get("sm_max_mhz") or 2070.0
-    traffic = far_traffic_per_launch() if (prec == "fp32" and nrhs == 1) else None
+    traffic = far_traffic_per_launch() if (prec == "fp32" and nrhs == 1 and world == 1) else None
 
-    # end to end through the public API with host buffers (pinned), copies inside
-    xh = torch.as_tensor(synth.random_complex(np.random.default_rng(2000 + rank), nv, nrhs)).t().contiguous().t()
+    # end to end through the public API with host buffers (pinned), copies inside: X from the
+    # host into the library's staging, the (partial) apply, the all-reduce, Y back to the host
+    xh = torch.as_tensor(synth.random_complex(np.random.default_rng(2000), nv, nrhs)).t().contiguous().t()
     xh = xh.pin_memory().t().contiguous().t() if nrhs == 1 else xh
     yh = torch.empty((nrhs, nv), dtype=torch.complex128).pin_memory().t()
-    g.sl_apply(mesh, k, xh, prec=prec, out=yh)
+    yd = torch.empty((nrhs, nv), dtype=torch.complex128, device=dev).t()
+
+    def e2e_step():
+        if world == 1:
+            g.sl_apply(mesh, k, xh, prec=prec, out=yh)  # returns once Y is back on the host
+            return
+        step(xh, yd)
+        yh.copy_(yd)
+
+    e2e_step()
     e2e_t = []
     for i in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
-        g.sl_apply(mesh, k, xh, prec=prec, out=yh)  # returns once Y is back on the host
+        e2e_step()
         e2e_t.append(time.perf_counter() - t0)
     e2e_mean = sum(e2e_t) / len(e2e_t)
     if world > 1:
         tt = torch.tensor([e2e_mean], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_mean = float(tt.item())
-    e2e_value = world * pairs / e2e_mean / 1e9
+    e2e_value = pairs / e2e_mean / 1e9
 
     solve = None
-    if args.solve is not False or args.solve_fp64:
+    if world == 1 and (args.solve is not False or args.solve_fp64):
         f = g.rhs_planewave(mesh, k, [cfg["dirs"][0]])
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -429,12 +455,14 @@ def run_gyps(args, rank, world, local_rank):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16x3+f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "mesh": "icosphere level 5 (20480 triangles)", "nv": nv, "nq": nq,
                        "k": k, "quad_points": cfg["q"], "nrhs": nrhs, "far": prec, "near": "fp64",
                        "l2": "flushed (512 MB write) before every step", "pairs_per_step": pairs,
-                       "ranks": "independent replicas, one right-hand side each"},
+                       "ranks": f"one operator sharded over {world} rank(s) by contiguous test-triangle ranges, "
+                                f"one all-reduce of Y (nv x nrhs complex) per step",
+                       "triangles_per_rank": mesh.nt // world},
             "roofline": dict(far_roofline(achieved, prec, nrhs, props.multi_processor_count, peak_mhz),
                              traffic=traffic,
                              kernel="far32_kernel<1,4,false>" if prec == "fp32" else "far_tc_kernel",
@@ -907,7 +935,7 @@ def run_efie(args):
     print(json.dumps(line), flush=True)
 
 
-def solve_large(g, mesh, v, t, k, F, dirs, args):
+def solve_large(g, mesh, v, t, k, F, dirs, args, hmat=None):
     """Workload sphere163842_k64_q3_r16, --solve: (flexible) GMRES to 1e-6 on all
     16 plane waves, tensor-core working operator, double-float operator for the
     true residual (the FP64 pipe would take about three minutes per check here);
@@ -921,8 +949,9 @@ def solve_large(g, mesh, v, t, k, F, dirs, args):
         P.load(args.precond_file)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    X, rep = g.gmres_solve(mesh, k, F, tol=1e-6, restart=300, maxit=args.solve_maxit, prec="tc_bf16x3",
-                           check_prec="df64", max_refine=3, precond=P)
+    working = "hmat" if hmat is not None else "tc_bf16x3"
+    X, rep = g.gmres_solve(mesh, k, F, tol=1e-6, restart=300, maxit=args.solve_maxit, prec=working,
+                           check_prec="df64", max_refine=3, precond=P, hmat=hmat)
     torch.cuda.synchronize()
     seconds = time.perf_counter() - t0
     patch = 4096
@@ -945,7 +974,7 @@ def solve_large(g, mesh, v, t, k, F, dirs, args):
             "check_applies": rep.check_applies, "refinements": rep.refinements, "status": rep.status,
             "precond": "learned (flexible GMRES)" if P is not None else "none",
             "precond_dropped": bool(rep.precond_fallback), "restart": 300,
-            "working": "tc_bf16x3", "check": "df64",
+            "working": working, "check": "df64",
             "residual_check_max": float(np.max(rep.true_residual)),
             "fp64_rows": int(rows.size), "fp64_patch_triangles": patch, "fp64_check_s": t_fp64,
             "fp64_residual_rows_max": float(res64.max()), "fp64_residual_rows_median": float(np.median(res64)),
@@ -1073,6 +1102,8 @@ def run_hmat(args):
         "diff_vs_fp32_all_pairs": {"columns": 2, "norm": err_norm, "element": err_elem},
         "clocks": clk,
     }
+    if args.solve:
+        line["solve"] = solve_large(g, mesh, v, t, k, x, dirs, args, hmat=h)
     print(json.dumps(line), flush=True)
     h.close()
 

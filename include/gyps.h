@@ -61,7 +61,9 @@ typedef enum {
     GYPS_PREC_DF64 = 3,         /* G and G u in double-float (hi + lo FP32 pairs, about 44 bits) on the
                                    FP32 pipe: FP64-class accuracy (about 1e-12 from FP64) at several
                                    times the FP64 pipe's speed; for true-residual checks */
-    GYPS_PREC_AUTO = 4          /* FP32 below 16 right-hand sides, tensor cores above */
+    GYPS_PREC_AUTO = 4,         /* FP32 below 16 right-hand sides, tensor cores above */
+    GYPS_PREC_HMAT = 5          /* gyps_gmres_solve only: the compressed far field opts->hmat (built
+                                   for this mesh and k) plus C as the Krylov loop's operator */
 } gyps_prec;
 
 /* Boundary integral equation that gyps_gmres_solve solves for sound-soft scattering. */
@@ -83,6 +85,7 @@ typedef enum {
 
 typedef struct gyps_mesh_s *gyps_mesh_t;
 typedef struct gyps_precond_s *gyps_precond_t;
+typedef struct gyps_hmat_s *gyps_hmat_t;  /* compressed far field (gyps_hmat_create) */
 
 typedef struct {
     int64_t nv;          /* vertices = P1 degrees of freedom */
@@ -181,8 +184,10 @@ gyps_status gyps_near_export(gyps_mesh_t mesh, int64_t *rowptr, int32_t *col, do
  *        tri_end) (both -1: all).  The far part then sums only over target
  *        points of those triangles and C only over those test triangles, so
  *        applies over a partition of the triangles add up to the full apply.
+ *        Every precision supports a range (the tensor-core form restricts
+ *        its 128-point target tiles to the range's points).
  * Errors: INVALID (nrhs, ld, k, range), UNSUPPORTED (tensor-core precision
- * with fewer than 16 right-hand sides), OOM, CUDA, TIMEOUT.
+ * with fewer than 16 right-hand sides or k = 0), OOM, CUDA, TIMEOUT.
  * TIMEOUT (a bounded device wait gave up, Y incomplete) is returned only when
  * X or Y is a host buffer: that call is synchronous and reports the waits of
  * its own launches.  With device X and Y the call returns after launching;
@@ -204,9 +209,13 @@ gyps_status gyps_near_correct(gyps_mesh_t mesh, int nrhs, const void *X, int64_t
  * LHS = integral(...)/(4 pi) + regularize(...)/(4 pi)):
  *     V = (1/4pi) Phi^T W G W Phi + C,   nv x nv complex double2,
  * column-major with ldv >= nv; V_ij pairs test function i with trial
- * function j.  prec: GYPS_PREC_FP64 or GYPS_PREC_FP32 (kernel values and the
- * partial sums of one thread, at most 6 q^2 terms, in FP32; added up in FP64).
- * Errors: INVALID, UNSUPPORTED (prec, or more than 65535 triangles), CUDA.
+ * function j.  prec: GYPS_PREC_FP64 (FP64 kernel values and sums, triangle
+ * pairs with FP64 atomics; at most 65535 triangles) or GYPS_PREC_FP32 (FP32
+ * kernel values and sums over blocks of 64 x 64 vertices along a Morton order,
+ * each entry of V written once; the complex-symmetric Gauss-Gauss part is
+ * computed for one block of each symmetric pair and written to both; any size
+ * that fits).  Errors: INVALID, UNSUPPORTED (prec, or more than 65535
+ * triangles in FP64), OOM, CUDA.
  */
 gyps_status gyps_sl_assemble(gyps_mesh_t mesh, double k, int prec, void *V, int64_t ldv, void *stream);
 
@@ -393,6 +402,7 @@ typedef struct {
     double timeout_ms;   /* wall-clock limit of the solve (0 = none): checked before every inner
                             iteration; when it passes, the cycle ends with the iterations done, the
                             true residual is computed and TIMEOUT is returned unless it meets tol */
+    gyps_hmat_t hmat;    /* with prec = GYPS_PREC_HMAT: the compressed operator (else NULL) */
 } gyps_gmres_opts;
 
 /* GMRES report, HOST.  Arrays are caller-owned, length nrhs, may be NULL. */
@@ -401,7 +411,10 @@ typedef struct {
     int32_t applies;         /* operator applies in the working precision */
     int32_t check_applies;   /* applies in check_prec */
     int32_t refinements;     /* refinement sweeps done */
-    int32_t precond_fallback;/* 1 when the preconditioner was dropped (non-finite output or a
+    int32_t precond_fallback;/* 2 when the network was not used: the mesh's electrical size k x radius
+                                (radius: largest vertex distance from the centroid) lies outside the
+                                range it was trained on, widened by 25 % (gyps_precond_range);
+                                1 when the preconditioner was dropped (non-finite output or a
                                 full cycle that did not halve the residual) */
     double *est_residual;    /* last Arnoldi residual estimate per column (relative) */
     double *true_residual;   /* ||F - V X||/||F|| with check_prec, per column */
@@ -521,8 +534,6 @@ gyps_status gyps_batch_destroy(gyps_batch_t batch);
  * Blocks are generated on the device from the same Gauss-point kernel as the
  * dense assembly (FP32 kernel values); the correction C stays FP64 and sparse.
  * ------------------------------------------------------------------------ */
-typedef struct gyps_hmat_s *gyps_hmat_t;
-
 typedef struct {
     int64_t clusters;
     int64_t dense_blocks;     /* blocks stored dense (A <= B), fallbacks included */
@@ -630,8 +641,15 @@ gyps_status gyps_precond_train_step(gyps_precond_t p, gyps_mesh_t mesh, double k
                                     int64_t ldr, const void *E, int64_t lde, double lr, double *loss,
                                     float *grad, void *stream);
 
+/* Range [ka_lo, ka_hi] of the electrical sizes k x radius of the meshes that
+ * gyps_precond_train_step has seen (ka_lo > ka_hi: none yet).  Flexible GMRES
+ * uses the network only inside this range widened by 25 % (the network's
+ * inputs carry k h, not the size of the body in wavelengths). */
+gyps_status gyps_precond_range(gyps_precond_t p, double *ka_lo, double *ka_hi);
+
 /* Checkpoint: parameters and Adam moments with a JSON header (format
- * "gyps-mpnn-1").  load checks the shape and rejects non-finite values. */
+ * "gyps-mpnn-1", with the training range).  load checks the shape and rejects
+ * non-finite values; a file without a range loads as untrained-range. */
 gyps_status gyps_precond_save(gyps_precond_t p, const char *path);
 gyps_status gyps_precond_load(gyps_precond_t p, const char *path);
 

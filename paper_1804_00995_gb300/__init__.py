@@ -27,7 +27,7 @@ __all__ = [
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgyps.so")
 
-PREC = {"fp64": 0, "fp32": 1, "tc_bf16x3": 2, "df64": 3, "auto": 4}
+PREC = {"fp64": 0, "fp32": 1, "tc_bf16x3": 2, "df64": 3, "auto": 4, "hmat": 5}
 NO_NEAR = 0x1
 
 _STATUS = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "NAN", 6: "TIMEOUT", 7: "UNSUPPORTED"}
@@ -75,7 +75,7 @@ class _GmresOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("check_prec", ctypes.c_int32), ("use_x0", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("precond", ctypes.c_void_p), ("formulation", ctypes.c_int32),
-                ("eta", ctypes.c_double), ("timeout_ms", ctypes.c_double)]
+                ("eta", ctypes.c_double), ("timeout_ms", ctypes.c_double), ("hmat", ctypes.c_void_p)]
 
 
 class _GmresReport(ctypes.Structure):
@@ -152,6 +152,8 @@ _SIGS = {
     "gyps_precond_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)],
                             ctypes.c_int),
     "gyps_precond_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "gyps_precond_range": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                           ctypes.c_int),
     "gyps_precond_info": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "gyps_precond_params": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
@@ -652,6 +654,12 @@ class Precond:
                                               grad.ctypes.data if grad is not None else None, _stream(stream)))
         return (loss.value, grad) if want_grad else loss.value
 
+    def range(self):
+        """(ka_lo, ka_hi): electrical sizes k x radius trained on (lo > hi: none)."""
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        _check(load().gyps_precond_range(self.handle, ctypes.byref(lo), ctypes.byref(hi)))
+        return lo.value, hi.value
+
     def save(self, path: str) -> None:
         _check(load().gyps_precond_save(self._h, str(path).encode()))
 
@@ -689,12 +697,14 @@ FORMULATION = {"sl": 0, "bw": 1, "cfie": 2, "efie": 3, "emcfie": 4}
 def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, maxit: int = 1000,
                 prec: str = "fp32", check_prec: str = "fp64", x0=None, max_refine: int = 3, raise_on_fail=False,
                 precond: "Precond" = None, stream=None, formulation: str = "sl", eta: float = None,
-                timeout_ms: float = 0.0):
+                timeout_ms: float = 0.0, hmat: "Hmat" = None):
     """Solves A X = F (gyps_gmres_solve), A = V ("sl"), 1/2 M + K - i eta V ("bw"),
     1/2 M + K' - i eta V ("cfie"; F from rhs_planewave_cfie with the same eta) or -T
     ("efie"; RWG coefficients, F from rhs_planewave_efie), or -eta T + (1 - eta)(Id/2 - nxK)
     ("emcfie", eta = beta; F from rhs_planewave_emcfie); eta defaults to k, or 1 at
     k = 0.  timeout_ms > 0 bounds the wall-clock time (status TIMEOUT, X = last iterate).
+    prec="hmat" takes the compressed operator `hmat` (built for this mesh and k) in the
+    Krylov loop; check_prec then judges the residual with a kernel product.
     Returns (X, GmresReport); NOT_CONVERGED and TIMEOUT raise only with raise_on_fail."""
     if eta is None:
         eta = 0.5 if formulation == "emcfie" else (float(k) if k > 0 else 1.0)
@@ -709,7 +719,8 @@ def gmres_solve(mesh: Mesh, k: float, F, tol: float = 1e-6, restart: int = 100, 
         x = _empty_colmajor(n, nrhs, f.device)
     opts = _GmresOpts(float(tol), int(restart), int(maxit), PREC[prec], PREC[check_prec], 1 if x0 is not None else 0,
                       int(max_refine), precond.handle.value if precond is not None else None,
-                      FORMULATION[formulation], float(eta), float(timeout_ms))
+                      FORMULATION[formulation], float(eta), float(timeout_ms),
+                      hmat._h.value if hmat is not None else None)
     est = np.zeros(nrhs)
     tru = np.zeros(nrhs)
     conv = np.zeros(nrhs, dtype=np.int32)

@@ -468,9 +468,9 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
                          int prec, uint32_t flags, int64_t tri_begin, int64_t tri_end, cudaStream_t s)
 {
     const bool full = (tri_begin == 0 && tri_end == m->nt);
-    if (prec == GYPS_PREC_AUTO) prec = (nrhs >= 16 && k > 0.0 && full) ? GYPS_PREC_TC_BF16X3 : GYPS_PREC_FP32;
-    if (prec == GYPS_PREC_TC_BF16X3 && (k <= 0.0 || !full))
-        return set_error(GYPS_ERR_UNSUPPORTED, "tensor-core precision needs k > 0 and all triangles");
+    if (prec == GYPS_PREC_AUTO) prec = (nrhs >= 16 && k > 0.0) ? GYPS_PREC_TC_BF16X3 : GYPS_PREC_FP32;
+    if (prec == GYPS_PREC_TC_BF16X3 && k <= 0.0)
+        return set_error(GYPS_ERR_UNSUPPORTED, "tensor-core precision needs k > 0");
     if (prec != GYPS_PREC_FP32 && prec != GYPS_PREC_FP64 && prec != GYPS_PREC_TC_BF16X3 && prec != GYPS_PREC_DF64)
         return set_error(GYPS_ERR_INVALID, "unknown precision");
     const int64_t t_begin = tri_begin * m->q, t_end = tri_end * m->q;
@@ -485,7 +485,7 @@ gyps_status apply_device(Mesh *m, double k, int nrhs, const double2 *X, int64_t 
 
     if (t_end > t_begin) {
         if (prec == GYPS_PREC_TC_BF16X3) {
-            GYPS_TRY(far_tc(m, k, X, ldx, nrhs, v, ldv, s));
+            GYPS_TRY(far_tc(m, k, X, ldx, nrhs, v, ldv, t_begin, t_end, s));
         } else if (prec == GYPS_PREC_FP32) {
             GYPS_TRY(grow(m, &m->ws_den, &m->ws_den_bytes, (size_t)(m->n_src_tiles * den_tile_floats(8)) * sizeof(float)));
             for (int c0 = 0; c0 < nrhs;) {

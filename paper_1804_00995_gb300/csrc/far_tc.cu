@@ -264,6 +264,7 @@ struct TcArgs {
     int64_t nq;       // targets = sources
     int64_t n_chunks; // source chunks (padded)
     int64_t n_tiles;  // target tiles of M
+    int64_t t_begin, t_end;  // target points [t_begin, t_end) (a range of test triangles)
     int64_t n_segs;   // source segments of SEG_CHUNKS chunks
     int ncols;        // valid right-hand sides in this pass (<= R)
     float ks;
@@ -513,9 +514,9 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
         for (int64_t it = 0; it < icount && ok; ++it) {
             const int64_t item = ifirst + it * istep;
             const int64_t seg = seg_of(item), tile = item - seg * n_tiles;
-            const int64_t t0 = tile * M;
+            const int64_t t0 = a.t_begin + tile * M;
             const int64_t tgt = t0 + row;
-            const float4 p = a.tgt[min(tgt, nq - 1)];
+            const float4 p = a.tgt[min(tgt, a.t_end - 1)];
             const float2 tx = make_float2(p.x * ks, p.x * ks);
             const float2 ty = make_float2(p.y * ks, p.y * ks);
             const float2 tz = make_float2(p.z * ks, p.z * ks);
@@ -580,7 +581,7 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
                 tmem_ld8(lane_base + (uint32_t)col0, r0);
                 tmem_ld8(lane_base + (uint32_t)(C::N + col0), r1);
                 tmem_ld_wait();
-                if (trow < nq) {
+                if (trow < a.t_end) {
 #pragma unroll
                     for (int i = 0; i < LD; ++i) {
                         const int col = col0 + i;
@@ -613,7 +614,8 @@ __global__ void __launch_bounds__(NT, 1) far_tc_kernel(const TcArgs a)
 }
 
 template <int R>
-gyps_status run(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, double2 *v, int64_t ldv, cudaStream_t s)
+gyps_status run(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, double2 *v, int64_t ldv, int64_t t_begin,
+                int64_t t_end, cudaStream_t s)
 {
     using C = Cfg<R>;
     const int64_t n_chunks = (m->nq + KS - 1) / KS;
@@ -627,7 +629,9 @@ gyps_status run(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, doub
     a.ldv = ldv;
     a.nq = m->nq;
     a.n_chunks = n_chunks;
-    a.n_tiles = (m->nq + M - 1) / M;
+    a.t_begin = t_begin;
+    a.t_end = t_end;
+    a.n_tiles = (t_end - t_begin + M - 1) / M;
     a.n_segs = (n_chunks + SEG_CHUNKS - 1) / SEG_CHUNKS;
     a.ncols = 0;
     a.ks = (float)k;
@@ -658,17 +662,18 @@ gyps_status run(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, doub
 }  // namespace tc
 
 gyps_status far_tc(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, double2 *v, int64_t ldv,
-                   cudaStream_t s)
+                   int64_t t_begin, int64_t t_end, cudaStream_t s)
 {
+    if (t_end <= t_begin) return GYPS_OK;
     // widest pass that the right-hand sides fill: every pass regenerates the kernel tiles
     if (nrhs >= 64) {
         const int full = nrhs / 64 * 64;
-        GYPS_TRY(tc::run<64>(m, k, X, ldx, full, v, ldv, s));
+        GYPS_TRY(tc::run<64>(m, k, X, ldx, full, v, ldv, t_begin, t_end, s));
         if (full == nrhs) return GYPS_OK;
-        return far_tc(m, k, X + (int64_t)full * ldx, ldx, nrhs - full, v + (int64_t)full * ldv, ldv, s);
+        return far_tc(m, k, X + (int64_t)full * ldx, ldx, nrhs - full, v + (int64_t)full * ldv, ldv, t_begin, t_end, s);
     }
-    if (nrhs > 16) return tc::run<32>(m, k, X, ldx, nrhs, v, ldv, s);
-    return tc::run<16>(m, k, X, ldx, nrhs, v, ldv, s);
+    if (nrhs > 16) return tc::run<32>(m, k, X, ldx, nrhs, v, ldv, t_begin, t_end, s);
+    return tc::run<16>(m, k, X, ldx, nrhs, v, ldv, t_begin, t_end, s);
 }
 
 }  // namespace gyps

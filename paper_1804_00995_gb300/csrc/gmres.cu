@@ -198,8 +198,10 @@ struct Solver {
     // (Brakhage-Werner), 1/2 M + K' - i eta V (direct combined field), all
     // nv x nrhs, or -T (the EFIE) and -eta T + (1 - eta)(Id/2 - nxK) (the
     // electromagnetic combined field with beta = eta), ne x nrhs.
+    Hmat *hm = nullptr;  // compressed operator of GYPS_PREC_HMAT
     gyps_status op(const double2 *X, int64_t ldx, double2 *Y, int prec)
     {
+        if (prec == GYPS_PREC_HMAT) return hmat_apply_device(hm, nrhs, X, ldx, Y, nv, s);
         if (form == GYPS_FORM_EFIE) return efie_apply_device(m, k, -1.0, nrhs, X, ldx, Y, nv, prec, s);
         if (form == GYPS_FORM_EM_CFIE) return emcfie_apply_device(m, k, eta, 1.0, nrhs, X, ldx, Y, nv, prec, s);
         if (form == GYPS_FORM_BRAKHAGE_WERNER || form == GYPS_FORM_DIRECT_CFIE)
@@ -439,6 +441,7 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
     S.nv = n;
     S.form = o.formulation;
     S.eta = o.eta;
+    S.hm = hmat_of(o.hmat);
     if (o.timeout_ms > 0.0) {
         S.has_deadline = true;
         S.deadline = std::chrono::steady_clock::now() +
@@ -453,9 +456,15 @@ gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t 
     GYPS_CUDA(cudaMalloc((void **)&S.w.R, blk));
     GYPS_CUDA(cudaMalloc((void **)&S.w.D, blk));
     if (o.precond) {
-        GYPS_CUDA(cudaMalloc((void **)&S.w.Z, blk * o.restart));
-        S.P = o.precond;
-        S.pre_on = true;
+        bool in_range = true;
+        GYPS_TRY(precond_in_range(o.precond, m, k, s, &in_range));
+        if (in_range) {
+            GYPS_CUDA(cudaMalloc((void **)&S.w.Z, blk * o.restart));
+            S.P = o.precond;
+            S.pre_on = true;
+        } else {
+            S.fallback = 2;  // outside the electrical sizes the network was trained on: plain GMRES
+        }
     }
     GYPS_CUDA(cudaMalloc((void **)&S.w.h, (size_t)(o.restart + 1) * nrhs * sizeof(double2)));
     GYPS_CUDA(cudaMalloc((void **)&S.w.nrm, nrhs * sizeof(double)));
@@ -559,6 +568,15 @@ extern "C" gyps_status gyps_gmres_solve(gyps_mesh_t h, double k, int nrhs, const
         o.formulation != GYPS_FORM_EM_CFIE)
         return set_error(GYPS_ERR_INVALID, "unknown formulation");
     const bool em = o.formulation == GYPS_FORM_EFIE || o.formulation == GYPS_FORM_EM_CFIE;
+    if (o.check_prec == GYPS_PREC_HMAT) return set_error(GYPS_ERR_INVALID, "the check needs a kernel precision");
+    if (o.prec == GYPS_PREC_HMAT) {
+        const Hmat *hm = hmat_of(o.hmat);
+        if (!hm) return set_error(GYPS_ERR_INVALID, "GYPS_PREC_HMAT needs opts->hmat");
+        if (o.formulation != GYPS_FORM_SINGLE_LAYER)
+            return set_error(GYPS_ERR_UNSUPPORTED, "the compressed operator is the single layer");
+        if (hmat_mesh(hm) != m || hmat_k(hm) != k)
+            return set_error(GYPS_ERR_INVALID, "opts->hmat was built for another mesh or wavenumber");
+    }
     if (em) {
         if (!(k > 0.0)) return set_error(GYPS_ERR_INVALID, "the EFIE needs k > 0");
         if (o.prec == GYPS_PREC_TC_BF16X3 || o.check_prec == GYPS_PREC_TC_BF16X3)

@@ -459,6 +459,127 @@ __global__ void __launch_bounds__(128) hm_rows_kernel(const hm::Term *terms, con
     }
 }
 
+// 8-byte asynchronous copy global -> shared (one complex FP32 value; any 8-byte
+// aligned address); src_bytes = 0 fills zeros.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// The row sums of hm_rows_kernel for 16 right-hand sides, tiled: a CTA owns 128
+// rows of a cluster; the columns of each term (a dense block, or U with its
+// projection) stream through shared memory in chunks of 32 (double-buffered
+// asynchronous copies, zero-filled past the block's edge); each thread owns 4
+// rows x 4 right-hand sides (16 complex sums) and reads per column 32 bytes of
+// the matrix and 32 bytes of x.  Chunk sums are folded into TwoSum pairs.
+constexpr int RT_ROWS = 128, RT_K = 32;
+struct RowsTileSmem {
+    float2 M[2][RT_K][RT_ROWS];     // 64 KB
+    float2 X[2][RT_K][hm::NRC];     // 8 KB
+};
+
+__global__ void __launch_bounds__(128) hm_rows16_kernel(const hm::Term *terms, const int32_t *term_ptr,
+                                                        const int64_t *voff, const int64_t *chunk_cluster,
+                                                        const int32_t *perm, const float2 *xloc, int64_t nv,
+                                                        const float2 *T, double2 *Y, int64_t ldy, int c0)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    RowsTileSmem &sm = *reinterpret_cast<RowsTileSmem *>(smraw);
+    const int64_t cc = chunk_cluster[blockIdx.x];
+    const int A = (int)(cc >> 32), chunk = (int)(cc & 0xffffffff);
+    const int64_t mA = voff[A + 1] - voff[A];
+    const int64_t row0 = (int64_t)chunk * RT_ROWS;
+    const int tid = threadIdx.x, rg = tid & 31, cg = tid >> 5;  // rows 4 rg .. 4 rg + 3, RHS 4 cg .. 4 cg + 3
+    float2 hi[4][4], lo[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = make_float2(0.f, 0.f);
+
+    for (int tt = term_ptr[A]; tt < term_ptr[A + 1]; ++tt) {
+        const hm::Term t = terms[tt];
+        const int nchunks = (t.ncol + RT_K - 1) / RT_K;
+        // issue chunk q into buffer q & 1: 32 columns x 128 rows of M, 32 x 16 values of x (or of the projection)
+        auto issue = [&](int q) {
+            const int buf = q & 1, j0 = q * RT_K;
+#pragma unroll 8
+            for (int u = 0; u < RT_K * RT_ROWS / 128; ++u) {  // 32 copies per thread, rows fastest
+                const int e = tid + 128 * u, jj = e / RT_ROWS, rr = e % RT_ROWS;
+                const int64_t row = row0 + rr, col = j0 + jj;
+                const bool ok = col < t.ncol && row < mA;
+                cp_async8(&sm.M[buf][jj][rr], t.M + (ok ? row + col * t.ld : 0), ok ? 8 : 0);
+            }
+#pragma unroll
+            for (int u = 0; u < RT_K * hm::NRC / 128; ++u) {  // 4 copies per thread
+                const int e = tid + 128 * u, jj = e / hm::NRC, c = e % hm::NRC;
+                const int64_t col = j0 + jj;
+                const bool ok = col < t.ncol;
+                const float2 *src = t.kind == 0 ? xloc + (ok ? t.src + col + (int64_t)c * nv : 0)
+                                                : T + (ok ? t.src + col * hm::NRC + c : 0);
+                cp_async8(&sm.X[buf][jj][c], src, ok ? 8 : 0);
+            }
+            cp_async_commit();
+        };
+        __syncthreads();  // the previous term's buffers are consumed
+        issue(0);
+        for (int q = 0; q < nchunks; ++q) {
+            if (q + 1 < nchunks) {
+                issue(q + 1);
+                cp_async_wait1();
+            } else {
+                cp_async_wait0();
+            }
+            __syncthreads();
+            const int buf = q & 1;
+            float2 acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+#pragma unroll 4
+            for (int jj = 0; jj < RT_K; ++jj) {
+                const float4 m01 = *reinterpret_cast<const float4 *>(&sm.M[buf][jj][4 * rg]);
+                const float4 m23 = *reinterpret_cast<const float4 *>(&sm.M[buf][jj][4 * rg + 2]);
+                const float4 x01 = *reinterpret_cast<const float4 *>(&sm.X[buf][jj][4 * cg]);
+                const float4 x23 = *reinterpret_cast<const float4 *>(&sm.X[buf][jj][4 * cg + 2]);
+                const float2 mv[4] = {make_float2(m01.x, m01.y), make_float2(m01.z, m01.w), make_float2(m23.x, m23.y),
+                                      make_float2(m23.z, m23.w)};
+                const float2 xv[4] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w), make_float2(x23.x, x23.y),
+                                      make_float2(x23.z, x23.w)};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        acc[a][b].x = fmaf(mv[a].x, xv[b].x, fmaf(-mv[a].y, xv[b].y, acc[a][b].x));
+                        acc[a][b].y = fmaf(mv[a].x, xv[b].y, fmaf(mv[a].y, xv[b].x, acc[a][b].y));
+                    }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    two_sum_acc(hi[a][b].x, lo[a][b].x, acc[a][b].x);
+                    two_sum_acc(hi[a][b].y, lo[a][b].y, acc[a][b].y);
+                }
+            __syncthreads();  // buffer q & 1 is free for chunk q + 2
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t i = row0 + 4 * rg + a;
+        if (i >= mA) continue;
+        const int64_t v = perm[voff[A] + i];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            Y[v + (int64_t)(c0 + 4 * cg + b) * ldy] =
+                make_double2((double)hi[a][b].x + (double)lo[a][b].x, (double)hi[a][b].y + (double)lo[a][b].y);
+    }
+}
+
 // ---------------------------------------------------------------- host: build
 static gyps_status dmalloc(Hmat *h, void **p, size_t bytes)
 {
@@ -846,9 +967,17 @@ static gyps_status apply_pass(Hmat *h, const double2 *X, int64_t ldx, double2 *Y
             h->d_proj, h->d_xloc, nv, h->d_T);
         GYPS_CUDA(cudaGetLastError());
     }
-    hm_rows_kernel<NR><<<(unsigned)h->row_chunks, 128, 0, s>>>(h->d_terms, h->d_term_ptr, h->voff_dev,
-                                                             h->d_chunk_cluster, h->d_perm, h->d_xloc, nv, h->d_T,
-                                                             Y, ldy, c0);
+    if (NR == hm::NRC) {
+        const int smem = (int)sizeof(RowsTileSmem);
+        GYPS_CUDA(cudaFuncSetAttribute(hm_rows16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        hm_rows16_kernel<<<(unsigned)h->row_chunks, 128, smem, s>>>(h->d_terms, h->d_term_ptr, h->voff_dev,
+                                                                   h->d_chunk_cluster, h->d_perm, h->d_xloc, nv,
+                                                                   h->d_T, Y, ldy, c0);
+    } else {
+        hm_rows_kernel<NR><<<(unsigned)h->row_chunks, 128, 0, s>>>(h->d_terms, h->d_term_ptr, h->voff_dev,
+                                                                 h->d_chunk_cluster, h->d_perm, h->d_xloc, nv, h->d_T,
+                                                                 Y, ldy, c0);
+    }
     GYPS_CUDA(cudaGetLastError());
     return GYPS_OK;
 }
@@ -879,6 +1008,17 @@ using namespace gyps;
 struct gyps_hmat_s {
     Hmat *h;
 };
+
+namespace gyps {
+Hmat *hmat_of(gyps_hmat_t h) { return h ? h->h : nullptr; }
+const Mesh *hmat_mesh(const Hmat *h) { return h->m; }
+double hmat_k(const Hmat *h) { return h->k; }
+gyps_status hmat_apply_device(Hmat *h, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
+                              cudaStream_t s)
+{
+    return apply_device_hm(h, nrhs, X, ldx, Y, ldy, s);
+}
+}  // namespace gyps
 
 extern "C" gyps_status gyps_hmat_create(gyps_mesh_t mesh, double k, double eps, int leaf_tiles, double eta,
                                         void *stream, gyps_hmat_t *out)

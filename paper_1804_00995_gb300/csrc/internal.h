@@ -113,6 +113,7 @@ struct Mesh {
     int32_t *d_adj_ptr = nullptr, *d_adj = nullptr;       // vertex neighbours over mesh edges
     float *d_vfeat = nullptr;                             // nv x 6: centred coordinates, unit normal
     double h_mean = 0.0;                                  // mean edge length
+    double radius = 0.0;                                  // largest vertex distance from the vertex centroid
     VertexTiles *vt = nullptr;                            // vertex tiles of the dense blocks (built on first use)
     int64_t device_bytes = 0;
     int num_sms = 0;
@@ -182,7 +183,7 @@ gyps_status run_far_dl_df(Mesh *m, double k, bool adj, const double2 *u64, int64
 gyps_status far_points(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, const float4 *tgt32,
                        const double4_32a *tgt64, int64_t npts, double2 *v, int64_t ldv, int prec, cudaStream_t s);
 gyps_status far_tc(Mesh *m, double k, const double2 *X, int64_t ldx, int nrhs, double2 *v, int64_t ldv,
-                   cudaStream_t s);
+                   int64_t t_begin, int64_t t_end, cudaStream_t s);
 cudaError_t launch_near_spmv(const Mesh &m, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
                              cudaStream_t s);
 
@@ -218,9 +219,20 @@ gyps_status assemble_tiles(Mesh *m, double k, double2 *V, int64_t ldv, cudaStrea
 gyps_status rhs_device(Mesh *m, double k, int nrhs, const double *dirs_host, double2 *F, int64_t ldf,
                        cudaStream_t s, bool cfie = false, double eta = 0.0);
 
+// a11: whether the mesh's electrical size k x radius lies in the range the network was trained on
+// (widened by 25 %; an untrained network has no range and is always in range)
+gyps_status precond_in_range(gyps_precond_t p, Mesh *m, double k, cudaStream_t s, bool *in_range);
 // a11: learned preconditioner Z = M(R) (device pointers)
 gyps_status precond_apply_device(gyps_precond_t p, Mesh *m, double k, int nrhs, const double2 *R, int64_t ldr,
                                  double2 *Z, int64_t ldz, cudaStream_t s);
+
+// NEXT-4: the compressed far field (hmat.cu); Y = (H + C) X with device pointers
+struct Hmat;
+Hmat *hmat_of(gyps_hmat_t h);
+const Mesh *hmat_mesh(const Hmat *h);
+double hmat_k(const Hmat *h);
+gyps_status hmat_apply_device(Hmat *h, int nrhs, const double2 *X, int64_t ldx, double2 *Y, int64_t ldy,
+                              cudaStream_t s);
 
 // a8
 gyps_status gmres_device(Mesh *m, double k, int nrhs, const double2 *F, int64_t ldf, double2 *X, int64_t ldx,

@@ -280,6 +280,8 @@ struct Mpnn {
     __nv_bfloat16 *pb = nullptr;
     int64_t step = 0;
     int device = 0;
+    // electrical sizes k x radius of the meshes trained on (lo > hi: none yet)
+    double ka_lo = 1e300, ka_hi = -1e300;
     // activation workspace
     float *ws = nullptr;
     size_t ws_bytes = 0;
@@ -352,6 +354,7 @@ static gyps_status ensure_graph(Mesh *m, cudaStream_t s)
         }
     }
     m->h_mean = esum / (double)std::max<int64_t>(ecount, 1);
+    m->radius = rad;
     GYPS_CUDA(cudaMalloc((void **)&m->d_adj_ptr, ptr.size() * sizeof(int32_t)));
     GYPS_CUDA(cudaMalloc((void **)&m->d_adj, std::max<size_t>(adj.size(), 1) * sizeof(int32_t)));
     GYPS_CUDA(cudaMalloc((void **)&m->d_vfeat, vf.size() * sizeof(float)));
@@ -665,6 +668,8 @@ extern "C" gyps_status gyps_precond_train_step(gyps_precond_t h, gyps_mesh_t mh,
     double2 *Zd = scr + 2 * (size_t)m->nv * nrhs;
     Acts a;
     GYPS_TRY(forward(P, m, k, nrhs, Rd, lr_d, Zd, m->nv, a, s));
+    P->ka_lo = std::min(P->ka_lo, k * m->radius);  // the graph (and the radius) exist after the forward
+    P->ka_hi = std::max(P->ka_hi, k * m->radius);
     std::vector<double> l(nrhs);
     GYPS_TRY(backward(P, m, nrhs, Zd, m->nv, Ed, le_d, a, l.data(), s));
     if (loss) {
@@ -701,7 +706,8 @@ extern "C" gyps_status gyps_precond_save(gyps_precond_t h, const char *path)
     char header[256];
     std::memset(header, 0, sizeof(header));
     std::snprintf(header, sizeof(header), "{\"format\": \"gyps-mpnn-1\", \"hidden\": %d, \"layers\": %d, \"nparams\": %lld, "
-                  "\"adam_step\": %lld}", P->H, P->L, (long long)P->nparams, (long long)P->step);
+                  "\"adam_step\": %lld, \"ka_lo\": %.17g, \"ka_hi\": %.17g}", P->H, P->L, (long long)P->nparams,
+                  (long long)P->step, P->ka_lo, P->ka_hi);
     bool ok = std::fwrite(header, 1, sizeof(header), f) == sizeof(header) &&
               std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
     ok = (std::fclose(f) == 0) && ok;
@@ -724,6 +730,11 @@ extern "C" gyps_status gyps_precond_load(gyps_precond_t h, const char *path)
     if (ok) ok = std::sscanf(header, "{\"format\": \"gyps-mpnn-1\", \"hidden\": %d, \"layers\": %d, \"nparams\": %lld, "
                              "\"adam_step\": %lld}", &hid, &lay, &np, &stp) == 4;
     ok = ok && hid == P->H && lay == P->L && np == P->nparams;
+    double ka_lo = 1e300, ka_hi = -1e300;  // optional (files without it: no range)
+    if (ok) {
+        const char *q = std::strstr(header, "\"ka_lo\": ");
+        if (q && std::sscanf(q, "\"ka_lo\": %lf, \"ka_hi\": %lf", &ka_lo, &ka_hi) != 2) ok = false;
+    }
     ok = ok && std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
     std::fclose(f);
     if (!ok) return set_error(GYPS_ERR_INVALID, "not a compatible preconditioner file");
@@ -737,5 +748,27 @@ extern "C" gyps_status gyps_precond_load(gyps_precond_t h, const char *path)
     GYPS_CUDA(cudaGetLastError());
     GYPS_CUDA(cudaDeviceSynchronize());
     P->step = stp;
+    P->ka_lo = ka_lo;
+    P->ka_hi = ka_hi;
+    return GYPS_OK;
+}
+
+namespace gyps {
+gyps_status precond_in_range(gyps_precond_t h, Mesh *m, double k, cudaStream_t s, bool *in_range)
+{
+    const Mpnn *P = reinterpret_cast<const Mpnn *>(h);
+    GYPS_TRY(ensure_graph(m, s));
+    const double ka = k * m->radius;
+    *in_range = P->ka_lo > P->ka_hi || (ka >= P->ka_lo / 1.25 && ka <= P->ka_hi * 1.25);
+    return GYPS_OK;
+}
+}  // namespace gyps
+
+extern "C" gyps_status gyps_precond_range(gyps_precond_t h, double *ka_lo, double *ka_hi)
+{
+    if (!h || !ka_lo || !ka_hi) return set_error(GYPS_ERR_INVALID, "NULL argument");
+    const Mpnn *P = reinterpret_cast<const Mpnn *>(h);
+    *ka_lo = P->ka_lo;
+    *ka_hi = P->ka_hi;
     return GYPS_OK;
 }

@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdint>
 #include <numeric>
+#include <string>
 #include <unordered_set>
 #include <vector>
 
@@ -264,22 +265,24 @@ __global__ void tile_panel_kernel(const int32_t *tt_tri, const int32_t *tt_loc, 
 template <int Q>
 struct TileCfg {
     static constexpr int NT = 128;
-    static constexpr int TPP = NT / Q;                          // target triangles per pass
-    static constexpr int SRC = Q == 3 ? 168 : Q == 7 ? 84 : 128;  // source triangles staged at once (multiple of 4)
-    static constexpr int HLD = NT + 1;                          // padded row of H (float2)
-    static constexpr int VLD = kTileV + 1;                      // padded row of Vacc (float2)
+    static constexpr int TPP = Q == 3 ? 40 : Q == 7 ? 17 : 120;   // target triangles per pass
+    static constexpr int SRC = Q == 3 ? 160 : Q == 7 ? 40 : 120;  // source triangles staged at once (multiple of 8)
+    static constexpr int LCAP = 16;                               // (triangle, position) entries of a slot in a pass
+    static constexpr int HLD = 121;                               // padded row of H (float2; odd: no conflicts)
     static constexpr int H_BYTES = kTileV * HLD * 8;
-    static constexpr int V_BYTES = kTileV * VLD * 8;
-    static constexpr int S_BYTES = SRC * Q * 16 + SRC * 8;       // staged source points, (triangle, slots)
-    static constexpr int T_BYTES = TPP * 8 + TPP * 4;            // (triangle, slots) and area of the pass's targets
-    static constexpr int SMEM = H_BYTES + V_BYTES + S_BYTES + T_BYTES;
+    static constexpr int S_BYTES = SRC * Q * 16 + SRC * 8;        // staged source points, (slots, area)
+    static constexpr int L_BYTES = kTileV * LCAP * 2 + kTileV * 4; // per-slot entry lists of a pass and counts
+    static constexpr int T_BYTES = TPP * 8 + TPP * 4 + 3 * 8 * 4; // (slots, area) of the pass's targets, area, R^T
+    static constexpr int SMEM = H_BYTES + S_BYTES + L_BYTES + T_BYTES;
+    static_assert(TPP * Q <= NT && TPP * Q < HLD, "a pass fits the threads and H");
+    static_assert(kTileV * (kTileV + 1) * 8 <= H_BYTES, "the block staging fits in H");
 };
 
-// Whole target passes: about 180 triangles touch 64 vertices of a closed surface.
+// Whole target passes: about 170 triangles touch 64 vertices of a closed surface.
 int64_t tile_tri_cap(int q)
 {
     const int tpp = q == 1 ? TileCfg<1>::TPP : q == 3 ? TileCfg<3>::TPP : TileCfg<7>::TPP;
-    return (int64_t)tpp * std::max<int64_t>(1, 170 / tpp);
+    return (int64_t)tpp * std::max<int64_t>(1, (170 + tpp / 2) / tpp);
 }
 
 __device__ __forceinline__ void cadd_scaled(float2 &acc, float2 g, float c)
@@ -325,8 +328,8 @@ struct PairSums {
 };
 
 template <int Q, bool LAP, bool SELF>
-__device__ __forceinline__ PairSums pair_sums(const float4 *__restrict__ spos, int b0, int b1, float2 ar, float2 tx,
-                                              float2 ty, float2 tz, int gk, const float (&R)[Q][3])
+__device__ __forceinline__ PairSums pair_sums(const float4 *__restrict__ sxy, const float4 *__restrict__ szg, int pr,
+                                              float2 ar, float2 tx, float2 ty, float2 tz, int gk, const float (&R)[Q][3])
 {
     const float2 inv2pi = make_float2(0.159154943091895335769f, 0.159154943091895335769f);
     const float2 mc1 = make_float2(-6.28318548202514648438f, -6.28318548202514648438f);  // -(2 pi in FP32)
@@ -337,10 +340,10 @@ __device__ __forceinline__ PairSums pair_sums(const float4 *__restrict__ spos, i
     o.t0r = o.t0i = o.t1r = o.t1i = o.t2r = o.t2i = make_float2(0.f, 0.f);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
-        const float4 p0 = spos[b0 * Q + l], p1 = spos[b1 * Q + l];
-        const float2 dx = __fadd2_rn(tx, make_float2(p0.x, p1.x));
-        const float2 dy = __fadd2_rn(ty, make_float2(p0.y, p1.y));
-        const float2 dz = __fadd2_rn(tz, make_float2(p0.z, p1.z));
+        const float4 xy = sxy[pr * Q + l], zg = szg[pr * Q + l];  // (x0, x1, y0, y1), (z0, z1, id0, id1)
+        const float2 dx = __fadd2_rn(tx, make_float2(xy.x, xy.y));
+        const float2 dy = __fadd2_rn(ty, make_float2(xy.z, xy.w));
+        const float2 dz = __fadd2_rn(tz, make_float2(zg.x, zg.y));
         float2 r2 = __fmul2_rn(dx, dx);
         r2 = __ffma2_rn(dy, dy, r2);
         r2 = __ffma2_rn(dz, dz, r2);
@@ -349,8 +352,8 @@ __device__ __forceinline__ PairSums pair_sums(const float4 *__restrict__ spos, i
         if (LAP) {
             gr = rs;
             if (SELF) {
-                if (__float_as_int(p0.w) == gk) gr.x = 0.0f;
-                if (__float_as_int(p1.w) == gk) gr.y = 0.0f;
+                if (__float_as_int(zg.z) == gk) gr.x = 0.0f;
+                if (__float_as_int(zg.w) == gk) gr.y = 0.0f;
             }
         } else {
             const float2 ph = __fmul2_rn(r2, rs);                                  // k r
@@ -361,11 +364,11 @@ __device__ __forceinline__ PairSums pair_sums(const float4 *__restrict__ spos, i
             gr = __fmul2_rn(cs, rs);                                               // exp(ikr) / (k r)
             gi = __fmul2_rn(sn, rs);
             if (SELF) {  // the point paired with itself: ik / k
-                if (__float_as_int(p0.w) == gk) {
+                if (__float_as_int(zg.z) == gk) {
                     gr.x = 0.0f;
                     gi.x = 1.0f;
                 }
-                if (__float_as_int(p1.w) == gk) {
+                if (__float_as_int(zg.w) == gk) {
                     gr.y = 0.0f;
                     gi.y = 1.0f;
                 }
@@ -416,58 +419,84 @@ __device__ __forceinline__ void pos_add(const PairSums &t, int h, uint32_t code,
     ps.a2.y += h ? t.t2i.y : t.t2i.x;
 }
 
-// Source-side sums of one target point against the staged triangles, four at a
-// time (two independent packed pairs; the count is padded to a multiple of
-// four with far-away triangles of zero area), added into the running sums of
-// the vertex positions in list order.
+#ifndef GYPS_TILE_UNROLL
+#define GYPS_TILE_UNROLL 4
+#endif
+#ifndef GYPS_TILE_MINB
+#define GYPS_TILE_MINB 3
+#endif
+constexpr int kTileUnroll = GYPS_TILE_UNROLL;  // 4 or 8
+
+// Source-side sums of one target point against the staged triangles, U at a
+// time (U / 2 independent packed pairs; the count is padded to a multiple of U
+// with far-away triangles of zero area), added into the running sums of the
+// vertex positions in list order.
 template <int Q, bool LAP, bool SELF>
-__device__ __forceinline__ void src_sums(const float4 *__restrict__ spos, const int2 *__restrict__ stl, int nst,
-                                         float4 tp, int gk, const float (&R)[Q][3], float2 *__restrict__ Hcol,
-                                         PosSums &ps)
+__device__ __forceinline__ void src_sums(const float4 *__restrict__ sxy, const float4 *__restrict__ szg,
+                                         const int2 *__restrict__ stl, int nst, float4 tp, int gk,
+                                         const float (&R)[Q][3], float2 *__restrict__ Hcol, PosSums &ps)
 {
     constexpr int HLD = TileCfg<Q>::HLD;
     const float2 tx = make_float2(tp.x, tp.x), ty = make_float2(tp.y, tp.y), tz = make_float2(tp.z, tp.z);
-    for (int b = 0; b < nst; b += 4) {
-        const int2 tl0 = stl[b], tl1 = stl[b + 1], tl2 = stl[b + 2], tl3 = stl[b + 3];
-        const PairSums pa = pair_sums<Q, LAP, SELF>(spos, b, b + 1, make_float2(__int_as_float(tl0.y), __int_as_float(tl1.y)),
-                                                    tx, ty, tz, gk, R);
-        const PairSums pb = pair_sums<Q, LAP, SELF>(spos, b + 2, b + 3,
-                                                    make_float2(__int_as_float(tl2.y), __int_as_float(tl3.y)), tx, ty,
-                                                    tz, gk, R);
-        pos_add(pa, 0, (uint32_t)tl0.x, Hcol, HLD, ps);
-        pos_add(pa, 1, (uint32_t)tl1.x, Hcol, HLD, ps);
-        pos_add(pb, 0, (uint32_t)tl2.x, Hcol, HLD, ps);
-        pos_add(pb, 1, (uint32_t)tl3.x, Hcol, HLD, ps);
+    constexpr int U = kTileUnroll;  // source triangles per step
+    for (int b = 0; b < nst; b += U) {
+        // the kernel sums of U triangles first (branch-free), then the running sums in order
+        PairSums pr[U / 2];
+        int2 tl[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) tl[u] = stl[b + u];
+#pragma unroll
+        for (int u = 0; u < U / 2; ++u)
+            pr[u] = pair_sums<Q, LAP, SELF>(sxy, szg, (b >> 1) + u,
+                                            make_float2(__int_as_float(tl[2 * u].y), __int_as_float(tl[2 * u + 1].y)),
+                                            tx, ty, tz, gk, R);
+#pragma unroll
+        for (int u = 0; u < U; ++u) pos_add(pr[u >> 1], u & 1, (uint32_t)tl[u].x, Hcol, HLD, ps);
     }
 }
 
 template <int Q, bool LAP, typename OutT>
-__global__ void __launch_bounds__(128, 2) tile_block_kernel(const TileArgs a, OutT *out)
+__global__ void __launch_bounds__(128, GYPS_TILE_MINB) tile_block_kernel(const TileArgs a, OutT *out)
 {
     using C = TileCfg<Q>;
-    constexpr int NT = C::NT, HLD = C::HLD, VLD = C::VLD;
+    constexpr int NT = C::NT, HLD = C::HLD, VLD = kTileV + 1;
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *H = reinterpret_cast<float2 *>(smem);
-    float2 *Vacc = reinterpret_cast<float2 *>(smem + C::H_BYTES);
-    float4 *spos = reinterpret_cast<float4 *>(smem + C::H_BYTES + C::V_BYTES);
-    int2 *stl = reinterpret_cast<int2 *>(spos + C::SRC * Q);
-    int2 *ttl = reinterpret_cast<int2 *>(smem + C::H_BYTES + C::V_BYTES + C::S_BYTES);
+    // staged source points, pair-interleaved: triangles 2p, 2p + 1, point l ->
+    // sxy[p Q + l] = (x0, x1, y0, y1), szg[p Q + l] = (z0, z1, id0, id1)
+    float4 *sxy = reinterpret_cast<float4 *>(smem + C::H_BYTES);
+    float4 *szg = sxy + (C::SRC / 2) * Q;
+    int2 *stl = reinterpret_cast<int2 *>(szg + (C::SRC / 2) * Q);
+    uint16_t *lst = reinterpret_cast<uint16_t *>(smem + C::H_BYTES + C::S_BYTES);
+    int *cnt = reinterpret_cast<int *>(lst + kTileV * C::LCAP);
+    int2 *ttl = reinterpret_cast<int2 *>(smem + C::H_BYTES + C::S_BYTES + C::L_BYTES);
     float *tarea = reinterpret_cast<float *>(ttl + C::TPP);
+    float *Rt = tarea + C::TPP;  // Rt[m][l]: R transposed, 3 x 8
     const int tid = threadIdx.x;
     float R[Q][3];
 #pragma unroll
     for (int l = 0; l < Q; ++l)
 #pragma unroll
         for (int m = 0; m < 3; ++m) R[l][m] = a.R[3 * l + m];
+    if (tid < 3 * Q) Rt[(tid % 3) * 8 + tid / 3] = a.R[tid];
+    // the block accumulator in registers: column j = tid % 64, rows 32 h .. 32 h + 31 with h = tid / 64
+    const int jcol = tid & (kTileV - 1), half = tid >> 6;
+    float2 acc[32];
 
-    // stages source triangles [sb, sb + nst) of tile-triangle list starting at t0
+    // stages source triangles [t0, t0 + nst) (positions, codes)
     auto stage = [&](int64_t t0, int nst) {
         __syncthreads();  // the previous contents are consumed
-        for (int e = tid; e < nst * Q; e += NT) spos[e] = a.pos[t0 * Q + e];
-        for (int e = tid; e < nst; e += NT) stl[e] = a.tl[t0 + e];
-        const int npad = (4 - (nst & 3)) & 3;  // pad to a multiple of 4: far-away triangles of zero area, no flush
-        for (int e = tid; e < npad * Q; e += NT) spos[nst * Q + e] = make_float4(1e6f, 1e6f, 1e6f, __int_as_float(-2));
-        for (int e = tid; e < npad; e += NT) stl[nst + e] = make_int2(0, 0);
+        const int npad = (kTileUnroll - nst % kTileUnroll) % kTileUnroll;  // pad: far-away triangles of zero area
+        for (int e = tid; e < (nst + npad) * Q; e += NT) {
+            const int b = e / Q, l = e - b * Q, h = b & 1, o = (b >> 1) * Q + l;
+            const float4 p = b < nst ? a.pos[t0 * Q + e] : make_float4(1e6f, 1e6f, 1e6f, __int_as_float(-2));
+            float *xy = reinterpret_cast<float *>(&sxy[o]), *zg = reinterpret_cast<float *>(&szg[o]);
+            xy[h] = p.x;
+            xy[2 + h] = p.y;
+            zg[h] = p.z;
+            zg[2 + h] = p.w;
+        }
+        for (int e = tid; e < nst + npad; e += NT) stl[e] = e < nst ? a.tl[t0 + e] : make_int2(0, 0);
         __syncthreads();
     };
 
@@ -475,7 +504,8 @@ __global__ void __launch_bounds__(128, 2) tile_block_kernel(const TileArgs a, Ou
         const int4 item = a.items[it];
         const int I = item.x, J = item.y;
         const bool self = item.z & 1;
-        for (int e = tid; e < kTileV * VLD; e += NT) Vacc[e] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < 32; ++r) acc[r] = make_float2(0.f, 0.f);
         const int tI0 = a.tile_ptr[I], nTI = a.tile_ptr[I + 1] - tI0;
         const int tJ0 = a.tile_ptr[J], nTJ = a.tile_ptr[J + 1] - tJ0;
         const bool once = nTJ <= C::SRC;  // T(J) stays staged over all passes
@@ -496,9 +526,12 @@ __global__ void __launch_bounds__(128, 2) tile_block_kernel(const TileArgs a, Ou
                     tarea[tt] = __int_as_float(tl.y);
                 }
             }
+            if (tid < kTileV) cnt[tid] = 0;
             const int gk = __float_as_int(tp.w);
+            if (tid < HLD) {
 #pragma unroll 8
-            for (int j = 0; j < kTileV; ++j) H[j * HLD + tid] = make_float2(0.f, 0.f);
+                for (int j = 0; j < kTileV; ++j) H[j * HLD + tid] = make_float2(0.f, 0.f);
+            }
             PosSums ps;
             ps.a0 = ps.a1 = ps.a2 = make_float2(0.f, 0.f);
             ps.c0 = ps.c1 = ps.c2 = -1;
@@ -507,9 +540,9 @@ __global__ void __launch_bounds__(128, 2) tile_block_kernel(const TileArgs a, Ou
                 if (!once) stage(tJ0 + sb, nst);
                 if (active) {
                     if (self)
-                        src_sums<Q, LAP, true>(spos, stl, nst, tp, gk, R, H + tid, ps);
+                        src_sums<Q, LAP, true>(sxy, szg, stl, nst, tp, gk, R, H + tid, ps);
                     else
-                        src_sums<Q, LAP, false>(spos, stl, nst, tp, gk, R, H + tid, ps);
+                        src_sums<Q, LAP, false>(sxy, szg, stl, nst, tp, gk, R, H + tid, ps);
                 }
             }
             if (active) {
@@ -517,39 +550,42 @@ __global__ void __launch_bounds__(128, 2) tile_block_kernel(const TileArgs a, Ou
                 pos_flush(H + tid, HLD, ps.c1, ps.a1);
                 pos_flush(H + tid, HLD, ps.c2, ps.a2);
             }
-            __syncthreads();  // H, ttl, tarea complete
-            if (tid < kTileV) {
-                const float2 *Hrow = H + tid * HLD;
-                for (int t = 0; t < ntp; ++t) {
-                    float2 r0 = make_float2(0.f, 0.f), r1 = r0, r2 = r0;
-#pragma unroll
-                    for (int l = 0; l < Q; ++l) {
-                        const float2 h = Hrow[t * Q + l];
-                        cadd_scaled(r0, h, R[l][0]);
-                        cadd_scaled(r1, h, R[l][1]);
-                        cadd_scaled(r2, h, R[l][2]);
-                    }
-                    const float ar = tarea[t];
-                    const uint32_t loc = (uint32_t)ttl[t].x;
-                    const int m0 = (int)(loc & 255u) - 1, m1 = (int)((loc >> 8) & 255u) - 1,
-                              m2 = (int)((loc >> 16) & 255u) - 1;
-                    if (m0 >= 0) {
-                        float2 v = Vacc[m0 * VLD + tid];
-                        Vacc[m0 * VLD + tid] = make_float2(fmaf(r0.x, ar, v.x), fmaf(r0.y, ar, v.y));
-                    }
-                    if (m1 >= 0) {
-                        float2 v = Vacc[m1 * VLD + tid];
-                        Vacc[m1 * VLD + tid] = make_float2(fmaf(r1.x, ar, v.x), fmaf(r1.y, ar, v.y));
-                    }
-                    if (m2 >= 0) {
-                        float2 v = Vacc[m2 * VLD + tid];
-                        Vacc[m2 * VLD + tid] = make_float2(fmaf(r2.x, ar, v.x), fmaf(r2.y, ar, v.y));
-                    }
+            __syncthreads();  // ttl, tarea and cnt are visible
+            // per test slot, the (target triangle, position) entries of this pass
+            for (int q3 = tid; q3 < 3 * ntp; q3 += NT) {
+                const int tt = q3 / 3, m = q3 - 3 * tt;
+                const int sl = (int)(((uint32_t)ttl[tt].x >> (8 * m)) & 255u) - 1;
+                if (sl >= 0) {
+                    const int e = atomicAdd(&cnt[sl], 1);
+                    if (e < C::LCAP) lst[sl * C::LCAP + e] = (uint16_t)((tt << 2) | m);
                 }
             }
-            __syncthreads();  // before the next pass refills H, ttl, tarea
+            __syncthreads();  // H and the lists complete
+            // Vacc[32 half + r][jcol] += sum over the slot's entries (triangle t, position m) of
+            // area_t sum_l R[l][m] H[jcol][t Q + l]
+            const float2 *Hrow = H + jcol * HLD;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const int sl = 32 * half + r;
+                const int n = min(cnt[sl], C::LCAP);
+                for (int e = 0; e < n; ++e) {
+                    const int code = lst[sl * C::LCAP + e];
+                    const int tt = code >> 2, m = code & 3;
+                    float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int l = 0; l < Q; ++l) cadd_scaled(v, Hrow[tt * Q + l], Rt[m * 8 + l]);
+                    const float ar = tarea[tt];
+                    acc[r].x = fmaf(v.x, ar, acc[r].x);
+                    acc[r].y = fmaf(v.y, ar, acc[r].y);
+                }
+            }
+            __syncthreads();  // before the next pass refills H, ttl, tarea, cnt
         }
-        // the block: rows of tile I, columns of tile J (and the transposed block)
+        // the block through shared memory (H's space): rows of tile I, columns of tile J
+        float2 *Vs = H;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) Vs[(32 * half + r) * VLD + jcol] = acc[r];
+        __syncthreads();
         const int32_t *rI = a.rowmap + (int64_t)I * kTileV, *rJ = a.rowmap + (int64_t)J * kTileV;
         const int32_t *cI = a.colmap + (int64_t)I * kTileV, *cJ = a.colmap + (int64_t)J * kTileV;
         OutT *blk = out + (a.item_off ? a.item_off[it] : 0);
@@ -557,16 +593,16 @@ __global__ void __launch_bounds__(128, 2) tile_block_kernel(const TileArgs a, Ou
         for (int e = tid; e < kTileV * kTileV; e += NT) {
             const int i = e % kTileV, j = e / kTileV;  // rows fastest
             const int32_t r = rI[i], c = cJ[j];
-            if (r >= 0 && c >= 0) blk[r + (int64_t)c * ld] = to_out<OutT>(Vacc[i * VLD + j], a.scale);
+            if (r >= 0 && c >= 0) blk[r + (int64_t)c * ld] = to_out<OutT>(Vs[i * VLD + j], a.scale);
         }
         if ((item.z & 2) && I != J) {
             for (int e = tid; e < kTileV * kTileV; e += NT) {
                 const int j = e % kTileV, i = e / kTileV;
                 const int32_t r = rJ[j], c = cI[i];
-                if (r >= 0 && c >= 0) blk[r + (int64_t)c * ld] = to_out<OutT>(Vacc[i * VLD + j], a.scale);
+                if (r >= 0 && c >= 0) blk[r + (int64_t)c * ld] = to_out<OutT>(Vs[i * VLD + j], a.scale);
             }
         }
-        __syncthreads();  // Vacc is read before the next item clears it
+        __syncthreads();  // Vs is read before the next item's first pass clears H
     }
 }
 
@@ -579,6 +615,15 @@ gyps_status vertex_tiles_prepare(Mesh *m, cudaStream_t s)
     GYPS_CUDA(cudaMemcpyAsync(vtx.data(), m->d_vtx, vtx.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     GYPS_CUDA(cudaMemcpyAsync(tri.data(), m->d_tri, tri.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     GYPS_CUDA(cudaStreamSynchronize(s));
+    {
+        // a slot collects at most one entry per incident triangle and pass
+        std::vector<int32_t> deg(m->nv, 0);
+        for (int32_t v : tri) ++deg[v];
+        const int32_t dmax = *std::max_element(deg.begin(), deg.end());
+        if (dmax > TileCfg<3>::LCAP)
+            return set_error(GYPS_ERR_UNSUPPORTED, "FP32 tile assembly: a vertex has " + std::to_string(dmax) +
+                                                       " triangles (at most 16)");
+    }
     VertexTiles *T = new VertexTiles();
     build_vertex_tiles(vtx, tri, m->nv, m->nt, tile_tri_cap(m->q), T);
     auto up = [&](auto **dst, const auto &v) -> gyps_status {

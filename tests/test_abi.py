@@ -59,7 +59,8 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib_path):
 
 
 STRUCTS = {"_MeshInfo": "gyps_mesh_info_t", "_Profile": "gyps_profile_t", "_BatchItem": "gyps_batch_item",
-           "_BatchInfo": "gyps_batch_info_t", "_GmresOpts": "gyps_gmres_opts", "_GmresReport": "gyps_gmres_report"}
+           "_BatchInfo": "gyps_batch_info_t", "_GmresOpts": "gyps_gmres_opts", "_GmresReport": "gyps_gmres_report",
+           "_HmatInfo": "gyps_hmat_info_t"}
 
 
 def test_binding_structs_match_the_header_layout(tmp_path):

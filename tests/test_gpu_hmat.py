@@ -88,3 +88,28 @@ def test_sphere163842_k64_hmat_sampled_rows(g):
     ref = om.apply(64.0, f.cpu().numpy(), rows=rows)[rows]
     assert rel(y[rows], ref) < 1e-4, h.info
     h.close()
+
+
+def test_gmres_with_the_compressed_operator(g, sphere4):
+    """GMRES with the compressed far field in the Krylov loop and double-float
+    residual checks with refinement: the FP64 residual of the result meets the
+    tolerance and the solution agrees with an FP32-operator solve."""
+    gm, om = sphere4
+    k = 8.0
+    h = g.Hmat(gm, k, eps=1e-5, leaf_tiles=1, eta=0.5)
+    f = g.rhs_planewave(gm, k, [(0.0, 0.0, 1.0), (0.6, 0.0, 0.8)])
+    x, rep = g.gmres_solve(gm, k, f, tol=1e-6, restart=200, maxit=800, prec="hmat", check_prec="df64",
+                           max_refine=4, hmat=h)
+    assert rep.status == "OK" and (rep.true_residual <= 1e-6).all(), (rep.status, rep.true_residual)
+    r = f - g.sl_apply(gm, k, x, prec="fp64")
+    for c in range(2):
+        assert float(torch.linalg.norm(r[:, c]) / torch.linalg.norm(f[:, c])) <= 1.01e-6
+    x32, rep32 = g.gmres_solve(gm, k, f, tol=1e-8, restart=200, maxit=800, prec="fp32", check_prec="df64",
+                               max_refine=4)
+    assert rel(x.cpu().numpy(), x32.cpu().numpy()) < 1e-3  # both residuals below 1e-6; cond(V) amplifies
+    other = g.Hmat(gm, 9.0, eps=1e-5, leaf_tiles=1, eta=0.5)
+    with pytest.raises(g.GypsError) as e:
+        g.gmres_solve(gm, k, f, prec="hmat", hmat=other)
+    assert e.value.status == "INVALID"
+    other.close()
+    h.close()

@@ -138,3 +138,32 @@ def test_training_lowers_the_loss_and_fgmres_converges(g):
         assert r["gmres"]["status"] == "OK" and r["fgmres_mpnn"]["status"] == "OK", r
         assert r["fgmres_mpnn"]["true_residual"] <= 1e-6
     assert sum(r["fgmres_mpnn"]["iterations"] for r in rows) < sum(r["gmres"]["iterations"] for r in rows), rows
+
+
+def test_network_is_used_only_inside_its_training_range(g, tmp_path):
+    """The network records the electrical sizes k x radius it was trained on;
+    flexible GMRES leaves it out (fallback 2, plain GMRES iterations) for a
+    mesh and k outside that range widened by 25 %, and uses it inside; the
+    range survives a checkpoint."""
+    v, t = synth.icosphere(2)
+    mesh = g.Mesh(v, t, 3)
+    P = g.Precond(64, 4, seed=5)
+    lo, hi = P.range()
+    assert lo > hi  # untrained: no range
+    rng = np.random.default_rng(5)
+    R = torch.as_tensor(synth.random_complex(rng, mesh.nv, 4)).cuda()
+    P.train_step(mesh, 3.0, R, R, 0.0)  # lr = 0: the gradient only, the range is recorded
+    lo, hi = P.range()
+    assert abs(lo - 3.0) < 1e-6 and abs(hi - 3.0) < 1e-6  # unit sphere: radius 1
+    path = str(tmp_path / "p.bin")
+    P.save(path)
+    Q = g.Precond(64, 4, seed=6)
+    Q.load(path)
+    assert Q.range() == (lo, hi)
+    F = g.rhs_planewave(mesh, 9.0, [(0.0, 0.0, 1.0)])
+    x0, r0 = g.gmres_solve(mesh, 9.0, F, tol=1e-6, restart=100, prec="fp32", check_prec="df64")
+    x1, r1 = g.gmres_solve(mesh, 9.0, F, tol=1e-6, restart=100, prec="fp32", check_prec="df64", precond=Q)
+    assert r1.precond_fallback == 2 and r1.iterations == r0.iterations and r1.status == "OK"
+    F3 = g.rhs_planewave(mesh, 3.3, [(0.0, 0.0, 1.0)])
+    _, r2 = g.gmres_solve(mesh, 3.3, F3, tol=1e-6, restart=100, prec="fp32", check_prec="df64", precond=Q)
+    assert r2.precond_fallback != 2

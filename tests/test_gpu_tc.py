@@ -43,16 +43,34 @@ def test_tc_far_part_ellipsoid():
     assert rel(y, om.far_apply(11.0, x)) < TC_TOL
 
 
-def test_tc_rejects_laplace_and_partial_ranges():
+def test_tc_rejects_laplace():
     import paper_1804_00995_gb300 as g
     v, t = synth.icosphere(1)
     gm = g.Mesh(v, t, 3)
     x = torch.zeros((gm.nv, 16), dtype=torch.complex128, device="cuda")
-    for kw in (dict(k=0.0), dict(k=2.0, tri_range=(0, 10))):
-        kk = kw.pop("k")
-        with pytest.raises(g.GypsError) as e:
-            g.sl_apply(gm, kk, x, prec="tc_bf16x3", **kw)
-        assert e.value.status == "UNSUPPORTED"
+    with pytest.raises(g.GypsError) as e:
+        g.sl_apply(gm, 0.0, x, prec="tc_bf16x3")
+    assert e.value.status == "UNSUPPORTED"
+
+
+@pytest.mark.parametrize("nrhs", [16, 40])
+def test_tc_triangle_ranges_add_up(nrhs):
+    """Tensor-core applies over a partition of the test triangles (ragged cuts,
+    one range of a single triangle) sum to the full tensor-core apply, and each
+    partial apply matches the oracle's rows of that range."""
+    import paper_1804_00995_gb300 as g
+    v, t = synth.icosphere(3)
+    gm = g.Mesh(v, t, 3)
+    om = oracle.Mesh(v, t, 3)
+    x = synth.random_complex(np.random.default_rng(nrhs), om.nv, nrhs)
+    xd = torch.as_tensor(x).cuda()
+    full = g.sl_apply(gm, 9.0, xd, prec="tc_bf16x3").cpu().numpy()
+    cuts = [0, 300, 301, 777, om.nt]
+    parts = [g.sl_apply(gm, 9.0, xd, prec="tc_bf16x3", tri_range=(a, b)).cpu().numpy() for a, b in zip(cuts[:-1], cuts[1:])]
+    assert rel(sum(parts), full) < 1e-6
+    assert rel(full, om.apply(9.0, x)) < TC_TOL
+    empty = g.sl_apply(gm, 9.0, xd, prec="tc_bf16x3", tri_range=(5, 5)).cpu().numpy()
+    assert np.abs(empty).max() == 0.0
 
 
 @pytest.mark.slow

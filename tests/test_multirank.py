@@ -1,14 +1,17 @@
-"""Multi-rank design on CPU (gloo, world size 2): the operator is sharded by
-test triangles; each rank sums the far part over the target points of its
-triangles and the correction over its test triangles; one all-reduce of the
-nv x nrhs result gives the full apply.  The arithmetic is the oracle's; what
-is tested is the partition and the exchange step."""
+"""Multi-rank design on CPU (gloo, world sizes 2 and 3): the operator is
+sharded by test triangles with bench.py's partition (triangle_range); each rank
+sums the far part over the target points of its triangles and the correction
+over its test triangles; one all-reduce of the nv x nrhs result, in the layout
+bench.py reduces (the real view of the column-major block's transpose), gives
+the full apply.  The arithmetic is the oracle's; what is tested is the
+partition and the exchange step."""
 import os
 import socket
 
 import numpy as np
 import pytest
 
+import bench
 import oracle
 import synth
 
@@ -49,25 +52,32 @@ def _rank_main(rank, world, port, out):
     v, t = synth.icosphere(2)
     om = oracle.Mesh(v, t, 3)
     x = synth.random_complex(np.random.default_rng(1), om.nv, 2)
-    cuts = np.linspace(0, om.nt, world + 1).astype(int)
-    y = _partial_apply(om, 6.0, x, cuts[rank], cuts[rank + 1])
-    buf = torch.as_tensor(np.stack([y.real, y.imag]))
-    dist.all_reduce(buf, op=dist.ReduceOp.SUM)
+    tb, te = bench.triangle_range(rank, world, om.nt)
+    y = _partial_apply(om, 6.0, x, tb, te)
+    yt = torch.as_tensor(np.ascontiguousarray(y.T))  # (nrhs, nv): the transpose of the column-major block
+    dist.all_reduce(torch.view_as_real(yt), op=dist.ReduceOp.SUM)
     if rank == 0:
-        np.save(out, buf.numpy())
+        np.save(out, yt.numpy().T)
     dist.barrier()
     dist.destroy_process_group()
 
 
-def test_two_rank_partition_all_reduce(tmp_path):
+def test_triangle_ranges_partition():
+    for world in (1, 2, 3, 8):
+        r = [bench.triangle_range(q, world, 20480) for q in range(world)]
+        assert r[0][0] == 0 and r[-1][1] == 20480
+        assert all(a[1] == b[0] for a, b in zip(r[:-1], r[1:]))
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_rank_partition_all_reduce(tmp_path, world):
     oracle.build()  # compile once before the ranks start
     import torch.multiprocessing as mp
     out = str(tmp_path / "y.npy")
-    mp.spawn(_rank_main, args=(2, _free_port(), out), nprocs=2, join=True)
-    got = np.load(out)
+    mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
+    y = np.load(out)
     v, t = synth.icosphere(2)
     om = oracle.Mesh(v, t, 3)
     x = synth.random_complex(np.random.default_rng(1), om.nv, 2)
     ref = om.apply(6.0, x)
-    y = got[0] + 1j * got[1]
     assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
