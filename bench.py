@@ -72,8 +72,8 @@ def parse():
                    help="sphere163842_k64_q3_r16 --solve: learned preconditioner saved by --save-precond")
     p.add_argument("--solve-maxit", type=int, default=1500)
     p.add_argument("--hmat-eps", type=float, default=1e-5, help="hmat workload: tolerance of the low-rank blocks")
-    p.add_argument("--hmat-leaf", type=int, default=16, help="hmat workload: vertex tiles per cluster")
-    p.add_argument("--hmat-eta", type=float, default=1.0, help="hmat workload: admissibility parameter")
+    p.add_argument("--hmat-leaf", type=int, default=8, help="hmat workload: vertex tiles per cluster")
+    p.add_argument("--hmat-eta", type=float, default=0.5, help="hmat workload: admissibility parameter")
     return p.parse_args()
 
 
@@ -1037,7 +1037,7 @@ def run_large(args):
 def run_hmat(args):
     """Workload hmat_sphere163842_k64_q3_r16: the compressed far field of the
     icosphere with 327680 triangles (q = 3, 983040 points) at k = 64 (eps 1e-5,
-    clusters of 16 vertex tiles, eta 1), 16 plane waves.  One step = one apply
+    clusters of 8 vertex tiles, eta 0.5 by default), 16 plane waves.  One step = one apply
     of H + C to all 16 columns.  Reported: build time, stored bytes against the
     dense matrix, ranks, the apply time next to one tensor-core all-pairs apply
     of the same columns, and the difference to the FP32 all-pairs apply on two

@@ -518,7 +518,7 @@ class Hmat:
     (gyps_hmat_create / apply): Y = (H + C) X, H the block low-rank Gauss-Gauss
     part to relative tolerance eps."""
 
-    def __init__(self, mesh: "Mesh", k: float, eps: float = 1e-5, leaf_tiles: int = 16, eta: float = 1.0,
+    def __init__(self, mesh: "Mesh", k: float, eps: float = 1e-5, leaf_tiles: int = 8, eta: float = 0.5,
                  stream=None):
         self.mesh = mesh
         self.k = float(k)
