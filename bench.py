@@ -57,7 +57,9 @@ def parse():
                             "efie_sphere10242_k8_q3", "hmat_sphere163842_k64_q3_r16"])
     p.add_argument("--precond-meshes", type=int, default=125, help="training meshes (16 solves each)")
     p.add_argument("--precond-steps", type=int, default=3000)
-    p.add_argument("--precond-test", type=int, default=8)
+    p.add_argument("--precond-test", type=int, default=50, help="held-out meshes (4 plane waves each)")
+    p.add_argument("--precond-data", default="krylov", choices=["noise", "krylov", "both"],
+                   help="training pairs: white-noise residuals, Krylov-iteration errors, or both")
     p.add_argument("--save-precond", default="", help="write the trained network here")
     p.add_argument("--nrhs", type=int, default=1, help="right-hand sides per apply (the workload has 1)")
     p.add_argument("--prec", default="fp32", choices=["fp32", "tc_bf16x3", "auto"],
@@ -533,11 +535,13 @@ def run_batch(args):
 
 def run_precond(args):
     """Workload precond_ellipsoids: learned message-passing preconditioner.
-    Training pairs (white-noise residual r, correction e = V^{-1} r) come from
-    the library's own GMRES solves (16 per mesh) on random ellipsoids of
-    5120-20480 triangles (q = 3) at k ~ U[4, 16] (seed 995); the network is
-    trained by the library's kernels; held-out ellipsoids (seed 996) with
-    plane-wave right-hand sides are solved to 1e-6 (FP64 residual) by flexible
+    Training pairs come from the library's own solves on random ellipsoids of
+    5120-20480 triangles (q = 3) at k ~ U[4, 16] (seed 995): by default the
+    errors of GMRES iterates on plane-wave right-hand sides with their
+    residuals (Krylov pairs), optionally also white-noise residuals r with
+    their corrections e = V^{-1} r (16 GMRES solves per mesh); the network is trained by the
+    library's kernels; held-out ellipsoids (seed 996) with 4 plane-wave
+    right-hand sides each are solved to 1e-6 (FP64 residual) by flexible
     GMRES + network and by plain GMRES."""
     import torch
 
@@ -547,7 +551,15 @@ def run_precond(args):
     gb.build()
     t0 = time.perf_counter()
     train_meshes = pt.random_meshes(995, args.precond_meshes, levels=(4, 5))
-    pairs, stats = pt.make_pairs(train_meshes, nrhs=16, tol=1e-3, maxit=300, seed=1)
+    pairs, stats = [], []
+    if args.precond_data in ("noise", "both"):
+        p_n, s_n = pt.make_pairs(train_meshes, nrhs=16, tol=1e-3, maxit=300, seed=1)
+        pairs += p_n
+        stats += s_n
+    if args.precond_data in ("krylov", "both"):
+        p_k, s_k = pt.make_krylov_pairs(train_meshes, ndirs=4, steps=(5, 15, 40), tol=1e-5, maxit=600, seed=3)
+        pairs += p_k
+        stats += s_k
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     P = g.Precond(64, 4, seed=995)
@@ -562,18 +574,29 @@ def run_precond(args):
     it_p = sum(r["fgmres_mpnn"]["iterations"] for r in both)
     s_g = sum(r["gmres"]["seconds"] for r in both)
     s_p = sum(r["fgmres_mpnn"]["seconds"] for r in both)
+    kept = [r for r in both if r["fgmres_mpnn"]["fallback"] == 0]
+
+    def tot(rs, solver, key):
+        return sum(r[solver][key] for r in rs)
     line = {
         "metric": "GMRES to 1e-6: flexible GMRES + learned preconditioner vs plain GMRES (iterations, seconds)",
         "value": (s_g / s_p) if s_p > 0 else None, "unit": "x (plain seconds / preconditioned seconds)",
         "higher_is_better": True, "data": "synthetic", "dtype": "bf16 weights, f32 activations",
-        "config": {"workload": "precond_ellipsoids", "train_meshes": len(train_meshes),
-                   "solves_generated": 16 * len(train_meshes), "pairs_kept": int(sum(s["kept"] for s in stats)),
+        "config": {"workload": "precond_ellipsoids", "train_meshes": len(train_meshes), "train_data": args.precond_data,
+                   "pairs_kept": int(sum(s["kept"] for s in stats)),
                    "levels": [4, 5], "k_range": [4, 16], "hidden": 64, "layers": 4, "steps": args.precond_steps,
                    "test_meshes": len(test_meshes), "rhs_per_test_mesh": 4, "restart": 100},
         "data_seconds": t_data, "train_seconds": log.seconds,
         "train_loss": log.losses,
         "both_converged": len(both), "iterations_plain": it_g, "iterations_precond": it_p,
         "seconds_plain": s_g, "seconds_precond": s_p,
+        "all_meshes": {"seconds_plain": tot(rows, "gmres", "seconds"), "seconds_precond": tot(rows, "fgmres_mpnn", "seconds"),
+                       "iterations_plain": tot(rows, "gmres", "iterations"),
+                       "iterations_precond": tot(rows, "fgmres_mpnn", "iterations")},
+        "network_kept": {"meshes": len(kept), "seconds_plain": tot(kept, "gmres", "seconds"),
+                         "seconds_precond": tot(kept, "fgmres_mpnn", "seconds"),
+                         "iterations_plain": tot(kept, "gmres", "iterations"),
+                         "iterations_precond": tot(kept, "fgmres_mpnn", "iterations")},
         "rows": [{k: (v if not isinstance(v, float) else round(v, 4)) for k, v in r.items()} for r in rows],
     }
     print(json.dumps(line), flush=True)

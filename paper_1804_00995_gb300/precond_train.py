@@ -72,6 +72,40 @@ def make_pairs(meshes, nrhs: int = 16, tol: float = 1e-2, maxit: int = 400, seed
     return pairs, stats
 
 
+def make_krylov_pairs(meshes, ndirs: int = 4, steps=(5, 15, 40), tol: float = 1e-5, maxit: int = 600, seed: int = 0):
+    """Pairs from the solver's own Krylov iterations.  For plane-wave
+    right-hand sides F (ndirs random directions) on each mesh: the GMRES
+    solution X* (to tol) and the iterates X_m after m GMRES steps from zero
+    (m in `steps`).  The errors E_m = X* - X_m and their residuals
+    R_m = V E_m (one apply, so each pair is exact whatever tol) are the inputs
+    and corrections that flexible GMRES hands the network.  Columns whose
+    solve stalls (near an interior resonance) give no pairs.
+    Returns (pairs, stats) like make_pairs."""
+    import torch
+    rng = np.random.default_rng(seed)
+    pairs, stats = [], []
+    for mesh, k, _ in meshes:
+        F = g.rhs_planewave(mesh, k, synth.plane_wave_dirs(rng, ndirs))
+        Xs, rep = g.gmres_solve(mesh, k, F, tol=tol, restart=100, maxit=maxit, prec="auto", check_prec="fp32",
+                                max_refine=0)
+        keep = np.flatnonzero(rep.converged)
+        stats.append(dict(iterations=rep.iterations, kept=int(keep.size) * len(steps), k=k))
+        if not keep.size:
+            continue
+        idx = torch.as_tensor(keep, device=Xs.device)
+        Rs, Es = [], []
+        for m in steps:
+            Xm, _ = g.gmres_solve(mesh, k, F, tol=1e-14, restart=m, maxit=m, prec="auto", check_prec="fp32",
+                                  max_refine=0)
+            E = (Xs[:, idx] - Xm[:, idx]).t().contiguous().t()
+            Rs.append(g.sl_apply(mesh, k, E, prec="fp32"))
+            Es.append(E)
+        R = torch.cat(Rs, dim=1).t().contiguous().t()
+        E = torch.cat(Es, dim=1).t().contiguous().t()
+        pairs.append(Pair(mesh, k, R, E))
+    return pairs, stats
+
+
 def train(P: "g.Precond", pairs, steps: int, lr: float = 1e-3, batch: int = 16, seed: int = 0, log_every: int = 50,
           lr_final: float = 1e-4):
     """Adam on random minibatches (columns of one pair set), cosine-free
