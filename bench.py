@@ -76,6 +76,9 @@ def parse():
     p.add_argument("--hmat-eps", type=float, default=1e-5, help="hmat workload: tolerance of the low-rank blocks")
     p.add_argument("--hmat-leaf", type=int, default=8, help="hmat workload: vertex tiles per cluster")
     p.add_argument("--hmat-eta", type=float, default=0.5, help="hmat workload: admissibility parameter")
+    p.add_argument("--hmat-level", type=int, default=0,
+                   help="hmat workload: icosphere level of a smaller case (0: the workload's level 7)")
+    p.add_argument("--hmat-k", type=float, default=0.0, help="hmat workload: wavenumber of a smaller case (0: 64)")
     return p.parse_args()
 
 
@@ -1071,9 +1074,10 @@ def run_hmat(args):
     from paper_1804_00995_gb300 import build as gb
     gb.build()
     cfg = synth.WORKLOADS["sphere163842_k64_q3_r16"]
-    v, t = synth.icosphere(cfg["level"])
+    level = args.hmat_level if args.hmat_level > 0 else cfg["level"]
+    v, t = synth.icosphere(level)
     mesh = g.Mesh(v, t, cfg["q"])
-    k = cfg["k"]
+    k = args.hmat_k if args.hmat_k > 0 else cfg["k"]
     dirs = synth.plane_wave_dirs(np.random.default_rng(cfg["seed"]), cfg["ndirs"])
     x = g.rhs_planewave(mesh, k, dirs)
     torch.cuda.synchronize()
@@ -1115,11 +1119,13 @@ def run_hmat(args):
         "metric": "compressed far field: ms per 16-column apply", "value": ms, "unit": "ms",
         "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
         "dtype": "f32 blocks, f64 correction and output",
-        "config": {"workload": "hmat_sphere163842_k64_q3_r16", "nv": mesh.nv, "nq": mesh.nq, "k": k, "nrhs": 16,
+        "config": {"workload": "hmat_sphere163842_k64_q3_r16" if level == cfg["level"] and k == cfg["k"]
+                   else f"hmat_icosphere{level}_k{k:g}_q3_r16 (smaller case)", "nv": mesh.nv, "nq": mesh.nq, "k": k, "nrhs": 16,
                    "eps": args.hmat_eps, "leaf_tiles": args.hmat_leaf, "eta": args.hmat_eta,
                    "l2": "blocks (tens of GB) larger than L2"},
         "build_s": build_s, "hmat": info, "compression": info["bytes"] / info["dense_bytes"],
         "stream_gbs": info["bytes"] / (ms * 1e-3) / 1e9,
+        "roofline": hmat_roofline(info, ms, clk),
         "equivalent_gpairs_per_s": pairs / (ms * 1e-3) / 1e9,
         "tensor_core_all_pairs_ms": tc_ms, "speedup_vs_tensor_core_all_pairs": tc_ms / ms,
         "diff_vs_fp32_all_pairs": {"columns": 2, "norm": err_norm, "element": err_elem},
@@ -1129,6 +1135,27 @@ def run_hmat(args):
         line["solve"] = solve_large(g, mesh, v, t, k, x, dirs, args, hmat=h)
     print(json.dumps(line), flush=True)
     h.close()
+
+
+def hmat_roofline(info, ms, clk):
+    """Roofline of the compressed apply, timed whole (gather, projections, rows, correction):
+    every stored complex FP32 value meets the 16 columns once in the rows kernel (16 complex
+    multiply-adds = 64 FP32 FMAs); the CUDA-core FMA peak is 152 SMs x 128 lanes x the measured
+    maximum SM clock.  The HBM view (stored bytes per apply over the measured copy bandwidth) is
+    given beside it."""
+    try:
+        peaks = json.loads(read_text(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {}
+    mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    fma = info["bytes"] / 8.0 * 64.0
+    achieved = fma / (ms * 1e-3) / 1e12
+    peak = 152 * 128 * mhz * 1e6 / 1e12
+    hbm = peaks.get("hbm_gbs")
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFMA/s", "frac": achieved / peak,
+            "peak_basis": f"152 SMs x 128 FP32 lanes x {mhz:g} MHz (of measured clock)",
+            "kernel": "hm_rows16_kernel (whole apply timed)", "traffic": None,
+            "hbm_frac": (info["bytes"] / (ms * 1e-3) / 1e9) / hbm if hbm else None}
 
 
 def run_assemble(args):

@@ -77,12 +77,17 @@ struct Hmat {
     // apply plan
     hm::Term *d_terms = nullptr;
     int32_t *d_term_ptr = nullptr;  // nc + 1
-    hm::Proj *d_proj = nullptr;
+    hm::Proj *d_proj = nullptr;  // sorted by source range
+    int2 *d_pgroups = nullptr;     // projections [x, y) sharing one source range (at most 32)
+    int64_t n_pgroups = 0;
+    int proj16_smem = 0;           // shared memory of hm_project16_kernel (0: not used)
     int64_t nproj = 0, tlen = 0;
     int32_t max_rank = 0;
     float2 *d_T = nullptr, *d_xloc = nullptr;
     int64_t row_chunks = 0;
     int64_t *d_chunk_cluster = nullptr;  // per row chunk: cluster << 32 | chunk index
+    int4 *d_rows_items = nullptr;        // 16-column pass: (cluster, row chunk, terms [z, w)), largest first
+    int64_t n_rows_items = 0;
     int64_t *voff_dev = nullptr;         // device copy of voff
     // statistics
     int64_t n_dense = 0, n_lowrank = 0, n_fallback = 0;
@@ -398,6 +403,79 @@ __global__ void __launch_bounds__(256) hm_project_kernel(const hm::Proj *proj, c
     if (ci < NR && p0 + pi < pr.r) T[pr.toff + (int64_t)(p0 + pi) * hm::NRC + ci] = acc;
 }
 
+// Butterfly reduce-scatter over a warp: on return, lane l holds the sum over
+// all 32 lanes of value l (at each step a lane keeps one half of its values and
+// adds the partner's copy of that half).
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int o = 16 >> st, h = 16 >> st;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+// The projections of the 16-column pass, grouped by source cluster: a CTA takes
+// projections [g.x, g.y) that share one source range x[src : src + len], stages
+// those 16 columns of x in shared memory once (xs[cp][j] = (x[j][2 cp],
+// x[j][2 cp + 1])), and each warp takes whole projections, two of their
+// columns at a time: lanes stride over j reading F coalesced, 16 complex sums
+// per column, then a reduce-scatter leaves value l = 2 c + (re, im) of the
+// column on lane l, stored as one 128-byte row of T.
+__global__ void __launch_bounds__(256) hm_project16_kernel(const hm::Proj *proj, const int2 *groups,
+                                                           const float2 *xloc, int64_t nv, float2 *T)
+{
+    extern __shared__ float4 xs[];
+    const int2 gr = groups[blockIdx.x];
+    const int64_t src = proj[gr.x].src, len = proj[gr.x].len;
+    for (int64_t e = threadIdx.x; e < 8 * len; e += blockDim.x) {
+        const int cp = (int)(e / len);
+        const int64_t j = e - (int64_t)cp * len;
+        const float2 a = xloc[src + j + (int64_t)(2 * cp) * nv], b = xloc[src + j + (int64_t)(2 * cp + 1) * nv];
+        xs[e] = make_float4(a.x, a.y, b.x, b.y);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    float *Tf = reinterpret_cast<float *>(T);
+    for (int pi = gr.x + warp; pi < gr.y; pi += nwarps) {
+        const hm::Proj pr = proj[pi];
+        for (int p = 0; p < pr.r; p += 2) {
+            const bool two = p + 1 < pr.r;
+            const float2 *F0 = pr.F + (int64_t)p * len, *F1 = two ? F0 + len : F0;
+            float v0[32], v1[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v0[i] = v1[i] = 0.f;
+#pragma unroll 2
+            for (int64_t j = lane; j < len; j += 32) {
+                const float2 f0 = F0[j], f1 = F1[j];
+#pragma unroll
+                for (int cp = 0; cp < 8; ++cp) {
+                    const float4 x = xs[(int64_t)cp * len + j];
+                    v0[4 * cp + 0] = fmaf(f0.x, x.x, fmaf(-f0.y, x.y, v0[4 * cp + 0]));
+                    v0[4 * cp + 1] = fmaf(f0.x, x.y, fmaf(f0.y, x.x, v0[4 * cp + 1]));
+                    v0[4 * cp + 2] = fmaf(f0.x, x.z, fmaf(-f0.y, x.w, v0[4 * cp + 2]));
+                    v0[4 * cp + 3] = fmaf(f0.x, x.w, fmaf(f0.y, x.z, v0[4 * cp + 3]));
+                    v1[4 * cp + 0] = fmaf(f1.x, x.x, fmaf(-f1.y, x.y, v1[4 * cp + 0]));
+                    v1[4 * cp + 1] = fmaf(f1.x, x.y, fmaf(f1.y, x.x, v1[4 * cp + 1]));
+                    v1[4 * cp + 2] = fmaf(f1.x, x.z, fmaf(-f1.y, x.w, v1[4 * cp + 2]));
+                    v1[4 * cp + 3] = fmaf(f1.x, x.w, fmaf(f1.y, x.z, v1[4 * cp + 3]));
+                }
+            }
+            const float s0 = reduce_scatter32(v0, lane);
+            const float s1 = reduce_scatter32(v1, lane);
+            Tf[2 * (pr.toff + (int64_t)p * hm::NRC) + lane] = s0;
+            if (two) Tf[2 * (pr.toff + (int64_t)(p + 1) * hm::NRC) + lane] = s1;
+        }
+    }
+}
+
 // y[rows of cluster A, chunk of 128] = sum over the cluster's terms, written to Y (FP64).
 template <int NR>
 __global__ void __launch_bounds__(128) hm_rows_kernel(const hm::Term *terms, const int32_t *term_ptr,
@@ -469,114 +547,147 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src, int src_by
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // The row sums of hm_rows_kernel for 16 right-hand sides, tiled: a CTA owns 128
-// rows of a cluster; the columns of each term (a dense block, or U with its
-// projection) stream through shared memory in chunks of 32 (double-buffered
-// asynchronous copies, zero-filled past the block's edge); each thread owns 4
-// rows x 4 right-hand sides (16 complex sums) and reads per column 32 bytes of
-// the matrix and 32 bytes of x.  Chunk sums are folded into TwoSum pairs.
-constexpr int RT_ROWS = 128, RT_K = 32;
+// rows of a cluster; the columns of its terms (dense blocks, and U with its
+// projection) stream through shared memory as one sequence of units of up to
+// RT_K columns, RT_S stages deep across term boundaries (asynchronous copies,
+// zero-filled past a block's edge), so that no term restarts the pipeline.
+// Each thread owns 4 rows (32 apart) x 4 right-hand sides (16 complex sums)
+// and reads per column 4 complex values of the matrix and 4 of x; unit sums
+// are folded into TwoSum pairs.
+#ifndef GYPS_RT_K
+#define GYPS_RT_K 32
+#endif
+#ifndef GYPS_RT_S
+#define GYPS_RT_S 2
+#endif
+constexpr int RT_ROWS = 128, RT_K = GYPS_RT_K, RT_S = GYPS_RT_S;
 struct RowsTileSmem {
-    float2 M[2][RT_K][RT_ROWS];     // 64 KB
-    float2 X[2][RT_K][hm::NRC];     // 8 KB
+    float2 M[RT_S][RT_K][RT_ROWS];
+    float2 X[RT_S][RT_K][hm::NRC];
 };
 
-__global__ void __launch_bounds__(128) hm_rows16_kernel(const hm::Term *terms, const int32_t *term_ptr,
-                                                        const int64_t *voff, const int64_t *chunk_cluster,
-                                                        const int32_t *perm, const float2 *xloc, int64_t nv,
-                                                        const float2 *T, double2 *Y, int64_t ldy, int c0)
+// Work item of a CTA: one row chunk of a cluster and a contiguous range of its
+// terms, cut so that items carry similar numbers of units and launched largest
+// first; the items of a row chunk add into Y (zeroed before the pass).
+// Position in a CTA's sequence of units: term tt, first column j0.
+struct UnitCursor {
+    int tt, j0;
+};
+
+__global__ void __launch_bounds__(128) hm_rows16_kernel(const hm::Term *terms, const int4 *items,
+                                                        const int64_t *voff, const int32_t *perm,
+                                                        const float2 *xloc, int64_t nv, const float2 *T, double2 *Y,
+                                                        int64_t ldy, int c0)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     RowsTileSmem &sm = *reinterpret_cast<RowsTileSmem *>(smraw);
-    const int64_t cc = chunk_cluster[blockIdx.x];
-    const int A = (int)(cc >> 32), chunk = (int)(cc & 0xffffffff);
+    const int4 item = items[blockIdx.x];
+    const int A = item.x;
     const int64_t mA = voff[A + 1] - voff[A];
-    const int64_t row0 = (int64_t)chunk * RT_ROWS;
-    const int tid = threadIdx.x, rg = tid & 31, cg = tid >> 5;  // rows 4 rg .. 4 rg + 3, RHS 4 cg .. 4 cg + 3
+    const int64_t row0 = (int64_t)item.y * RT_ROWS;
+    // rows rg, rg + 32, rg + 64, rg + 96 (consecutive lanes read consecutive rows: no bank
+    // conflicts), RHS 4 cg .. 4 cg + 3 (one per warp: broadcast reads)
+    const int tid = threadIdx.x, rg = tid & 31, cg = tid >> 5;
+    const int tt_end = item.w;
     float2 hi[4][4], lo[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = make_float2(0.f, 0.f);
 
-    for (int tt = term_ptr[A]; tt < term_ptr[A + 1]; ++tt) {
-        const hm::Term t = terms[tt];
-        const int nchunks = (t.ncol + RT_K - 1) / RT_K;
-        // issue chunk q into buffer q & 1: 32 columns x 128 rows of M, 32 x 16 values of x (or of the projection)
-        auto issue = [&](int q) {
-            const int buf = q & 1, j0 = q * RT_K;
+    // copies of the unit at cursor u into stage st (an empty commit group past the end)
+    auto issue = [&](UnitCursor &u, int st) {
+        if (u.tt < tt_end) {
+            const hm::Term t = terms[u.tt];
 #pragma unroll 8
-            for (int u = 0; u < RT_K * RT_ROWS / 128; ++u) {  // 32 copies per thread, rows fastest
-                const int e = tid + 128 * u, jj = e / RT_ROWS, rr = e % RT_ROWS;
-                const int64_t row = row0 + rr, col = j0 + jj;
+            for (int k = 0; k < RT_K * RT_ROWS / 128; ++k) {  // rows fastest
+                const int e = tid + 128 * k, jj = e / RT_ROWS, rr = e % RT_ROWS;
+                const int64_t row = row0 + rr, col = u.j0 + jj;
                 const bool ok = col < t.ncol && row < mA;
-                cp_async8(&sm.M[buf][jj][rr], t.M + (ok ? row + col * t.ld : 0), ok ? 8 : 0);
+                cp_async8(&sm.M[st][jj][rr], t.M + (ok ? row + col * t.ld : 0), ok ? 8 : 0);
             }
-#pragma unroll
-            for (int u = 0; u < RT_K * hm::NRC / 128; ++u) {  // 4 copies per thread
-                const int e = tid + 128 * u, jj = e / hm::NRC, c = e % hm::NRC;
-                const int64_t col = j0 + jj;
+            for (int e = tid; e < RT_K * hm::NRC; e += 128) {
+                const int jj = e / hm::NRC, c = e % hm::NRC;
+                const int64_t col = u.j0 + jj;
                 const bool ok = col < t.ncol;
                 const float2 *src = t.kind == 0 ? xloc + (ok ? t.src + col + (int64_t)c * nv : 0)
                                                 : T + (ok ? t.src + col * hm::NRC + c : 0);
-                cp_async8(&sm.X[buf][jj][c], src, ok ? 8 : 0);
+                cp_async8(&sm.X[st][jj][c], src, ok ? 8 : 0);
             }
-            cp_async_commit();
-        };
-        __syncthreads();  // the previous term's buffers are consumed
-        issue(0);
-        for (int q = 0; q < nchunks; ++q) {
-            if (q + 1 < nchunks) {
-                issue(q + 1);
-                cp_async_wait1();
-            } else {
-                cp_async_wait0();
+            u.j0 += RT_K;
+            if (u.j0 >= t.ncol) {
+                ++u.tt;
+                u.j0 = 0;
             }
-            __syncthreads();
-            const int buf = q & 1;
-            float2 acc[4][4];
+        }
+        cp_async_commit();
+    };
+
+    UnitCursor ui{item.z, 0}, uc{item.z, 0};
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+    for (int st = 0; st + 1 < RT_S; ++st) issue(ui, st);
+    for (int q = 0; uc.tt < tt_end; ++q) {
+        issue(ui, (q + RT_S - 1) % RT_S);  // its stage held unit q - 1, consumed before the last barrier
+        cp_async_wait_n<RT_S - 1>();        // unit q landed
+        __syncthreads();
+        const int st = q % RT_S;
+        const int ncol = terms[uc.tt].ncol;
+        const int nj = min(RT_K, ncol - uc.j0);
+        float2 acc[4][4];
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+        const int njr = (nj + 3) & ~3;  // zero-filled past the edge
 #pragma unroll 4
-            for (int jj = 0; jj < RT_K; ++jj) {
-                const float4 m01 = *reinterpret_cast<const float4 *>(&sm.M[buf][jj][4 * rg]);
-                const float4 m23 = *reinterpret_cast<const float4 *>(&sm.M[buf][jj][4 * rg + 2]);
-                const float4 x01 = *reinterpret_cast<const float4 *>(&sm.X[buf][jj][4 * cg]);
-                const float4 x23 = *reinterpret_cast<const float4 *>(&sm.X[buf][jj][4 * cg + 2]);
-                const float2 mv[4] = {make_float2(m01.x, m01.y), make_float2(m01.z, m01.w), make_float2(m23.x, m23.y),
-                                      make_float2(m23.z, m23.w)};
-                const float2 xv[4] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w), make_float2(x23.x, x23.y),
-                                      make_float2(x23.z, x23.w)};
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        acc[a][b].x = fmaf(mv[a].x, xv[b].x, fmaf(-mv[a].y, xv[b].y, acc[a][b].x));
-                        acc[a][b].y = fmaf(mv[a].x, xv[b].y, fmaf(mv[a].y, xv[b].x, acc[a][b].y));
-                    }
-            }
+        for (int jj = 0; jj < njr; ++jj) {
+            const float4 x01 = *reinterpret_cast<const float4 *>(&sm.X[st][jj][4 * cg]);
+            const float4 x23 = *reinterpret_cast<const float4 *>(&sm.X[st][jj][4 * cg + 2]);
+            const float2 mv[4] = {sm.M[st][jj][rg], sm.M[st][jj][rg + 32], sm.M[st][jj][rg + 64],
+                                  sm.M[st][jj][rg + 96]};
+            const float2 xv[4] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w), make_float2(x23.x, x23.y),
+                                  make_float2(x23.z, x23.w)};
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    two_sum_acc(hi[a][b].x, lo[a][b].x, acc[a][b].x);
-                    two_sum_acc(hi[a][b].y, lo[a][b].y, acc[a][b].y);
+                    acc[a][b].x = fmaf(mv[a].x, xv[b].x, fmaf(-mv[a].y, xv[b].y, acc[a][b].x));
+                    acc[a][b].y = fmaf(mv[a].x, xv[b].y, fmaf(mv[a].y, xv[b].x, acc[a][b].y));
                 }
-            __syncthreads();  // buffer q & 1 is free for chunk q + 2
         }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                two_sum_acc(hi[a][b].x, lo[a][b].x, acc[a][b].x);
+                two_sum_acc(hi[a][b].y, lo[a][b].y, acc[a][b].y);
+            }
+        uc.j0 += RT_K;
+        if (uc.j0 >= ncol) {
+            ++uc.tt;
+            uc.j0 = 0;
+        }
+        __syncthreads();  // stage st is free for unit q + RT_S
     }
+    cp_async_wait_n<0>();  // empty groups only, by now
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const int64_t i = row0 + 4 * rg + a;
+        const int64_t i = row0 + rg + 32 * a;
         if (i >= mA) continue;
         const int64_t v = perm[voff[A] + i];
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-            Y[v + (int64_t)(c0 + 4 * cg + b) * ldy] =
-                make_double2((double)hi[a][b].x + (double)lo[a][b].x, (double)hi[a][b].y + (double)lo[a][b].y);
+        for (int b = 0; b < 4; ++b) {
+            double *y = reinterpret_cast<double *>(Y + v + (int64_t)(c0 + 4 * cg + b) * ldy);
+            atomicAdd(y, (double)hi[a][b].x + (double)lo[a][b].x);  // a row chunk's terms span several CTAs
+            atomicAdd(y + 1, (double)hi[a][b].y + (double)lo[a][b].y);
+        }
     }
 }
 
@@ -940,6 +1051,49 @@ static gyps_status build(Hmat *h, cudaStream_t s)
         ptr.push_back((int32_t)flat.size());
         for (int64_t q = 0; q * 128 < msize((int)c); ++q) chunks.push_back((c << 32) | q);
     }
+    // projections grouped by source range for the 16-column pass (stable: ties keep block order)
+    std::stable_sort(proj.begin(), proj.end(), [](const hm::Proj &a, const hm::Proj &b) { return a.src < b.src; });
+    std::vector<int2> groups;
+    int64_t maxlen = 0;
+    for (size_t i = 0; i < proj.size();) {
+        size_t e = i;
+        while (e < proj.size() && proj[e].src == proj[i].src && e - i < 32) ++e;
+        groups.push_back(make_int2((int)i, (int)e));
+        maxlen = std::max<int64_t>(maxlen, proj[i].len);
+        i = e;
+    }
+    const int64_t psmem = 8 * maxlen * (int64_t)sizeof(float4);
+    h->proj16_smem = psmem <= 200 * 1024 ? (int)psmem : 0;
+    h->n_pgroups = (int64_t)groups.size();
+    GYPS_TRY(upload(h, &h->d_pgroups, groups, s));
+    // 16-column rows pass: row chunks cut into term ranges of at most `cap` units, largest first
+    {
+        auto units_of = [](const hm::Term &t) { return (int64_t)(t.ncol + RT_K - 1) / RT_K; };
+        int64_t total = 0;
+        for (int64_t c = 0; c < h->nc; ++c)
+            for (int32_t tt = ptr[c]; tt < ptr[c + 1]; ++tt) total += units_of(flat[tt]) * ((msize((int)c) + 127) / 128);
+        const int64_t cap = std::max<int64_t>(32, total / 4096);
+        std::vector<std::pair<int64_t, int4>> items;
+        for (int64_t c = 0; c < h->nc; ++c)
+            for (int q = 0; (int64_t)q * 128 < msize((int)c); ++q) {
+                int32_t tb = ptr[c];
+                int64_t u = 0;
+                for (int32_t tt = ptr[c]; tt < ptr[c + 1]; ++tt) {
+                    u += units_of(flat[tt]);
+                    if (u >= cap || tt + 1 == ptr[c + 1]) {
+                        items.push_back({u, make_int4((int)c, q, tb, tt + 1)});
+                        tb = tt + 1;
+                        u = 0;
+                    }
+                }
+            }
+        std::stable_sort(items.begin(), items.end(),
+                         [](const std::pair<int64_t, int4> &a, const std::pair<int64_t, int4> &b) { return a.first > b.first; });
+        std::vector<int4> iv;
+        for (auto &it : items) iv.push_back(it.second);
+        h->n_rows_items = (int64_t)iv.size();
+        GYPS_TRY(upload(h, &h->d_rows_items, iv, s));
+    }
     h->nproj = (int64_t)proj.size();
     h->tlen = toff;
     h->row_chunks = (int64_t)chunks.size();
@@ -962,7 +1116,13 @@ static gyps_status apply_pass(Hmat *h, const double2 *X, int64_t ldx, double2 *Y
     const int64_t nv = h->m->nv;
     hm_gather_kernel<<<dim3((unsigned)((nv + 255) / 256), NR), 256, 0, s>>>(h->d_perm, nv, X, ldx, c0, NR, h->d_xloc);
     GYPS_CUDA(cudaGetLastError());
-    if (h->nproj > 0) {
+    if (h->nproj > 0 && NR == hm::NRC && h->proj16_smem > 0) {
+        GYPS_CUDA(cudaFuncSetAttribute(hm_project16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       h->proj16_smem));
+        hm_project16_kernel<<<(unsigned)h->n_pgroups, 256, h->proj16_smem, s>>>(h->d_proj, h->d_pgroups, h->d_xloc,
+                                                                              nv, h->d_T);
+        GYPS_CUDA(cudaGetLastError());
+    } else if (h->nproj > 0) {
         hm_project_kernel<NR><<<dim3((unsigned)h->nproj, (unsigned)((h->max_rank + 15) / 16)), 256, 0, s>>>(
             h->d_proj, h->d_xloc, nv, h->d_T);
         GYPS_CUDA(cudaGetLastError());
@@ -970,9 +1130,11 @@ static gyps_status apply_pass(Hmat *h, const double2 *X, int64_t ldx, double2 *Y
     if (NR == hm::NRC) {
         const int smem = (int)sizeof(RowsTileSmem);
         GYPS_CUDA(cudaFuncSetAttribute(hm_rows16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        hm_rows16_kernel<<<(unsigned)h->row_chunks, 128, smem, s>>>(h->d_terms, h->d_term_ptr, h->voff_dev,
-                                                                   h->d_chunk_cluster, h->d_perm, h->d_xloc, nv,
-                                                                   h->d_T, Y, ldy, c0);
+        GYPS_CUDA(cudaMemset2DAsync(Y + (int64_t)c0 * ldy, (size_t)ldy * sizeof(double2), 0,
+                                    (size_t)nv * sizeof(double2), hm::NRC, s));
+        if (h->n_rows_items > 0)
+            hm_rows16_kernel<<<(unsigned)h->n_rows_items, 128, smem, s>>>(h->d_terms, h->d_rows_items, h->voff_dev,
+                                                                         h->d_perm, h->d_xloc, nv, h->d_T, Y, ldy, c0);
     } else {
         hm_rows_kernel<NR><<<(unsigned)h->row_chunks, 128, 0, s>>>(h->d_terms, h->d_term_ptr, h->voff_dev,
                                                                  h->d_chunk_cluster, h->d_perm, h->d_xloc, nv, h->d_T,
