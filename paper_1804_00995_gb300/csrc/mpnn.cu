@@ -102,6 +102,72 @@ __global__ void dense_kernel(const float *X1, const float *X2, const __nv_bfloat
     Y[row * O + o] = y;
 }
 
+// The same layer for 64 outputs, register-tiled: a block of 64 x 16 threads
+// covers 64 rows (thread (o, ry): output o of rows 4 ry .. 4 ry + 3), the
+// weights go to shared memory once per 64 rows, and per 4 inputs a thread makes
+// 4 weight loads and 4 broadcast float4 loads of x for 16 FMAs.  Inputs are
+// padded to a multiple of 4 with zero weights.
+template <int I1, int I2>
+constexpr int dense64_smem()
+{
+    return 2 * (((I1 + I2) + 3) & ~3) * 64 * (int)sizeof(float);
+}
+
+template <int I1, int I2, bool RELU, bool RES>
+__global__ void __launch_bounds__(1024) dense64_kernel(const float *X1, const float *X2, const __nv_bfloat16 *W1,
+                                                       const __nv_bfloat16 *W2, const __nv_bfloat16 *bias,
+                                                       const float *RESin, float *A, float *Y, int64_t rows)
+{
+    constexpr int O = 64, RPT = 4, RPB = 16 * RPT, IN = I1 + I2, INP = (IN + 3) & ~3;
+    extern __shared__ __align__(16) float dsm[];
+    float *w = dsm;            // [INP][O]
+    float *x = dsm + INP * O;  // [RPB][INP]
+    const int o = threadIdx.x, ry = threadIdx.y, tid = ry * O + o;
+    for (int e = tid; e < INP * O; e += O * 16) {
+        const int i = e / O, oo = e - i * O;
+        float v = 0.0f;
+        if (i < I1)
+            v = __bfloat162float(W1[i * O + oo]);
+        else if (i < IN)
+            v = __bfloat162float(W2[(i - I1) * O + oo]);
+        w[e] = v;
+    }
+    const int64_t row0 = (int64_t)blockIdx.x * RPB;
+    for (int e = tid; e < RPB * INP; e += O * 16) {
+        const int r = e / INP, c = e - r * INP;
+        const int64_t row = row0 + r;
+        float v = 0.0f;
+        if (row < rows && c < IN) v = c < I1 ? X1[row * I1 + c] : X2[row * I2 + (c - I1)];
+        x[e] = v;
+    }
+    __syncthreads();
+    const float b0 = __bfloat162float(bias[o]);
+    float acc[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) acc[r] = b0;
+#pragma unroll 4
+    for (int i = 0; i < INP; i += 4) {
+        const float w0 = w[i * O + o], w1 = w[(i + 1) * O + o], w2 = w[(i + 2) * O + o], w3 = w[(i + 3) * O + o];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const float4 xv = *reinterpret_cast<const float4 *>(&x[(ry * RPT + r) * INP + i]);
+            acc[r] = fmaf(xv.x, w0, acc[r]);
+            acc[r] = fmaf(xv.y, w1, acc[r]);
+            acc[r] = fmaf(xv.z, w2, acc[r]);
+            acc[r] = fmaf(xv.w, w3, acc[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int64_t row = row0 + ry * RPT + r;
+        if (row >= rows) continue;
+        if (A) A[row * O + o] = acc[r];
+        float y = RELU ? fmaxf(acc[r], 0.0f) : acc[r];
+        if (RES) y += RESin[row * O + o];
+        Y[row * O + o] = y;
+    }
+}
+
 // M[b, i, :] = mean over neighbours j of H[b, j, :]
 __global__ void gather_mean_kernel(const int32_t *adj_ptr, const int32_t *adj, const float *Hin, int64_t nv, int B,
                                    int Hd, float *M)
@@ -426,15 +492,18 @@ static gyps_status forward(Mpnn *P, Mesh *m, double k, int B, const double2 *R, 
     features_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(R, ldr, m->d_vfeat, nv, B, rsum, kh, a.F);
     GYPS_CUDA(cudaGetLastError());
     const __nv_bfloat16 *W = P->pb;
-    const unsigned g64 = (unsigned)((rows + 15) / 16);
-    dense_kernel<NIN, 0, 64, true, false><<<g64, dim3(64, 16), 0, s>>>(a.F, nullptr, W + P->off_win, nullptr,
-                                                                       W + P->off_bin, nullptr, a.A0, a.Hs[0], rows);
+    const unsigned g64r = (unsigned)((rows + 63) / 64);
+    constexpr int smem_in = dense64_smem<NIN, 0>(), smem_mp = dense64_smem<64, 64>();
+    GYPS_CUDA(cudaFuncSetAttribute(dense64_kernel<64, 64, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   smem_mp));
+    dense64_kernel<NIN, 0, true, false><<<g64r, dim3(64, 16), smem_in, s>>>(a.F, nullptr, W + P->off_win, nullptr,
+                                                                            W + P->off_bin, nullptr, a.A0, a.Hs[0], rows);
     GYPS_CUDA(cudaGetLastError());
     for (int l = 0; l < P->L; ++l) {
         gather_mean_kernel<<<(unsigned)((rows + 15) / 16), dim3(64, 16), 0, s>>>(m->d_adj_ptr, m->d_adj, a.Hs[l], nv, B,
                                                                                   64, a.Ms[l]);
         GYPS_CUDA(cudaGetLastError());
-        dense_kernel<64, 64, 64, true, true><<<g64, dim3(64, 16), 0, s>>>(
+        dense64_kernel<64, 64, true, true><<<g64r, dim3(64, 16), smem_mp, s>>>(
             a.Hs[l], a.Ms[l], W + P->ws_off(l), W + P->wn_off(l), W + P->b_off(l), a.Hs[l], a.As[l], a.Hs[l + 1], rows);
         GYPS_CUDA(cudaGetLastError());
     }
