@@ -272,7 +272,10 @@ struct TileCfg {
     static constexpr int H_BYTES = kTileV * HLD * 8;
     static constexpr int S_BYTES = SRC * Q * 16 + SRC * 8;        // staged source points, (slots, area)
     static constexpr int L_BYTES = kTileV * LCAP * 2 + kTileV * 4; // per-slot entry lists of a pass and counts
-    static constexpr int T_BYTES = TPP * 8 + TPP * 4 + 3 * 8 * 4; // (slots, area) of the pass's targets, area, R^T
+    // (slots, area) of the pass's targets, area, R^T; then, 16-byte aligned, area x R^T[m][l]
+    // per target triangle as (c, c)
+    static constexpr int C_OFF = (TPP * 8 + TPP * 4 + 3 * 8 * 4 + 15) / 16 * 16;
+    static constexpr int T_BYTES = C_OFF + TPP * 3 * Q * 8;
     static constexpr int SMEM = H_BYTES + S_BYTES + L_BYTES + T_BYTES;
     static_assert(TPP * Q <= NT && TPP * Q < HLD, "a pass fits the threads and H");
     static_assert(kTileV * (kTileV + 1) * 8 <= H_BYTES, "the block staging fits in H");
@@ -283,12 +286,6 @@ int64_t tile_tri_cap(int q)
 {
     const int tpp = q == 1 ? TileCfg<1>::TPP : q == 3 ? TileCfg<3>::TPP : TileCfg<7>::TPP;
     return (int64_t)tpp * std::max<int64_t>(1, (170 + tpp / 2) / tpp);
-}
-
-__device__ __forceinline__ void cadd_scaled(float2 &acc, float2 g, float c)
-{
-    acc.x = fmaf(g.x, c, acc.x);
-    acc.y = fmaf(g.y, c, acc.y);
 }
 
 template <typename OutT>
@@ -472,6 +469,7 @@ __global__ void __launch_bounds__(128, GYPS_TILE_MINB) tile_block_kernel(const T
     int2 *ttl = reinterpret_cast<int2 *>(smem + C::H_BYTES + C::S_BYTES + C::L_BYTES);
     float *tarea = reinterpret_cast<float *>(ttl + C::TPP);
     float *Rt = tarea + C::TPP;  // Rt[m][l]: R transposed, 3 x 8
+    float2 *ctab = reinterpret_cast<float2 *>(smem + C::H_BYTES + C::S_BYTES + C::L_BYTES + C::C_OFF);  // [tt][m][l]
     const int tid = threadIdx.x;
     float R[Q][3];
 #pragma unroll
@@ -560,7 +558,12 @@ __global__ void __launch_bounds__(128, GYPS_TILE_MINB) tile_block_kernel(const T
                     if (e < C::LCAP) lst[sl * C::LCAP + e] = (uint16_t)((tt << 2) | m);
                 }
             }
-            __syncthreads();  // H and the lists complete
+            for (int c3 = tid; c3 < 3 * Q * ntp; c3 += NT) {
+                const int tt = c3 / (3 * Q), rem = c3 - tt * 3 * Q, m = rem / Q, l = rem - m * Q;
+                const float c = tarea[tt] * Rt[m * 8 + l];
+                ctab[c3] = make_float2(c, c);
+            }
+            __syncthreads();  // H, the lists and the coefficients complete
             // Vacc[32 half + r][jcol] += sum over the slot's entries (triangle t, position m) of
             // area_t sum_l R[l][m] H[jcol][t Q + l]
             const float2 *Hrow = H + jcol * HLD;
@@ -571,12 +574,9 @@ __global__ void __launch_bounds__(128, GYPS_TILE_MINB) tile_block_kernel(const T
                 for (int e = 0; e < n; ++e) {
                     const int code = lst[sl * C::LCAP + e];
                     const int tt = code >> 2, m = code & 3;
-                    float2 v = make_float2(0.f, 0.f);
+                    const float2 *hp = Hrow + tt * Q, *cp = ctab + (tt * 3 + m) * Q;
 #pragma unroll
-                    for (int l = 0; l < Q; ++l) cadd_scaled(v, Hrow[tt * Q + l], Rt[m * 8 + l]);
-                    const float ar = tarea[tt];
-                    acc[r].x = fmaf(v.x, ar, acc[r].x);
-                    acc[r].y = fmaf(v.y, ar, acc[r].y);
+                    for (int l = 0; l < Q; ++l) acc[r] = __ffma2_rn(cp[l], hp[l], acc[r]);
                 }
             }
             __syncthreads();  // before the next pass refills H, ttl, tarea, cnt
