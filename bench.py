@@ -1208,7 +1208,7 @@ def run_assemble(args):
         "dtype": "f32 kernel values and sums, f64 output",
         "roofline": {"bound": "alu", "achieved": gp, "peak": sfu, "unit": UNIT, "frac": gp / sfu,
                      "peak_basis": f"{props.multi_processor_count} SMs x 16/3 pairs/clk x {peak_mhz:.0f} MHz",
-                     "kernel": "tile_block_kernel<3,false,double2>", "traffic": None},
+                     "kernel": "tile_block_kernel<3,false,true,double2>", "traffic": None},
         "config": {"workload": "assemble_sphere10242", "nv": mesh.nv, "nt": mesh.nt, "q": 3, "k": k,
                    "v_bytes": 16 * mesh.nv ** 2},
         "fp32": out["fp32"], "fp64": out["fp64"],

@@ -324,7 +324,9 @@ struct PairSums {
     float2 t0r, t0i, t1r, t1i, t2r, t2i;
 };
 
-template <int Q, bool LAP, bool SELF>
+// CIRC (rules whose R[l][m] is beta + (alpha - beta) [l == m], as the 3-point rule):
+// t_m = area (beta sum_l G_l + (alpha - beta) G_m), without the per-point products.
+template <int Q, bool LAP, bool SELF, bool CIRC>
 __device__ __forceinline__ PairSums pair_sums(const float4 *__restrict__ sxy, const float4 *__restrict__ szg, int pr,
                                               float2 ar, float2 tx, float2 ty, float2 tz, int gk, const float (&R)[Q][3])
 {
@@ -335,6 +337,8 @@ __device__ __forceinline__ PairSums pair_sums(const float4 *__restrict__ sxy, co
     const float2 nmagic = make_float2(-12582912.0f, -12582912.0f);
     PairSums o;
     o.t0r = o.t0i = o.t1r = o.t1i = o.t2r = o.t2i = make_float2(0.f, 0.f);
+    float2 gl_r[CIRC ? Q : 1], gl_i[CIRC ? Q : 1];  // per-point values (CIRC)
+    float2 sr = make_float2(0.f, 0.f), si = make_float2(0.f, 0.f);
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
         const float4 xy = sxy[pr * Q + l], zg = szg[pr * Q + l];  // (x0, x1, y0, y1), (z0, z1, id0, id1)
@@ -371,6 +375,15 @@ __device__ __forceinline__ PairSums pair_sums(const float4 *__restrict__ sxy, co
                 }
             }
         }
+        if (CIRC) {
+            gl_r[CIRC ? l : 0] = gr;
+            sr = __fadd2_rn(sr, gr);
+            if (!LAP) {
+                gl_i[CIRC ? l : 0] = gi;
+                si = __fadd2_rn(si, gi);
+            }
+            continue;
+        }
         const float2 k0 = make_float2(R[l][0], R[l][0]), k1 = make_float2(R[l][1], R[l][1]),
                      k2 = make_float2(R[l][2], R[l][2]);
         o.t0r = __ffma2_rn(gr, k0, o.t0r);
@@ -381,6 +394,22 @@ __device__ __forceinline__ PairSums pair_sums(const float4 *__restrict__ sxy, co
             o.t1i = __ffma2_rn(gi, k1, o.t1i);
             o.t2i = __ffma2_rn(gi, k2, o.t2i);
         }
+    }
+    if (CIRC) {
+        static_assert(!CIRC || Q == 3, "one point per vertex");
+        const float2 cb = __fmul2_rn(ar, make_float2(R[0][1], R[0][1]));                    // area beta
+        const float2 ca = __fmul2_rn(ar, make_float2(R[0][0] - R[0][1], R[0][0] - R[0][1]));  // area (alpha - beta)
+        const float2 br = __fmul2_rn(cb, sr);
+        o.t0r = __ffma2_rn(ca, gl_r[0], br);
+        o.t1r = __ffma2_rn(ca, gl_r[CIRC ? 1 : 0], br);
+        o.t2r = __ffma2_rn(ca, gl_r[CIRC ? 2 : 0], br);
+        if (!LAP) {
+            const float2 bi = __fmul2_rn(cb, si);
+            o.t0i = __ffma2_rn(ca, gl_i[0], bi);
+            o.t1i = __ffma2_rn(ca, gl_i[CIRC ? 1 : 0], bi);
+            o.t2i = __ffma2_rn(ca, gl_i[CIRC ? 2 : 0], bi);
+        }
+        return o;
     }
     o.t0r = __fmul2_rn(o.t0r, ar);
     o.t1r = __fmul2_rn(o.t1r, ar);
@@ -428,7 +457,7 @@ constexpr int kTileUnroll = GYPS_TILE_UNROLL;  // 4 or 8
 // time (U / 2 independent packed pairs; the count is padded to a multiple of U
 // with far-away triangles of zero area), added into the running sums of the
 // vertex positions in list order.
-template <int Q, bool LAP, bool SELF>
+template <int Q, bool LAP, bool SELF, bool CIRC>
 __device__ __forceinline__ void src_sums(const float4 *__restrict__ sxy, const float4 *__restrict__ szg,
                                          const int2 *__restrict__ stl, int nst, float4 tp, int gk,
                                          const float (&R)[Q][3], float2 *__restrict__ Hcol, PosSums &ps)
@@ -444,7 +473,7 @@ __device__ __forceinline__ void src_sums(const float4 *__restrict__ sxy, const f
         for (int u = 0; u < U; ++u) tl[u] = stl[b + u];
 #pragma unroll
         for (int u = 0; u < U / 2; ++u)
-            pr[u] = pair_sums<Q, LAP, SELF>(sxy, szg, (b >> 1) + u,
+            pr[u] = pair_sums<Q, LAP, SELF, CIRC>(sxy, szg, (b >> 1) + u,
                                             make_float2(__int_as_float(tl[2 * u].y), __int_as_float(tl[2 * u + 1].y)),
                                             tx, ty, tz, gk, R);
 #pragma unroll
@@ -452,7 +481,7 @@ __device__ __forceinline__ void src_sums(const float4 *__restrict__ sxy, const f
     }
 }
 
-template <int Q, bool LAP, typename OutT>
+template <int Q, bool LAP, bool CIRC, typename OutT>
 __global__ void __launch_bounds__(128, GYPS_TILE_MINB) tile_block_kernel(const TileArgs a, OutT *out)
 {
     using C = TileCfg<Q>;
@@ -538,9 +567,9 @@ __global__ void __launch_bounds__(128, GYPS_TILE_MINB) tile_block_kernel(const T
                 if (!once) stage(tJ0 + sb, nst);
                 if (active) {
                     if (self)
-                        src_sums<Q, LAP, true>(sxy, szg, stl, nst, tp, gk, R, H + tid, ps);
+                        src_sums<Q, LAP, true, CIRC>(sxy, szg, stl, nst, tp, gk, R, H + tid, ps);
                     else
-                        src_sums<Q, LAP, false>(sxy, szg, stl, nst, tp, gk, R, H + tid, ps);
+                        src_sums<Q, LAP, false, CIRC>(sxy, szg, stl, nst, tp, gk, R, H + tid, ps);
                 }
             }
             if (active) {
@@ -703,7 +732,11 @@ template <int Q, bool LAP, typename OutT>
 static gyps_status launch_blocks_q(Mesh *m, const TileArgs &a, OutT *out, cudaStream_t s)
 {
     using C = TileCfg<Q>;
-    auto kern = tile_block_kernel<Q, LAP, OutT>;
+    // the 3-point rule: R[l][m] = beta + (alpha - beta) [l == m]
+    bool circ = Q == 3;
+    for (int l = 0; l < Q && circ; ++l)
+        for (int c = 0; c < 3; ++c) circ = circ && a.R[3 * l + c] == (l == c ? a.R[0] : a.R[1]);
+    auto kern = circ ? tile_block_kernel<Q, LAP, Q == 3, OutT> : tile_block_kernel<Q, LAP, false, OutT>;
     GYPS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     int occ = 0;
     GYPS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::NT, C::SMEM));
