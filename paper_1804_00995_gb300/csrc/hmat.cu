@@ -559,15 +559,18 @@ __device__ __forceinline__ void cp_async_wait_n()
 // RT_K columns, RT_S stages deep across term boundaries (asynchronous copies,
 // zero-filled past a block's edge), so that no term restarts the pipeline.
 // Each thread owns 4 rows (32 apart) x 4 right-hand sides (16 complex sums)
-// and reads per column 4 complex values of the matrix and 4 of x; unit sums
-// are folded into TwoSum pairs.
+// and reads per column 4 complex values of the matrix and 4 of x; FP32 sums of
+// RT_FOLD units at a time are folded into TwoSum pairs.
 #ifndef GYPS_RT_K
 #define GYPS_RT_K 32
 #endif
 #ifndef GYPS_RT_S
 #define GYPS_RT_S 2
 #endif
-constexpr int RT_ROWS = 128, RT_K = GYPS_RT_K, RT_S = GYPS_RT_S;
+#ifndef GYPS_RT_FOLD
+#define GYPS_RT_FOLD 4
+#endif
+constexpr int RT_ROWS = 128, RT_K = GYPS_RT_K, RT_S = GYPS_RT_S, RT_FOLD = GYPS_RT_FOLD;  // RT_FOLD: a power of 2
 struct RowsTileSmem {
     float2 M[RT_S][RT_K][RT_ROWS];
     float2 X[RT_S][RT_K][hm::NRC];
@@ -630,6 +633,11 @@ __global__ void __launch_bounds__(128) hm_rows16_kernel(const hm::Term *terms, c
         cp_async_commit();
     };
 
+    float2 acc[4][4];  // FP32 sums of up to RT_FOLD units
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
     UnitCursor ui{item.z, 0}, uc{item.z, 0};
 #pragma unroll
     for (int st = 0; st + 1 < RT_S; ++st) issue(ui, st);
@@ -640,11 +648,6 @@ __global__ void __launch_bounds__(128) hm_rows16_kernel(const hm::Term *terms, c
         const int st = q % RT_S;
         const int ncol = terms[uc.tt].ncol;
         const int nj = min(RT_K, ncol - uc.j0);
-        float2 acc[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
         const int njr = (nj + 3) & ~3;  // zero-filled past the edge
 #pragma unroll 4
         for (int jj = 0; jj < njr; ++jj) {
@@ -662,17 +665,20 @@ __global__ void __launch_bounds__(128) hm_rows16_kernel(const hm::Term *terms, c
                     acc[a][b].y = fmaf(mv[a].x, xv[b].y, fmaf(mv[a].y, xv[b].x, acc[a][b].y));
                 }
         }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                two_sum_acc(hi[a][b].x, lo[a][b].x, acc[a][b].x);
-                two_sum_acc(hi[a][b].y, lo[a][b].y, acc[a][b].y);
-            }
         uc.j0 += RT_K;
         if (uc.j0 >= ncol) {
             ++uc.tt;
             uc.j0 = 0;
+        }
+        if ((q & (RT_FOLD - 1)) == RT_FOLD - 1 || uc.tt >= tt_end) {  // fold every RT_FOLD units and at the end
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    two_sum_acc(hi[a][b].x, lo[a][b].x, acc[a][b].x);
+                    two_sum_acc(hi[a][b].y, lo[a][b].y, acc[a][b].y);
+                    acc[a][b] = make_float2(0.f, 0.f);
+                }
         }
         __syncthreads();  // stage st is free for unit q + RT_S
     }
