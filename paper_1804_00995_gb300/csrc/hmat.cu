@@ -553,9 +553,9 @@ __device__ __forceinline__ void cp_async_wait_n()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// The row sums of hm_rows_kernel for 16 right-hand sides, tiled: a CTA owns 128
-// rows of a cluster; the columns of its terms (dense blocks, and U with its
-// projection) stream through shared memory as one sequence of units of up to
+// The row sums of hm_rows_kernel for 16 right-hand sides, tiled: a CTA takes one
+// work item, 128 rows of a cluster and a range of its terms; the columns of those
+// terms (dense blocks, and U with its projection) stream through shared memory as one sequence of units of up to
 // RT_K columns, RT_S stages deep across term boundaries (asynchronous copies,
 // zero-filled past a block's edge), so that no term restarts the pipeline.
 // Each thread owns 4 rows (32 apart) x 4 right-hand sides (16 complex sums)
