@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--precond-meshes", type=int, default=125, help="training meshes (16 solves each)")
     p.add_argument("--precond-steps", type=int, default=3000)
     p.add_argument("--precond-test", type=int, default=50, help="held-out meshes (4 plane waves each)")
+    p.add_argument("--precond-krylov-steps", default="5,15,40",
+                   help="GMRES steps m of the iterates whose errors make the Krylov pairs")
     p.add_argument("--precond-data", default="krylov", choices=["noise", "krylov", "both"],
                    help="training pairs: white-noise residuals, Krylov-iteration errors, or both")
     p.add_argument("--save-precond", default="", help="write the trained network here")
@@ -560,7 +562,8 @@ def run_precond(args):
         pairs += p_n
         stats += s_n
     if args.precond_data in ("krylov", "both"):
-        p_k, s_k = pt.make_krylov_pairs(train_meshes, ndirs=4, steps=(5, 15, 40), tol=1e-5, maxit=600, seed=3)
+        ksteps = tuple(int(v) for v in args.precond_krylov_steps.split(","))
+        p_k, s_k = pt.make_krylov_pairs(train_meshes, ndirs=4, steps=ksteps, tol=1e-5, maxit=600, seed=3)
         pairs += p_k
         stats += s_k
     torch.cuda.synchronize()
@@ -585,7 +588,7 @@ def run_precond(args):
         "metric": "GMRES to 1e-6: flexible GMRES + learned preconditioner vs plain GMRES (iterations, seconds)",
         "value": (s_g / s_p) if s_p > 0 else None, "unit": "x (plain seconds / preconditioned seconds)",
         "higher_is_better": True, "data": "synthetic", "dtype": "bf16 weights, f32 activations",
-        "config": {"workload": "precond_ellipsoids", "train_meshes": len(train_meshes), "train_data": args.precond_data,
+        "config": {"workload": "precond_ellipsoids", "train_meshes": len(train_meshes), "train_data": args.precond_data, "krylov_steps": args.precond_krylov_steps,
                    "pairs_kept": int(sum(s["kept"] for s in stats)),
                    "levels": [4, 5], "k_range": [4, 16], "hidden": 64, "layers": 4, "steps": args.precond_steps,
                    "test_meshes": len(test_meshes), "rhs_per_test_mesh": 4, "restart": 100},
